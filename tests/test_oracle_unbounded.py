@@ -1,0 +1,159 @@
+"""Pins for the oracle's unbounded solve (Sec. 2.6, Hockney-Eastwood) and G2 kernel.
+
+  * brute-force direct summation psi_i = -s h^d sum_j G(x_i - x_j) f_j on
+    small grids (the exact result the doubled-domain convolution must equal);
+  * the kernel itself: -lap G = Gaussian checked by finite differences of the
+    closed form, and the r -> 0 limits;
+  * the Gaussian semigroup closed form of a blob's potential,
+    erf(r / sqrt(2(s^2 + sigma^2))) / (4 pi r) in 3D, with the error falling
+    as the grid is refined;
+  * the curl: the doubled-domain solution differentiated in real space with
+    the closed-form Fourier differentiation matrix.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+import oracle
+import workloads
+from oracle import green
+from oracle.desc import Desc
+
+
+def direct_sum(desc, f, pts=None, padded=False):
+    dim = desc.dim
+    h = [desc.h(a) for a in range(dim)]
+    n = [desc.n[a] for a in range(dim)]
+    src = np.argwhere(np.ones(tuple(reversed(n)), dtype=bool))  # [j][(z),y,x]
+    fv = f.reshape(-1)
+    if pts is None:
+        shape = tuple(2 * m for m in reversed(n)) if padded else tuple(reversed(n))
+        pts = np.argwhere(np.ones(shape, dtype=bool))
+    out = np.zeros(len(pts))
+    hd = np.prod(h)
+    for i, p in enumerate(pts):
+        r2 = 0.0
+        for k in range(dim):
+            ax = dim - 1 - k
+            d = p[k] - src[:, k]
+            if padded:
+                M = 2 * n[ax]
+                d = np.mod(d, M)
+                d = np.minimum(d, M - d)
+            r2 = r2 + (d * h[ax]) ** 2
+        out[i] = -desc.rhs_scale * hd * np.sum(green.green(dim, np.sqrt(r2), desc.sigma) * fv)
+    return out
+
+
+@pytest.mark.parametrize("dim,n", [(3, 6), (3, 8), (2, 12), (2, 16)])
+def test_direct_sum(dim, n):
+    rng = np.random.default_rng(n + dim)
+    d = Desc(dim, (n, n + 2, n)[:dim], (-0.5,) * dim, (0.5, 0.7, 0.4)[:dim], ("U",) * dim, True,
+             rhs_scale=-1.3, sigma=0.09)
+    f = rng.normal(size=d.shape())
+    psi, _ = oracle.solve(d, f)
+    ref = direct_sum(d, f).reshape(d.shape())
+    assert np.max(np.abs(psi[0] - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_kernel_laplacian_3d():
+    sigma = 0.1
+    eps = 1e-3
+    for r in (0.03, 0.1, 0.25, 0.6):
+        # radial Laplacian (1/r^2) d/dr (r^2 dG/dr) by central differences
+        g = lambda s: green.g2_3d(np.array(s), sigma)
+        d1p = (g(r + eps) - g(r)) / eps
+        d1m = (g(r) - g(r - eps)) / eps
+        lap = ((r + eps / 2) ** 2 * d1p - (r - eps / 2) ** 2 * d1m) / eps / r ** 2
+        zeta = math.exp(-r * r / (2 * sigma * sigma)) / ((2 * math.pi) ** 1.5 * sigma ** 3)
+        assert abs(lap + zeta) < 2e-4 * max(zeta, 1.0)
+
+
+def test_kernel_laplacian_2d():
+    sigma = 0.1
+    eps = 1e-3
+    for r in (0.03, 0.1, 0.25, 0.6):
+        g = lambda s: green.g2_2d(np.array(s), sigma)
+        d1p = (g(r + eps) - g(r)) / eps
+        d1m = (g(r) - g(r - eps)) / eps
+        lap = ((r + eps / 2) * d1p - (r - eps / 2) * d1m) / eps / r
+        zeta = math.exp(-r * r / (2 * sigma * sigma)) / (2 * math.pi * sigma ** 2)
+        assert abs(lap + zeta) < 2e-4 * max(zeta, 1.0)
+
+
+def test_kernel_origin_limits():
+    for sigma in (0.05, 0.3):
+        r = np.array([1e-6 * sigma])
+        assert abs(green.g2_3d(r, sigma)[0] - green.g2_3d(np.array([0.0]), sigma)[0]) < 1e-9
+        assert abs(green.g2_2d(r, sigma)[0] - green.g2_2d(np.array([0.0]), sigma)[0]) < 1e-9
+
+
+def blob_potential(r, s, sigma):
+    a = math.sqrt(2 * (s * s + sigma * sigma))
+    safe = np.where(r > 0, r, 1.0)
+    return np.where(r > 0, special.erf(safe / a) / (4 * math.pi * safe), 2 / (a * 4 * math.pi ** 1.5))
+
+
+def test_gaussian_blob_closed_form():
+    errs = []
+    for n in (24, 48):
+        h = 1.0 / n
+        sigma = 2 * h
+        s = 0.06
+        d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, rhs_scale=-1.0, sigma=sigma)
+        c = (0.5 * h, 0.5 * h, 0.5 * h)  # centred on a grid node
+        f = workloads.gaussian_blob_field(n, c, s)
+        psi, _ = oracle.solve(d, f)
+        x = workloads.node_positions(-0.5, 0.5, n, True, n)
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        r = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2)
+        ref = blob_potential(r, s, sigma)
+        errs.append(np.max(np.abs(psi[0] - ref)) / np.max(ref))
+    assert errs[1] < errs[0]
+    assert errs[1] < 1e-3
+
+
+def fourier_diff_matrix(M, period):
+    """Trefethen's closed-form spectral differentiation matrix (Nyquist-free)."""
+    D = np.zeros((M, M))
+    for i in range(M):
+        for j in range(M):
+            if i == j:
+                continue
+            k = i - j
+            if M % 2 == 0:
+                D[i, j] = 0.5 * (-1) ** k / math.tan(k * math.pi / M)
+            else:
+                D[i, j] = 0.5 * (-1) ** k / math.sin(k * math.pi / M)
+    return D * (2 * math.pi / period)
+
+
+def test_curl_matches_real_space_differentiation():
+    n = 6
+    d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, op="CURL", ncomp=3,
+             rhs_scale=-1.0, sigma=0.15)
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=(3, n, n, n))
+    psi, u = oracle.solve(d, f)
+    # full doubled-domain potential by brute force, then real-space derivatives
+    full = np.stack([direct_sum(d, f[c], padded=True).reshape((2 * n,) * 3) for c in range(3)])
+    Dm = fourier_diff_matrix(2 * n, 2 * n * d.h(0))
+    dx = lambda a: np.einsum("ij,zyj->zyi", Dm, a)
+    dy = lambda a: np.einsum("ij,zjx->zix", Dm, a)
+    dz = lambda a: np.einsum("ij,jyx->iyx", Dm, a)
+    curl = np.stack([dy(full[2]) - dz(full[1]), dz(full[0]) - dx(full[2]), dx(full[1]) - dy(full[0])])
+    ref = curl[:, :n, :n, :n]
+    np.testing.assert_allclose(psi, full[:, :n, :n, :n], atol=1e-12)
+    assert np.max(np.abs(u - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def test_nabla_returns_source_ps_periodic():
+    # NABLA after a PS solve gives back the source (minus its mean)
+    n = 16
+    d = Desc(3, (n,) * 3, (0,) * 3, (1.0, 2.0, 1.5), ("P",) * 3, True, "PS", op="NABLA")
+    rng = np.random.default_rng(1)
+    f = rng.normal(size=d.shape())
+    _, lap = oracle.solve(d, f)
+    np.testing.assert_allclose(lap[0], f - f.mean(), atol=1e-11)
