@@ -1,0 +1,207 @@
+/*
+ * sailfish_gb300.h -- C ABI of the GB300 fast Poisson solver library
+ * (libsailfish_gb300.so).
+ *
+ * The library solves  lap(psi) = rhs_scale * f  on a rectangular 2D or 3D
+ * grid with the spectral method of SailFFish (Saverin, arXiv 2301.01145):
+ * forward transform, point-wise multiply by the eigenvalues or by the
+ * transformed Green's function, optional spectral operator, inverse
+ * transform (Sec. 2.4, "Calculating and Retrieving the Solution").
+ *
+ * Conventions used by every call
+ *  - Arrays are row-major [component][z][y][x] (x fastest), 2D: [component][y][x].
+ *  - Element type is float (SF_F32) or double (SF_F64), chosen per plan.
+ *  - Device pointers must be CUDA device (or managed) memory on the current
+ *    device, 16-byte aligned.  Host pointers are only accepted by
+ *    sf_solve_host.  The caller owns every buffer it passes; the library
+ *    records pointers (no copies) and reads/writes them when the enqueued work
+ *    runs on the plan's stream, so buffers must stay alive until then.
+ *  - Every call returns an sf_status; no C++ exception crosses the ABI.
+ *    sf_last_error() gives a thread-local human-readable detail string.
+ *  - Work is asynchronous on the plan's CUDA stream unless stated otherwise.
+ *    Device-side failures (a scheduler wait that gave up, a CUDA error) are
+ *    reported by sf_sync() or by the next call on the plan.
+ *  - No call is thread-safe on the same plan; distinct plans are independent.
+ */
+#ifndef SAILFISH_GB300_H
+#define SAILFISH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sf_plan_s *sf_plan; /* opaque; created and owned by the library */
+
+typedef enum {
+  SF_OK = 0,
+  SF_ERR_ARG = -1,         /* invalid argument or descriptor                         */
+  SF_ERR_UNSUPPORTED = -2, /* valid option combination that this library lacks       */
+  SF_ERR_CUDA = -3,        /* a CUDA runtime call failed (detail in sf_last_error)   */
+  SF_ERR_OOM = -4,         /* device allocation failed                               */
+  SF_ERR_STATE = -5,       /* call out of order (e.g. solve without a source)        */
+  SF_ERR_TIMEOUT = -6      /* a bounded device-side wait in the scheduler gave up    */
+} sf_status;
+
+/* Boundary type of an axis (Sec. 2.4.1 solver types; Sec. 2.5 bounded, 2.6 unbounded). */
+typedef enum { SF_BC_PERIODIC = 0, SF_BC_DIRICHLET = 1, SF_BC_NEUMANN = 2, SF_BC_UNBOUNDED = 3 } sf_bc;
+
+/* Grid type (Sec. 2.4.2, Eq. gridpos): REGULAR = cell-boundary nodes, STAGGERED = cell centres. */
+typedef enum { SF_GRID_REGULAR = 0, SF_GRID_STAGGERED = 1 } sf_grid;
+
+/* Spectral operator applied to psi after the convolution (Sec. 2.4.3, Eq. ft_sd). */
+typedef enum { SF_OP_NONE = 0, SF_OP_GRAD = 1, SF_OP_DIV = 2, SF_OP_CURL = 3, SF_OP_NABLA = 4 } sf_op;
+
+/* Eigenvalue type for bounded axes (Sec. 2.5.2, Table 1). */
+typedef enum { SF_EIG_PS = 0, SF_EIG_FD2 = 1 } sf_eig;
+
+/* Regularised Green's function for unbounded axes (Sec. 2.6.2): order-2 Gaussian. */
+typedef enum { SF_GREEN_G2 = 0 } sf_green;
+
+typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
+
+/* Plan flags (sf_plan_desc.flags). */
+#define SF_FLAG_UNFUSED 1u /* one kernel launch per pass instead of one persistent launch */
+
+/*
+ * Problem description (Sec. 2.4 solver options, Sec. 2.5.1 Table 1).
+ *   dim        2 or 3.
+ *   n[a]       cell count N_c per axis a = x, y, z (n[2] ignored in 2D).  Every
+ *              FFT length used (N_c for periodic, 2 N_c otherwise) must be of the
+ *              form 2^p or 3*2^p and lie in [4, 2048]; N_c >= 2 (>= 3 for
+ *              regular Dirichlet).
+ *   lo, hi     domain bounds X_l, X_u per axis.
+ *   bc[a][s]   boundary type of axis a on its lower (s = 0) and upper (s = 1)
+ *              face.  Both faces of an axis must agree (the paper's solvers
+ *              use uniform boundaries, Sec. 2.4.1).  Either every axis is
+ *              periodic/unbounded, or every axis is Dirichlet/Neumann.
+ *   grid       REGULAR or STAGGERED.  Unbounded axes need STAGGERED.
+ *   eig        PS or FD2 (bounded axes; ignored when unbounded).
+ *   op         spectral operator on psi; needs periodic or unbounded axes.
+ *              GRAD: ncomp 1 -> dim outputs.  DIV: ncomp = dim -> 1 output.
+ *              CURL: 3D ncomp 3 -> 3 outputs; 2D ncomp 1 -> 2 outputs.
+ *              NABLA: ncomp -> ncomp outputs.
+ *   green      kernel for unbounded solves; green_sigma its Gaussian width.
+ *   ncomp      number of field components solved together (1..3).
+ *   prec       arithmetic of the solve (tables are always built in FP64).
+ *   rhs_scale  the plan solves lap(psi) = rhs_scale * f.
+ *   flags      SF_FLAG_* bits, 0 by default.
+ */
+typedef struct {
+  int32_t dim;
+  int32_t n[3];
+  double lo[3];
+  double hi[3];
+  int32_t bc[3][2];
+  int32_t grid;
+  int32_t eig;
+  int32_t op;
+  int32_t green;
+  double green_sigma;
+  int32_t ncomp;
+  int32_t prec;
+  double rhs_scale;
+  uint32_t flags;
+} sf_plan_desc;
+
+/*
+ * Array extents per axis (Sec. 2.4.2 "the number of resolved grid positions
+ * changes depending on the type of solver"):
+ *   periodic, unbounded, staggered Dirichlet/Neumann:  N_c points
+ *   regular Dirichlet/Neumann:                         N_c + 1 points
+ * For regular Dirichlet axes the two boundary nodes of the source are ignored
+ * and those of psi are filled with the face values (0 without face data).
+ */
+
+/* Create a plan (Sec. 2.4.4 "Solver Initialization": grid set-up, transform
+ * plans, Green's function / eigenvalues, operators).  Allocates the plan's
+ * tables and workspace with cudaMalloc on the current device and, for
+ * unbounded axes, tabulates G and transforms it in FP64 on the GPU.
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream) on which all
+ * later work of the plan is enqueued.  On failure *out is NULL. */
+sf_status sf_plan_create(sf_plan *out, const sf_plan_desc *d, void *cuda_stream);
+
+/* Change the stream later work is enqueued on. */
+sf_status sf_plan_set_stream(sf_plan p, void *cuda_stream);
+
+/* Shapes as [ncomp][z][y][x] (2D: [ncomp][1][y][x]) of the source (in_shape),
+ * of psi (out_shape) and of the operator output (op_shape, all zero when op is
+ * NONE), and the bytes of device workspace the plan holds.  Any pointer may be
+ * NULL. */
+sf_status sf_plan_query(sf_plan p, size_t in_shape[4], size_t out_shape[4], size_t op_shape[4],
+                        size_t *workspace_bytes);
+
+/* Paper's Set_Input (Sec. 2.4.5): record the device source f; no copy. */
+sf_status sf_set_source(sf_plan p, const void *dev_f);
+
+/* Inhomogeneous boundary data for FD2 solves (Sec. 2.5.2, Sec. 4.2).
+ * axis 0..dim-1, side 0 (X_l) or 1 (X_u).  dev_face holds one value per node
+ * of the two other axes, row-major with the higher axis first ([z][y] for an x
+ * face, [z][x] for a y face, [y][x] for a z face; 2D: [y] or [x]).
+ * Dirichlet: psi on the face; Neumann: d psi / d x_axis on the face.
+ * NULL removes the face (homogeneous).  Only for ncomp == 1, FD2, D/N axes. */
+sf_status sf_set_boundary(sf_plan p, int axis, int side, const void *dev_face);
+
+/* Paper's Forward_Transform + Convolution + Backward_Transform (Sec. 2.4.5):
+ * enqueue the forward transforms, the point-wise multiply, the operator and
+ * every inverse transform except the last (x) one, whose output is written
+ * by sf_get_output.  Needs a source. */
+sf_status sf_solve(sf_plan p);
+
+/* Paper's Get_Output: enqueue the final inverse transform along x fused with
+ * the extraction of the unpadded result and the Dirichlet boundary fill,
+ * writing psi ([ncomp][...]) and, when op != NONE, the operator output. */
+sf_status sf_get_output(sf_plan p, void *dev_psi, void *dev_op_out);
+
+/* Set_Input + solve + Get_Output in one call (one persistent kernel launch
+ * unless SF_FLAG_UNFUSED). */
+sf_status sf_execute(sf_plan p, const void *dev_f, void *dev_psi, void *dev_op_out);
+
+/* End-to-end solve on HOST buffers: copies f host->device, solves, copies psi
+ * (and the operator output) device->host, all on the plan stream, and waits
+ * for completion.  Pinned host memory gives full copy bandwidth.  Uses device
+ * staging buffers owned by the plan. */
+sf_status sf_solve_host(sf_plan p, const void *host_f, void *host_psi, void *host_op_out);
+
+/* Transposed solve for gradients: given dL/dpsi (g_psi, may be NULL) and
+ * dL/d(op output) (g_op, may be NULL), write dL/df into g_f.  The solve is
+ * affine in f; boundary data only shifts it, so it does not enter here.
+ * Same pass structure as the solve with the multiplier applied to the
+ * conjugate-transposed operator (the paper has no adjoint; this is the
+ * exact transpose of the discrete map). */
+sf_status sf_solve_adjoint(sf_plan p, const void *dev_g_psi, const void *dev_g_op, void *dev_g_f);
+
+/* Batched solve of independent problems in one persistent kernel launch.
+ * plans: n plans of the same precision (their own stream is ignored; the
+ * batch uses cuda_stream).  The batch references the plans' tables and owns
+ * a work list and workspace; destroy it before its plans. */
+sf_status sf_batch_create(sf_plan *batch, const sf_plan *plans, int n, void *cuda_stream);
+
+/* Enqueue one batched solve: f[i], psi[i], op[i] are the i-th problem's
+ * buffers (op may be NULL, or op[i] NULL when that plan has no operator).
+ * The first call captures the launch sequence into a CUDA graph that later
+ * calls replay while the pointers stay the same. */
+sf_status sf_batch_solve(sf_plan batch, const void *const *f, void *const *psi, void *const *op);
+
+/* Wait for the plan's stream and report device-side status (SF_ERR_TIMEOUT if
+ * a scheduler wait gave up, SF_ERR_CUDA on an asynchronous CUDA error). */
+sf_status sf_sync(sf_plan p);
+
+/* Kernel launches one sf_execute / sf_batch_solve enqueues (for accounting). */
+int sf_plan_launches(sf_plan p);
+
+/* Release a plan or batch and its device memory (waits for its stream). */
+sf_status sf_plan_destroy(sf_plan p);
+
+const char *sf_status_string(sf_status s);
+const char *sf_last_error(void);
+
+/* Library version string. */
+const char *sf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAILFISH_GB300_H */

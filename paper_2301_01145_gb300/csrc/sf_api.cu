@@ -1,0 +1,1017 @@
+// sf_api.cu -- host implementation of the C ABI declared in include/sailfish_gb300.h.
+//
+// Plan creation follows the initialisation sequence of Sec. 2.4.4 (grid
+// set-up, transform plans, Green's function or eigenvalues, operators); the
+// solve follows the execution sequence of Sec. 2.4.5.  All tables are built
+// in FP64 (host libm for twiddles, phases, eigenvalues and wavenumbers; FP64
+// GPU kernels for the Green's function and its transform) and rounded once
+// to the plan's precision.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sailfish_gb300.h"
+#include "sf_kernels.cuh"
+
+using namespace sfg;
+
+namespace {
+
+thread_local std::string g_err;
+
+sf_status fail(sf_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+#define SF_CK(call)                                                                                  \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return fail(SF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define SF_TRY(expr)              \
+  do {                            \
+    sf_status s_ = (expr);        \
+    if (s_ != SF_OK) return s_;   \
+  } while (0)
+
+const double kPi = 3.14159265358979323846264338327950288;
+const size_t kSmemBudget = 112 * 1024;  // per CTA: two CTAs share one SM
+const int kMaxW = 16;
+const unsigned long long kTimeoutNs = 2000000000ull;  // 2 s bound on any scheduler wait
+
+bool valid_len(int L) {
+  if (L < 4 || L > 2048) return false;
+  int m = L;
+  if (m % 3 == 0) m /= 3;
+  return (m & (m - 1)) == 0;
+}
+
+// radix plan: one radix-3 stage if needed, then radix-16 stages, then 2/4/8
+int radix_plan(int L, int *rad) {
+  int n = 0;
+  int m = L;
+  if (m % 3 == 0) {
+    rad[n++] = 3;
+    m /= 3;
+  }
+  while (m >= 16) {
+    rad[n++] = 16;
+    m /= 16;
+  }
+  if (m > 1) rad[n++] = m;
+  return n;
+}
+
+struct AxisHost {
+  int kind, n, nodes, u0, nu, L, ns, k0, nst, radix[5];
+  double Ldom, h;
+  std::vector<double> tw, phase, lam, kap, kap2;  // complex tables interleaved re,im
+};
+
+// per-axis transform geometry and tables (Table 1; Sec. 2.4.3 wavenumbers)
+AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, bool cpath) {
+  AxisHost a{};
+  a.kind = kind;
+  a.n = n;
+  a.Ldom = hi - lo;
+  a.h = a.Ldom / n;
+  switch (kind) {
+    case AK_P: a.nodes = n; a.u0 = 0; a.nu = n; a.L = n; a.k0 = 0; break;
+    case AK_U: a.nodes = n; a.u0 = 0; a.nu = n; a.L = 2 * n; a.k0 = 0; break;
+    case AK_DR: a.nodes = n + 1; a.u0 = 1; a.nu = n - 1; a.L = 2 * n; a.k0 = 1; break;
+    case AK_NR: a.nodes = n + 1; a.u0 = 0; a.nu = n + 1; a.L = 2 * n; a.k0 = 0; break;
+    case AK_DS: a.nodes = n; a.u0 = 0; a.nu = n; a.L = 2 * n; a.k0 = 1; break;
+    case AK_NS: a.nodes = n; a.u0 = 0; a.nu = n; a.L = 2 * n; a.k0 = 0; break;
+  }
+  if (cpath) a.ns = is_x ? a.L / 2 + 1 : a.L;
+  else a.ns = a.nu;
+  a.nst = radix_plan(a.L, a.radix);
+  const int L = a.L;
+  a.tw.resize(2 * (size_t)L);
+  for (int j = 0; j < L; ++j) {
+    const double ang = -2.0 * kPi * (double)j / (double)L;
+    a.tw[2 * j] = std::cos(ang);
+    a.tw[2 * j + 1] = std::sin(ang);
+  }
+  a.phase.assign(2 * (size_t)(n + 1), 0.0);
+  for (int k = 0; k <= n; ++k) {
+    double re = 1, im = 0;
+    const double c = std::cos(kPi * k / (2.0 * n)), s = std::sin(kPi * k / (2.0 * n));
+    switch (kind) {
+      case AK_DR: re = 0; im = -1; break;
+      case AK_NS: re = c; im = s; break;
+      case AK_DS: re = s; im = -c; break;  // -i e^{i pi k/2n}
+      default: break;
+    }
+    a.phase[2 * k] = re;
+    a.phase[2 * k + 1] = im;
+  }
+  a.lam.assign(a.ns, 0.0);
+  a.kap.assign(a.ns, 0.0);
+  a.kap2.assign(a.ns, 0.0);
+  for (int i = 0; i < a.ns; ++i) {
+    if (kind == AK_P) {
+      const int k = i;  // FFT index (x: half spectrum)
+      const int kk = std::min(k, n - k);
+      if (eig == SF_EIG_PS) a.lam[i] = -std::pow(2.0 * kPi * kk / a.Ldom, 2);
+      else a.lam[i] = -(4.0 / (a.h * a.h)) * std::pow(std::sin(kPi * k / n), 2);
+    } else if (kind != AK_U) {
+      const int m = i + a.k0;  // mode number of Table 1
+      if (eig == SF_EIG_PS) a.lam[i] = -std::pow(kPi * m / a.Ldom, 2);
+      else a.lam[i] = -(4.0 / (a.h * a.h)) * std::pow(std::sin(kPi * m / (2.0 * n)), 2);
+    }
+    if (cpath) {
+      const int M = L;  // points of the periodic (possibly doubled) axis
+      const double period = (kind == AK_U) ? 2.0 * a.Ldom : a.Ldom;
+      const int k = i;
+      int ks = (k <= M / 2) ? k : k - M;
+      const double kap2v = std::pow(2.0 * kPi * std::min(k, M - k) / period, 2);
+      if (M % 2 == 0 && k == M / 2) ks = 0;  // Nyquist: no odd derivative
+      a.kap[i] = 2.0 * kPi * ks / period;
+      a.kap2[i] = kap2v;
+    }
+  }
+  return a;
+}
+
+template <typename T> struct DevMem {
+  std::vector<void *> ptrs;
+  ~DevMem() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+  sf_status alloc(void **out, size_t bytes) {
+    *out = nullptr;
+    if (bytes == 0) return SF_OK;
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *out = nullptr;
+      return fail(e == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA,
+                  std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    ptrs.push_back(*out);
+    return SF_OK;
+  }
+  template <typename U> sf_status upload(U **out, const std::vector<double> &v, bool complex_pairs) {
+    std::vector<U> tmp(v.size());
+    for (size_t i = 0; i < v.size(); ++i) tmp[i] = (U)v[i];
+    void *p = nullptr;
+    SF_TRY(alloc(&p, tmp.size() * sizeof(U)));
+    if (!tmp.empty()) SF_CK(cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(U), cudaMemcpyHostToDevice));
+    *out = (U *)p;
+    (void)complex_pairs;
+    return SF_OK;
+  }
+};
+
+template <typename T> sf_status fill_axis(Axis<T> &d, const AxisHost &h, DevMem<T> &mem) {
+  d.kind = h.kind;
+  d.n = h.n;
+  d.nodes = h.nodes;
+  d.u0 = h.u0;
+  d.nu = h.nu;
+  d.L = h.L;
+  d.ns = h.ns;
+  d.k0 = h.k0;
+  d.nst = h.nst;
+  for (int i = 0; i < 5; ++i) d.radix[i] = h.radix[i];
+  T *tw, *ph, *lam, *kap, *kap2;
+  SF_TRY(mem.template upload<T>(&tw, h.tw, true));
+  SF_TRY(mem.template upload<T>(&ph, h.phase, true));
+  SF_TRY(mem.template upload<T>(&lam, h.lam, false));
+  SF_TRY(mem.template upload<T>(&kap, h.kap, false));
+  SF_TRY(mem.template upload<T>(&kap2, h.kap2, false));
+  d.tw = reinterpret_cast<const cx<T> *>(tw);
+  d.phase = reinterpret_cast<const cx<T> *>(ph);
+  d.lam = lam;
+  d.kap = kap;
+  d.kap2 = kap2;
+  return SF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pass lists and their execution
+// ---------------------------------------------------------------------------
+template <typename T> int pass_tiles(const Prob<T> &P, const Pass<T> &ps) {
+  const int W = ps.W;
+  switch (ps.kind) {
+    case PK_XFWD: return P.nin * P.nuz * cdiv(P.nuy, 2 * W);
+    case PK_YFWD: return P.nin * P.nsx * cdiv(P.nuz, lines_per_tile(P.cpath, W));
+    case PK_ZSTAGE: return P.nsx * cdiv(P.nsy, lines_per_tile(P.cpath, W));
+    case PK_YINV: return P.nout * P.nsx * cdiv(P.nuz, lines_per_tile(P.cpath, W));
+    case PK_XINV: return P.nout * P.nuz * cdiv(P.nuy, 2 * W);
+    case PK_YSTAGE2: return cdiv(P.nsx, lines_per_tile(P.cpath, W));
+    case PK_FILL: return cdiv(P.fill_count * P.nout, 4096);
+    case PK_ZFWD: return P.nsx * cdiv(P.nsy, 2 * W);
+  }
+  return 0;
+}
+
+// choose the tile width W (packed lines) for a pass: largest power of two that
+// fits the shared-memory budget and does not exceed the lines available
+template <typename T> void size_pass(const Prob<T> &P, Pass<T> &ps) {
+  int L = 0, nbuf = 2, lines = 1;
+  switch (ps.kind) {
+    case PK_XFWD: L = P.ax[0].L; lines = cdiv(P.nuy, 2); break;
+    case PK_XINV: L = P.ax[0].L; lines = cdiv(P.nuy, 2); break;
+    case PK_YFWD:
+    case PK_YINV: L = P.ax[1].L; lines = P.cpath ? P.nuz : cdiv(P.nuz, 2); break;
+    case PK_ZSTAGE: L = P.ax[2].L; nbuf = P.ncomp + 2; lines = P.cpath ? P.nsy : cdiv(P.nsy, 2); break;
+    case PK_YSTAGE2: L = P.ax[1].L; nbuf = P.ncomp + 2; lines = P.cpath ? P.nsx : cdiv(P.nsx, 2); break;
+    case PK_ZFWD: L = P.ax[2].L; lines = cdiv(P.nsy, 2); break;
+    case PK_FILL: ps.W = 1; ps.Wp = 1; ps.nbuf = 0; ps.bufsz = 0; return;
+  }
+  int W = kMaxW;
+  while (W > 1 && W / 2 >= lines) W >>= 1;
+  for (;; W >>= 1) {
+    const int Wp = W > 1 ? W + 1 : 1;
+    const size_t bs = std::max((size_t)L * Wp, (size_t)(L + 2) * W);
+    if (W == 1 || nbuf * bs * sizeof(cx<T>) <= kSmemBudget) {
+      ps.W = W;
+      ps.Wp = Wp;
+      ps.nbuf = nbuf;
+      ps.bufsz = (int)bs;
+      return;
+    }
+  }
+}
+
+template <typename T> struct ExecList {
+  std::vector<Pass<T>> passes;
+  std::vector<int> start;
+  Pass<T> *d_passes = nullptr;
+  int *d_start = nullptr;
+  unsigned *d_done = nullptr;
+  size_t smem = 0;
+  int total = 0;
+
+  void add(const Prob<T> &P, int kind, int prob, int dep0 = -1, int dep1 = -1) {
+    Pass<T> ps{};
+    ps.kind = kind;
+    ps.prob = prob;
+    size_pass<T>(P, ps);
+    ps.ntiles = pass_tiles<T>(P, ps);
+    ps.dep[0] = dep0;
+    ps.dep[1] = dep1;
+    ps.depcnt[0] = dep0 >= 0 ? passes[dep0].ntiles : 0;
+    ps.depcnt[1] = dep1 >= 0 ? passes[dep1].ntiles : 0;
+    if (ps.ntiles > 0) passes.push_back(ps);
+  }
+  sf_status upload(DevMem<T> &mem) {
+    start.assign(passes.size() + 1, 0);
+    smem = 0;
+    for (size_t i = 0; i < passes.size(); ++i) {
+      start[i + 1] = start[i] + passes[i].ntiles;
+      smem = std::max(smem, (size_t)passes[i].nbuf * passes[i].bufsz * sizeof(cx<T>));
+    }
+    total = start.back();
+    void *p;
+    SF_TRY(mem.alloc(&p, std::max<size_t>(1, passes.size()) * sizeof(Pass<T>)));
+    d_passes = (Pass<T> *)p;
+    SF_TRY(mem.alloc(&p, start.size() * sizeof(int)));
+    d_start = (int *)p;
+    SF_TRY(mem.alloc(&p, std::max<size_t>(1, passes.size()) * sizeof(unsigned)));
+    d_done = (unsigned *)p;
+    if (!passes.empty()) SF_CK(cudaMemcpy(d_passes, passes.data(), passes.size() * sizeof(Pass<T>), cudaMemcpyHostToDevice));
+    SF_CK(cudaMemcpy(d_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return SF_OK;
+  }
+};
+
+template <typename T> sf_status set_kernel_attrs() {
+  static bool done = false;
+  if (done) return SF_OK;
+  SF_CK(cudaFuncSetAttribute(k_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  SF_CK(cudaFuncSetAttribute(k_exec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  done = true;
+  return SF_OK;
+}
+
+// add the dependency edges of a linear chain: each pass waits for all tiles of
+// the previous one (FILL touches disjoint nodes and waits for nothing)
+template <typename T>
+sf_status launch_list(ExecList<T> &ex, const Prob<T> *d_probs, bool fused, cudaStream_t st, ExecCtl *ctl, unsigned *sticky,
+                      const IOArgs<T> &io, int *launches) {
+  SF_TRY(set_kernel_attrs<T>());
+  if (ex.passes.empty()) return SF_OK;
+  if (fused) {
+    SF_CK(cudaMemsetAsync(ex.d_done, 0, ex.passes.size() * sizeof(unsigned), st));
+    SF_CK(cudaMemsetAsync(ctl, 0, sizeof(ExecCtl), st));
+    int dev = 0, nsm = 0, per = 0;
+    SF_CK(cudaGetDevice(&dev));
+    SF_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SF_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_exec<T>, SF_THREADS, ex.smem));
+    if (per < 1) return fail(SF_ERR_CUDA, "executor does not fit on an SM");
+    const int grid = std::min(ex.total, nsm * per);
+    k_exec<T><<<grid, SF_THREADS, ex.smem, st>>>(d_probs, ex.d_passes, ex.d_start, (int)ex.passes.size(), ex.d_done, ctl,
+                                                 sticky, kTimeoutNs, io);
+    SF_CK(cudaGetLastError());
+    if (launches) *launches += 1;
+  } else {
+    for (size_t i = 0; i < ex.passes.size(); ++i) {
+      const Pass<T> &ps = ex.passes[i];
+      const size_t sm = (size_t)ps.nbuf * ps.bufsz * sizeof(cx<T>);
+      k_pass<T><<<ps.ntiles, SF_THREADS, sm, st>>>(d_probs, ex.d_passes, (int)i, io);
+      SF_CK(cudaGetLastError());
+      if (launches) *launches += 1;
+    }
+  }
+  return SF_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the plan object
+// ---------------------------------------------------------------------------
+struct sf_plan_s {
+  virtual ~sf_plan_s() {}
+  sf_plan_desc d{};
+  cudaStream_t stream = nullptr;
+  bool is_batch = false;
+  int launches_per_exec = 0;
+  virtual sf_status solve_part(bool front, bool back, const void *f, void *psi, void *op, int *launches) = 0;
+  virtual sf_status adjoint(const void *gp, const void *go, void *gf) = 0;
+  virtual sf_status sync() = 0;
+  virtual sf_status query(size_t in_shape[4], size_t out_shape[4], size_t op_shape[4], size_t *ws) = 0;
+  virtual sf_status set_face(int axis, int side, const void *p) = 0;
+  virtual sf_status host_solve(const void *hf, void *hpsi, void *hop) = 0;
+  const void *src = nullptr;
+  bool solved = false;
+};
+
+template <typename T> struct PlanImpl : sf_plan_s {
+  DevMem<T> mem;
+  Prob<T> P{};   // forward problem
+  Prob<T> PA{};  // adjoint problem
+  Prob<T> *d_probs = nullptr;  // [0] forward, [1] adjoint
+  ExecList<T> ex_front, ex_back, ex_all, ex_adj;
+  ExecCtl *ctl = nullptr;
+  unsigned *sticky = nullptr;
+  const T *faces[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  size_t ws_bytes = 0;
+  size_t field_elems = 0, op_elems = 0;
+  void *st_in = nullptr, *st_psi = nullptr, *st_op = nullptr;  // host-solve staging
+
+  bool fused() const { return !(d.flags & SF_FLAG_UNFUSED); }
+
+  IOArgs<T> io_forward(const void *f, void *psi, void *op) const {
+    IOArgs<T> io{};
+    io.use = 1;
+    for (int c = 0; c < P.ncomp; ++c) io.in[c] = f ? (const T *)f + c * field_elems : nullptr;
+    for (int c = 0; c < P.ncomp; ++c) io.out[c] = psi ? (T *)psi + c * field_elems : nullptr;
+    for (int o = 0; o < P.nop; ++o) io.out[P.ncomp + o] = op ? (T *)op + o * field_elems : nullptr;
+    int hf = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int s = 0; s < 2; ++s) {
+        io.face[a][s] = faces[a][s];
+        if (faces[a][s]) hf = 1;
+      }
+    io.has_face = hf;
+    return io;
+  }
+
+  sf_status init(const sf_plan_desc &desc, cudaStream_t st);
+  sf_status build_green();
+
+  sf_status solve_part(bool front, bool back, const void *f, void *psi, void *op, int *launches) override {
+    IOArgs<T> io = io_forward(f, psi, op);
+    if (front && back) return launch_list<T>(ex_all, d_probs, fused(), stream, ctl, sticky, io, launches);
+    if (front) return launch_list<T>(ex_front, d_probs, fused(), stream, ctl, sticky, io, launches);
+    return launch_list<T>(ex_back, d_probs, fused(), stream, ctl, sticky, io, launches);
+  }
+
+  sf_status adjoint(const void *gp, const void *go, void *gf) override {
+    IOArgs<T> io{};
+    io.use = 1;
+    for (int c = 0; c < P.ncomp; ++c) io.in[c] = gp ? (const T *)gp + c * field_elems : nullptr;
+    for (int o = 0; o < P.nop; ++o) io.in[P.ncomp + o] = go ? (const T *)go + o * field_elems : nullptr;
+    for (int c = 0; c < P.ncomp; ++c) io.out[c] = (T *)gf + c * field_elems;
+    io.has_face = 0;
+    return launch_list<T>(ex_adj, d_probs + 1, fused(), stream, ctl, sticky, io, nullptr);
+  }
+
+  sf_status sync() override {
+    SF_CK(cudaStreamSynchronize(stream));
+    unsigned s = 0;
+    SF_CK(cudaMemcpy(&s, sticky, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (s) {
+      SF_CK(cudaMemset(sticky, 0, sizeof(unsigned)));
+      return fail(SF_ERR_TIMEOUT, "a scheduler wait exceeded its bound; results are invalid");
+    }
+    return SF_OK;
+  }
+
+  sf_status query(size_t in_shape[4], size_t out_shape[4], size_t op_shape[4], size_t *ws) override {
+    const size_t nz = d.dim == 3 ? P.ax[2].nodes : 1;
+    const size_t s3[3] = {nz, (size_t)P.ax[1].nodes, (size_t)P.ax[0].nodes};
+    if (in_shape) {
+      in_shape[0] = P.ncomp;
+      for (int i = 0; i < 3; ++i) in_shape[i + 1] = s3[i];
+    }
+    if (out_shape) {
+      out_shape[0] = P.ncomp;
+      for (int i = 0; i < 3; ++i) out_shape[i + 1] = s3[i];
+    }
+    if (op_shape) {
+      op_shape[0] = P.nop;
+      for (int i = 0; i < 3; ++i) op_shape[i + 1] = P.nop ? s3[i] : 0;
+    }
+    if (ws) *ws = ws_bytes;
+    return SF_OK;
+  }
+
+  sf_status set_face(int axis, int side, const void *p) override {
+    if (axis < 0 || axis >= d.dim || side < 0 || side > 1) return fail(SF_ERR_ARG, "axis/side out of range");
+    const int k = P.ax[axis].kind;
+    if (p && !(k == AK_DR || k == AK_DS || k == AK_NR || k == AK_NS))
+      return fail(SF_ERR_ARG, "boundary data needs a Dirichlet or Neumann axis");
+    if (p && d.eig != SF_EIG_FD2) return fail(SF_ERR_UNSUPPORTED, "inhomogeneous boundaries need FD2 eigenvalues (Sec. 2.5.2)");
+    if (p && P.ncomp != 1) return fail(SF_ERR_UNSUPPORTED, "boundary data only for scalar solves");
+    faces[axis][side] = (const T *)p;
+    return SF_OK;
+  }
+
+  sf_status host_solve(const void *hf, void *hpsi, void *hop) override {
+    const size_t fb = field_elems * sizeof(T);
+    if (!st_in) {
+      SF_TRY(mem.alloc(&st_in, fb * P.ncomp));
+      SF_TRY(mem.alloc(&st_psi, fb * P.ncomp));
+      if (P.nop) SF_TRY(mem.alloc(&st_op, fb * P.nop));
+    }
+    SF_CK(cudaMemcpyAsync(st_in, hf, fb * P.ncomp, cudaMemcpyHostToDevice, stream));
+    SF_TRY(solve_part(true, true, st_in, st_psi, st_op, nullptr));
+    SF_CK(cudaMemcpyAsync(hpsi, st_psi, fb * P.ncomp, cudaMemcpyDeviceToHost, stream));
+    if (P.nop && hop) SF_CK(cudaMemcpyAsync(hop, st_op, fb * P.nop, cudaMemcpyDeviceToHost, stream));
+    return sync();
+  }
+};
+
+static int axis_kind(int bc, int grid) {
+  const bool stag = grid == SF_GRID_STAGGERED;
+  switch (bc) {
+    case SF_BC_PERIODIC: return AK_P;
+    case SF_BC_UNBOUNDED: return AK_U;
+    case SF_BC_DIRICHLET: return stag ? AK_DS : AK_DR;
+    case SF_BC_NEUMANN: return stag ? AK_NS : AK_NR;
+  }
+  return -1;
+}
+
+static int op_outputs(int op, int dim, int ncomp) {
+  switch (op) {
+    case SF_OP_GRAD: return dim;
+    case SF_OP_DIV: return 1;
+    case SF_OP_CURL: return dim == 3 ? 3 : 2;
+    case SF_OP_NABLA: return ncomp;
+  }
+  return 0;
+}
+
+static sf_status validate(const sf_plan_desc &d) {
+  if (d.dim != 2 && d.dim != 3) return fail(SF_ERR_ARG, "dim must be 2 or 3");
+  if (d.prec != SF_F32 && d.prec != SF_F64) return fail(SF_ERR_ARG, "prec must be SF_F32 or SF_F64");
+  if (d.grid != SF_GRID_REGULAR && d.grid != SF_GRID_STAGGERED) return fail(SF_ERR_ARG, "bad grid type");
+  if (d.ncomp < 1 || d.ncomp > 3) return fail(SF_ERR_ARG, "ncomp must be 1..3");
+  if (d.op < SF_OP_NONE || d.op > SF_OP_NABLA) return fail(SF_ERR_ARG, "bad operator");
+  if (d.eig != SF_EIG_PS && d.eig != SF_EIG_FD2) return fail(SF_ERR_ARG, "bad eigenvalue type");
+  if (!(d.rhs_scale == d.rhs_scale) || d.rhs_scale == 0.0 || std::isinf(d.rhs_scale))
+    return fail(SF_ERR_ARG, "rhs_scale must be finite and non-zero");
+  int ncp = 0, nreal = 0, nunb = 0;
+  for (int a = 0; a < d.dim; ++a) {
+    if (d.bc[a][0] != d.bc[a][1]) return fail(SF_ERR_UNSUPPORTED, "different boundary types on the two faces of an axis");
+    const int bc = d.bc[a][0];
+    if (bc < SF_BC_PERIODIC || bc > SF_BC_UNBOUNDED) return fail(SF_ERR_ARG, "bad boundary type");
+    if (!(d.hi[a] > d.lo[a])) return fail(SF_ERR_ARG, "domain bounds need hi > lo");
+    const int n = d.n[a];
+    const int minn = (bc == SF_BC_DIRICHLET && d.grid == SF_GRID_REGULAR) ? 3 : 2;
+    if (n < minn) return fail(SF_ERR_ARG, "too few cells on an axis");
+    const int L = bc == SF_BC_PERIODIC ? n : 2 * n;
+    if (!valid_len(L)) return fail(SF_ERR_UNSUPPORTED, "FFT length " + std::to_string(L) + " is not 2^p or 3*2^p in [4, 2048]");
+    if (bc == SF_BC_PERIODIC || bc == SF_BC_UNBOUNDED) ++ncp;
+    else ++nreal;
+    if (bc == SF_BC_UNBOUNDED) ++nunb;
+  }
+  if (ncp && nreal) return fail(SF_ERR_UNSUPPORTED, "mixing periodic/unbounded with Dirichlet/Neumann axes");
+  if (nunb && nunb != d.dim) return fail(SF_ERR_UNSUPPORTED, "semi-unbounded domains");
+  if (nunb && d.grid != SF_GRID_STAGGERED) return fail(SF_ERR_UNSUPPORTED, "unbounded solves need the staggered grid");
+  if (nunb && d.green != SF_GREEN_G2) return fail(SF_ERR_UNSUPPORTED, "only the G2 kernel is available");
+  if (nunb && !(d.green_sigma > 0.0)) return fail(SF_ERR_ARG, "green_sigma must be positive");
+  if (ncp && d.bc[0][0] == SF_BC_PERIODIC && (d.n[0] % 2)) return fail(SF_ERR_UNSUPPORTED, "odd periodic x length");
+  if (d.op != SF_OP_NONE) {
+    if (nreal) return fail(SF_ERR_UNSUPPORTED, "spectral operators on Dirichlet/Neumann axes");
+    if (d.op == SF_OP_GRAD && d.ncomp != 1) return fail(SF_ERR_ARG, "GRAD needs ncomp = 1");
+    if (d.op == SF_OP_DIV && d.ncomp != d.dim) return fail(SF_ERR_ARG, "DIV needs ncomp = dim");
+    if (d.op == SF_OP_CURL && d.ncomp != (d.dim == 3 ? 3 : 1)) return fail(SF_ERR_ARG, "CURL needs ncomp 3 (3D) or 1 (2D)");
+  }
+  if (d.ncomp + op_outputs(d.op, d.dim, d.ncomp) > SF_MAXF) return fail(SF_ERR_ARG, "too many fields");
+  return SF_OK;
+}
+
+template <typename T> static void derive_extents(Prob<T> &P) {
+  P.nsx = P.ax[0].ns;
+  P.nuy = P.ax[1].nu;
+  P.nsy = P.ax[1].ns;
+  P.nuz = P.dim == 3 ? P.ax[2].nu : 1;
+  P.nsz = P.dim == 3 ? P.ax[2].ns : 1;
+  const int ndx = P.ax[0].nodes, ndy = P.ax[1].nodes, ndz = P.dim == 3 ? P.ax[2].nodes : 1;
+  int fill = 0;
+  if (P.ax[1].kind == AK_DR) fill += 2 * ndz * ndx;
+  if (P.dim == 3 && P.ax[2].kind == AK_DR) fill += 2 * ndy * ndx;
+  P.fill_count = fill;
+}
+
+template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cudaStream_t st) {
+  d = desc;
+  stream = st;
+  SF_TRY(set_kernel_attrs<T>());
+  Prob<T> &p = P;
+  p.dim = d.dim;
+  p.ncomp = d.ncomp;
+  p.nop = op_outputs(d.op, d.dim, d.ncomp);
+  p.op = d.op;
+  const int k0 = axis_kind(d.bc[0][0], d.grid);
+  p.cpath = (k0 == AK_P || k0 == AK_U) ? 1 : 0;
+  p.green = (k0 == AK_U) ? 1 : 0;
+  p.rhs_scale = (T)d.rhs_scale;
+  double prodL = 1.0, hd = 1.0;
+  AxisHost ah[3];
+  for (int a = 0; a < 3; ++a) {
+    if (a < d.dim) {
+      ah[a] = build_axis(axis_kind(d.bc[a][0], d.grid), d.n[a], d.lo[a], d.hi[a], d.eig, a == 0, p.cpath);
+      prodL *= ah[a].L;
+      hd *= ah[a].h;
+    } else {  // unused z axis of a 2D problem: a trivial periodic axis of one point
+      ah[a] = AxisHost{};
+      ah[a].kind = AK_P;
+      ah[a].n = 1;
+      ah[a].nodes = 1;
+      ah[a].nu = 1;
+      ah[a].L = 1;
+      ah[a].ns = 1;
+    }
+    if (a < d.dim) SF_TRY(fill_axis<T>(p.ax[a], ah[a], mem));
+    else {
+      p.ax[a] = Axis<T>{};
+      p.ax[a].kind = AK_P;
+      p.ax[a].n = 1;
+      p.ax[a].nodes = 1;
+      p.ax[a].nu = 1;
+      p.ax[a].L = 1;
+      p.ax[a].ns = 1;
+    }
+  }
+  p.mscale = (T)(d.rhs_scale / prodL);
+  derive_extents<T>(p);
+  field_elems = (size_t)p.ax[0].nodes * p.ax[1].nodes * (d.dim == 3 ? p.ax[2].nodes : 1);
+  // FD2 lifting weights (Sec. 2.5.2 boundary weighting; divided by rhs_scale
+  // because the multiplier carries rhs_scale)
+  for (int a = 0; a < d.dim; ++a) {
+    const double h = ah[a].h;
+    double w0 = 0, w1 = 0;
+    switch (ah[a].kind) {
+      case AK_DR: w0 = w1 = -1.0 / (h * h); break;
+      case AK_DS: w0 = w1 = -2.0 / (h * h); break;
+      case AK_NR: w0 = 2.0 / h; w1 = -2.0 / h; break;
+      case AK_NS: w0 = 1.0 / h; w1 = -1.0 / h; break;
+    }
+    p.facew[a][0] = (T)(w0 / d.rhs_scale);
+    p.facew[a][1] = (T)(w1 / d.rhs_scale);
+  }
+  // workspace: every buffer sized for ncomp + nop fields (forward and adjoint)
+  const int nf = p.ncomp + p.nop;
+  const size_t esz = p.cpath ? sizeof(cx<T>) : sizeof(T);
+  const size_t eA = (size_t)nf * p.nsx * p.nuz * p.nuy;
+  const size_t eI = d.dim == 3 ? (size_t)nf * p.nsx * p.nuz * p.nsy : 0;
+  SF_TRY(mem.alloc(&p.A, eA * esz));
+  SF_TRY(mem.alloc(&p.B, eA * esz));
+  if (eI) {
+    SF_TRY(mem.alloc(&p.I1, eI * esz));
+    SF_TRY(mem.alloc(&p.I2, eI * esz));
+  }
+  ws_bytes = (2 * eA + 2 * eI) * esz;
+  void *tmp;
+  SF_TRY(mem.alloc(&tmp, sizeof(ExecCtl)));
+  ctl = (ExecCtl *)tmp;
+  SF_TRY(mem.alloc(&tmp, sizeof(unsigned)));
+  sticky = (unsigned *)tmp;
+  SF_CK(cudaMemset(sticky, 0, sizeof(unsigned)));
+  if (p.green) {
+    p.gny = d.n[1] + 1;
+    p.gnz = d.dim == 3 ? d.n[2] + 1 : 1;
+    SF_TRY(build_green());
+    (void)hd;
+  }
+  // forward / adjoint variants
+  p.nin = p.ncomp;
+  p.nout = nf;
+  p.adjoint = 0;
+  p.nrw = 0;
+  PA = p;
+  PA.nin = nf;
+  PA.nout = p.ncomp;
+  PA.adjoint = 1;
+  for (int a = 0; a < d.dim; ++a)
+    if (p.ax[a].kind == AK_NR) PA.nrw = 1;
+  SF_TRY(mem.alloc(&tmp, 2 * sizeof(Prob<T>)));
+  d_probs = (Prob<T> *)tmp;
+  SF_CK(cudaMemcpy(d_probs, &P, sizeof(Prob<T>), cudaMemcpyHostToDevice));
+  SF_CK(cudaMemcpy(d_probs + 1, &PA, sizeof(Prob<T>), cudaMemcpyHostToDevice));
+  // pass lists (Sec. 2.3 order: x, y, z forward; z, y, x inverse)
+  auto front = [&](ExecList<T> &ex, const Prob<T> &Q) {
+    ex.add(Q, PK_XFWD, 0);
+    if (d.dim == 3) {
+      ex.add(Q, PK_YFWD, 0, (int)ex.passes.size() - 1);
+      ex.add(Q, PK_ZSTAGE, 0, (int)ex.passes.size() - 1);
+      ex.add(Q, PK_YINV, 0, (int)ex.passes.size() - 1);
+    } else {
+      ex.add(Q, PK_YSTAGE2, 0, (int)ex.passes.size() - 1);
+    }
+  };
+  auto back = [&](ExecList<T> &ex, const Prob<T> &Q, int dep) {
+    ex.add(Q, PK_XINV, 0, dep);
+    if (Q.fill_count) ex.add(Q, PK_FILL, 0);
+  };
+  front(ex_front, P);
+  back(ex_back, P, -1);
+  front(ex_all, P);
+  back(ex_all, P, (int)ex_all.passes.size() - 1);
+  {
+    ExecList<T> &ex = ex_adj;
+    front(ex, PA);
+    back(ex, PA, (int)ex.passes.size() - 1);
+    for (auto &ps : ex.passes) ps.prob = 0;  // d_probs + 1 is passed for the adjoint
+  }
+  SF_TRY(ex_front.upload(mem));
+  SF_TRY(ex_back.upload(mem));
+  SF_TRY(ex_all.upload(mem));
+  SF_TRY(ex_adj.upload(mem));
+  launches_per_exec = fused() ? 1 : (int)ex_all.passes.size();
+  return SF_OK;
+}
+
+// Green's table (Sec. 2.6.2): G tabulated on the octant of the doubled grid in
+// FP64, transformed by a 3D (2D) DCT-I -- the DFT of the mirrored table -- with
+// the FP64 kernels, scaled by -rhs_scale h^d / prod(L) and rounded to T.
+template <typename T> sf_status PlanImpl<T>::build_green() {
+  const int dim = d.dim;
+  const int nx = d.n[0], ny = d.n[1], nz = dim == 3 ? d.n[2] : 0;
+  double h[3] = {0, 0, 0};
+  double hd = 1.0, prodL = 1.0;
+  for (int a = 0; a < dim; ++a) {
+    h[a] = (d.hi[a] - d.lo[a]) / d.n[a];
+    hd *= h[a];
+    prodL *= 2.0 * d.n[a];
+  }
+  const size_t cnt = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+  DevMem<double> tmem;
+  void *oct, *A, *I1, *out;
+  SF_TRY(tmem.alloc(&oct, cnt * sizeof(double)));
+  SF_TRY(tmem.alloc(&A, cnt * sizeof(double)));
+  SF_TRY(tmem.alloc(&I1, cnt * sizeof(double)));
+  SF_TRY(tmem.alloc(&out, cnt * sizeof(double)));
+  sfg::k_green_octant<<<1024, 256, 0, stream>>>((double *)oct, nx, ny, nz, h[0], h[1], h[2], d.green_sigma, dim);
+  SF_CK(cudaGetLastError());
+  // FP64 real-path problem: regular-Neumann (DCT-I) on every axis, forward only
+  Prob<double> G{};
+  G.dim = dim;
+  G.ncomp = 1;
+  G.nin = 1;
+  G.nout = 1;
+  G.cpath = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      AxisHost ah = build_axis(AK_NR, d.n[a], 0.0, 1.0, SF_EIG_PS, a == 0, false);
+      SF_TRY(fill_axis<double>(G.ax[a], ah, tmem));
+    } else {
+      G.ax[a] = Axis<double>{};
+      G.ax[a].kind = AK_P;
+      G.ax[a].n = G.ax[a].nodes = G.ax[a].nu = G.ax[a].L = G.ax[a].ns = 1;
+    }
+  }
+  derive_extents<double>(G);
+  G.A = A;
+  G.I1 = dim == 3 ? I1 : out;
+  G.fwd_out = (double *)out;
+  void *dprob;
+  SF_TRY(tmem.alloc(&dprob, sizeof(Prob<double>)));
+  SF_CK(cudaMemcpy(dprob, &G, sizeof(Prob<double>), cudaMemcpyHostToDevice));
+  ExecList<double> ex;
+  ex.add(G, PK_XFWD, 0);
+  ex.add(G, PK_YFWD, 0, 0);
+  if (dim == 3) ex.add(G, PK_ZFWD, 0, 1);
+  SF_TRY(ex.upload(tmem));
+  IOArgs<double> io{};
+  io.use = 1;
+  io.in[0] = (const double *)oct;
+  SF_TRY(launch_list<double>(ex, (const Prob<double> *)dprob, false, stream, nullptr, nullptr, io, nullptr));
+  void *gh;
+  SF_TRY(mem.alloc(&gh, cnt * sizeof(T)));
+  const double scale = -d.rhs_scale * hd / prodL;
+  sfg::k_convert_scale<T><<<1024, 256, 0, stream>>>((T *)gh, (const double *)out, cnt, scale);
+  SF_CK(cudaGetLastError());
+  SF_CK(cudaStreamSynchronize(stream));
+  P.ghat = (const T *)gh;
+  return SF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batch
+// ---------------------------------------------------------------------------
+template <typename T> struct BatchImpl : sf_plan_s {
+  DevMem<T> mem;
+  std::vector<PlanImpl<T> *> plans;
+  std::vector<Prob<T>> probs;
+  Prob<T> *d_probs = nullptr;
+  ExecList<T> ex;
+  ExecCtl *ctl = nullptr;
+  unsigned *sticky = nullptr;
+  std::vector<const void *> last_f;
+  std::vector<void *> last_psi, last_op;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap = nullptr;  // private stream for graph capture (the legacy stream cannot be captured)
+
+  ~BatchImpl() override {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap) cudaStreamDestroy(cap);
+  }
+
+  sf_status init(const sf_plan *ps, int n, cudaStream_t st) {
+    stream = st;
+    is_batch = true;
+    for (int i = 0; i < n; ++i) plans.push_back(static_cast<PlanImpl<T> *>(ps[i]));
+    probs.resize(n);
+    for (int i = 0; i < n; ++i) probs[i] = plans[i]->P;
+    // level-synchronous order: every problem's pass j before any pass j+1, so a
+    // problem's dependency is (almost always) complete when its next pass starts
+    std::vector<std::vector<int>> kinds(n);
+    for (int i = 0; i < n; ++i) {
+      for (auto &p : plans[i]->ex_all.passes) kinds[i].push_back(p.kind);
+    }
+    std::vector<int> last(n, -1);
+    size_t maxlen = 0;
+    for (auto &k : kinds) maxlen = std::max(maxlen, k.size());
+    for (size_t lvl = 0; lvl < maxlen; ++lvl) {
+      for (int i = 0; i < n; ++i) {
+        if (lvl >= kinds[i].size()) continue;
+        const int kind = kinds[i][lvl];
+        const int dep = (kind == PK_FILL) ? -1 : last[i];
+        const size_t before = ex.passes.size();
+        ex.add(probs[i], kind, i, dep);
+        if (ex.passes.size() > before && kind != PK_FILL) last[i] = (int)ex.passes.size() - 1;
+      }
+    }
+    void *tmp;
+    SF_TRY(mem.alloc(&tmp, std::max(1, n) * sizeof(Prob<T>)));
+    d_probs = (Prob<T> *)tmp;
+    SF_TRY(mem.alloc(&tmp, sizeof(ExecCtl)));
+    ctl = (ExecCtl *)tmp;
+    SF_TRY(mem.alloc(&tmp, sizeof(unsigned)));
+    sticky = (unsigned *)tmp;
+    SF_CK(cudaMemset(sticky, 0, sizeof(unsigned)));
+    SF_TRY(ex.upload(mem));
+    last_f.assign(n, nullptr);
+    last_psi.assign(n, nullptr);
+    last_op.assign(n, nullptr);
+    launches_per_exec = 1;
+    return SF_OK;
+  }
+
+  sf_status run(const void *const *f, void *const *psi, void *const *op) {
+    const int n = (int)plans.size();
+    bool changed = !gexec;
+    for (int i = 0; i < n; ++i) {
+      void *o = op ? op[i] : nullptr;
+      if (f[i] != last_f[i] || psi[i] != last_psi[i] || o != last_op[i]) changed = true;
+    }
+    if (changed) {
+      SF_CK(cudaStreamSynchronize(stream));
+      for (int i = 0; i < n; ++i) {
+        Prob<T> &q = probs[i];
+        PlanImpl<T> *pl = plans[i];
+        void *o = op ? op[i] : nullptr;
+        for (int c = 0; c < SF_MAXF; ++c) {
+          q.in_ptr[c] = nullptr;
+          q.out_ptr[c] = nullptr;
+        }
+        for (int c = 0; c < q.ncomp; ++c) {
+          q.in_ptr[c] = (const T *)f[i] + c * pl->field_elems;
+          q.out_ptr[c] = (T *)psi[i] + c * pl->field_elems;
+        }
+        for (int c = 0; c < q.nop; ++c) q.out_ptr[q.ncomp + c] = o ? (T *)o + c * pl->field_elems : nullptr;
+        last_f[i] = f[i];
+        last_psi[i] = psi[i];
+        last_op[i] = o;
+      }
+      SF_CK(cudaMemcpy(d_probs, probs.data(), n * sizeof(Prob<T>), cudaMemcpyHostToDevice));
+      if (!gexec) {
+        // capture memsets + the persistent launch into a graph (Sec. "persistent batched scheduler")
+        cudaGraph_t g;
+        if (!cap) SF_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        SF_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        IOArgs<T> io{};
+        io.use = 0;
+        sf_status s = launch_list<T>(ex, d_probs, true, cap, ctl, sticky, io, nullptr);
+        cudaError_t e = cudaStreamEndCapture(cap, &g);
+        if (s != SF_OK) return s;
+        if (e != cudaSuccess) return fail(SF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(SF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+    }
+    SF_CK(cudaGraphLaunch(gexec, stream));
+    return SF_OK;
+  }
+
+  sf_status solve_part(bool, bool, const void *, void *, void *, int *) override {
+    return fail(SF_ERR_STATE, "use sf_batch_solve on a batch");
+  }
+  sf_status adjoint(const void *, const void *, void *) override { return fail(SF_ERR_STATE, "not available on a batch"); }
+  sf_status sync() override {
+    SF_CK(cudaStreamSynchronize(stream));
+    unsigned s = 0;
+    SF_CK(cudaMemcpy(&s, sticky, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (s) {
+      SF_CK(cudaMemset(sticky, 0, sizeof(unsigned)));
+      return fail(SF_ERR_TIMEOUT, "a scheduler wait exceeded its bound; results are invalid");
+    }
+    return SF_OK;
+  }
+  sf_status query(size_t *, size_t *, size_t *, size_t *) override { return fail(SF_ERR_STATE, "query a member plan"); }
+  sf_status set_face(int, int, const void *) override { return fail(SF_ERR_STATE, "not available on a batch"); }
+  sf_status host_solve(const void *, void *, void *) override { return fail(SF_ERR_STATE, "not available on a batch"); }
+};
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *sf_version(void) { return "sailfish-gb300 0.1"; }
+
+const char *sf_status_string(sf_status s) {
+  switch (s) {
+    case SF_OK: return "SF_OK";
+    case SF_ERR_ARG: return "SF_ERR_ARG";
+    case SF_ERR_UNSUPPORTED: return "SF_ERR_UNSUPPORTED";
+    case SF_ERR_CUDA: return "SF_ERR_CUDA";
+    case SF_ERR_OOM: return "SF_ERR_OOM";
+    case SF_ERR_STATE: return "SF_ERR_STATE";
+    case SF_ERR_TIMEOUT: return "SF_ERR_TIMEOUT";
+  }
+  return "unknown status";
+}
+
+const char *sf_last_error(void) { return g_err.c_str(); }
+
+sf_status sf_plan_create(sf_plan *out, const sf_plan_desc *d, void *cuda_stream) {
+  if (!out || !d) return fail(SF_ERR_ARG, "null argument");
+  *out = nullptr;
+  SF_TRY(validate(*d));
+  sf_plan_s *p = nullptr;
+  sf_status s;
+  try {
+    if (d->prec == SF_F32) {
+      auto *q = new PlanImpl<float>();
+      p = q;
+      s = q->init(*d, (cudaStream_t)cuda_stream);
+    } else {
+      auto *q = new PlanImpl<double>();
+      p = q;
+      s = q->init(*d, (cudaStream_t)cuda_stream);
+    }
+  } catch (const std::exception &e) {
+    delete p;
+    return fail(SF_ERR_OOM, std::string("host exception: ") + e.what());
+  }
+  if (s != SF_OK) {
+    delete p;
+    return s;
+  }
+  *out = p;
+  return SF_OK;
+}
+
+sf_status sf_plan_set_stream(sf_plan p, void *cuda_stream) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  p->stream = (cudaStream_t)cuda_stream;
+  return SF_OK;
+}
+
+sf_status sf_plan_query(sf_plan p, size_t in_shape[4], size_t out_shape[4], size_t op_shape[4], size_t *ws) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  return p->query(in_shape, out_shape, op_shape, ws);
+}
+
+sf_status sf_set_source(sf_plan p, const void *dev_f) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  if (p->is_batch) return fail(SF_ERR_STATE, "not available on a batch");
+  p->src = dev_f;
+  return SF_OK;
+}
+
+sf_status sf_set_boundary(sf_plan p, int axis, int side, const void *dev_face) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  return p->set_face(axis, side, dev_face);
+}
+
+sf_status sf_solve(sf_plan p) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  if (p->is_batch) return fail(SF_ERR_STATE, "use sf_batch_solve on a batch");
+  if (!p->src) return fail(SF_ERR_STATE, "no source set");
+  SF_TRY(p->solve_part(true, false, p->src, nullptr, nullptr, nullptr));
+  p->solved = true;
+  return SF_OK;
+}
+
+sf_status sf_get_output(sf_plan p, void *dev_psi, void *dev_op_out) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  if (p->is_batch) return fail(SF_ERR_STATE, "use sf_batch_solve on a batch");
+  if (!p->solved) return fail(SF_ERR_STATE, "sf_get_output before sf_solve");
+  if (!dev_psi) return fail(SF_ERR_ARG, "null psi");
+  if (p->d.op != SF_OP_NONE && !dev_op_out) return fail(SF_ERR_ARG, "plan has an operator: op output needed");
+  return p->solve_part(false, true, p->src, dev_psi, dev_op_out, nullptr);
+}
+
+sf_status sf_execute(sf_plan p, const void *dev_f, void *dev_psi, void *dev_op_out) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  if (p->is_batch) return fail(SF_ERR_STATE, "use sf_batch_solve on a batch");
+  if (!dev_f || !dev_psi) return fail(SF_ERR_ARG, "null buffer");
+  if (p->d.op != SF_OP_NONE && !dev_op_out) return fail(SF_ERR_ARG, "plan has an operator: op output needed");
+  p->src = dev_f;
+  SF_TRY(p->solve_part(true, true, dev_f, dev_psi, dev_op_out, nullptr));
+  p->solved = true;
+  return SF_OK;
+}
+
+sf_status sf_solve_host(sf_plan p, const void *host_f, void *host_psi, void *host_op_out) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  if (!host_f || !host_psi) return fail(SF_ERR_ARG, "null buffer");
+  if (p->d.op != SF_OP_NONE && !host_op_out) return fail(SF_ERR_ARG, "plan has an operator: op output needed");
+  return p->host_solve(host_f, host_psi, host_op_out);
+}
+
+sf_status sf_solve_adjoint(sf_plan p, const void *g_psi, const void *g_op, void *g_f) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  if (!g_f) return fail(SF_ERR_ARG, "null output");
+  return p->adjoint(g_psi, g_op, g_f);
+}
+
+sf_status sf_batch_create(sf_plan *batch, const sf_plan *plans, int n, void *cuda_stream) {
+  if (!batch || !plans || n < 1) return fail(SF_ERR_ARG, "bad batch arguments");
+  *batch = nullptr;
+  const int prec = plans[0] ? plans[0]->d.prec : -1;
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || plans[i]->is_batch) return fail(SF_ERR_ARG, "batch members must be plans");
+    if (plans[i]->d.prec != prec) return fail(SF_ERR_UNSUPPORTED, "batch members must share the precision");
+  }
+  sf_plan_s *b = nullptr;
+  sf_status s;
+  if (prec == SF_F32) {
+    auto *q = new BatchImpl<float>();
+    b = q;
+    s = q->init(plans, n, (cudaStream_t)cuda_stream);
+  } else {
+    auto *q = new BatchImpl<double>();
+    b = q;
+    s = q->init(plans, n, (cudaStream_t)cuda_stream);
+  }
+  if (s != SF_OK) {
+    delete b;
+    return s;
+  }
+  b->d = plans[0]->d;
+  *batch = b;
+  return SF_OK;
+}
+
+sf_status sf_batch_solve(sf_plan batch, const void *const *f, void *const *psi, void *const *op) {
+  if (!batch || !batch->is_batch) return fail(SF_ERR_ARG, "not a batch");
+  if (!f || !psi) return fail(SF_ERR_ARG, "null buffer table");
+  if (batch->d.prec == SF_F32) return static_cast<BatchImpl<float> *>(batch)->run(f, psi, op);
+  return static_cast<BatchImpl<double> *>(batch)->run(f, psi, op);
+}
+
+sf_status sf_sync(sf_plan p) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  return p->sync();
+}
+
+int sf_plan_launches(sf_plan p) { return p ? p->launches_per_exec : 0; }
+
+sf_status sf_plan_destroy(sf_plan p) {
+  if (!p) return SF_OK;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  else cudaDeviceSynchronize();
+  delete p;
+  return SF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,199 @@
+// sf_kernels.cuh -- kernels of the solver: one-pass launches, the persistent
+// work-list executor, and the FP64 set-up kernels for the Green's table.
+#pragma once
+
+#include "sf_tiles.cuh"
+
+namespace sfg {
+
+#define SF_THREADS 256
+
+// Per-launch pointers: user buffers are kernel arguments so that every launch
+// (and every captured graph node) carries its own copy.
+template <typename T> struct IOArgs {
+  int use;
+  int has_face;
+  const T *in[SF_MAXF];
+  T *out[SF_MAXF];
+  const T *face[3][2];
+};
+
+template <typename T>
+__device__ __forceinline__ void load_prob(Prob<T> &dst, const Prob<T> *src, const IOArgs<T> &io) {
+  // cooperative copy of the (read-only) problem description into shared memory
+  const int nwords = sizeof(Prob<T>) / 4;
+  const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+  uint32_t *d = reinterpret_cast<uint32_t *>(&dst);
+  for (int i = threadIdx.x; i < nwords; i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+  if (threadIdx.x == 0 && io.use) {
+    for (int i = 0; i < SF_MAXF; ++i) {
+      dst.in_ptr[i] = io.in[i];
+      dst.out_ptr[i] = io.out[i];
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int s2 = 0; s2 < 2; ++s2) dst.face[a][s2] = io.face[a][s2];
+    dst.has_face = io.has_face;
+  }
+  __syncthreads();
+}
+
+// one launch = one pass; blockIdx.x is the tile
+template <typename T>
+__global__ void __launch_bounds__(SF_THREADS) k_pass(const Prob<T> *probs, const Pass<T> *passes, int pass_idx, IOArgs<T> io) {
+  extern __shared__ __align__(16) unsigned char sf_smem[];
+  __shared__ __align__(16) Prob<T> sP;
+  __shared__ Pass<T> sPass;
+  if (threadIdx.x == 0) sPass = passes[pass_idx];
+  __syncthreads();
+  load_prob<T>(sP, probs + sPass.prob, io);
+  run_tile<T>(sP, sPass, blockIdx.x, reinterpret_cast<cx<T> *>(sf_smem), (size_t)sPass.bufsz);
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Persistent executor: CTAs pull work items (pass, tile) from a queue in list
+// order; an item waits (bounded in time and iterations) until the passes it
+// depends on have completed the required number of tiles.  Dependencies only
+// point to earlier items, which are held by running CTAs, so progress never
+// depends on CTA residency.  A wait that gives up records SF_ERR_TIMEOUT and
+// the item is skipped (its counter still advances so nothing else hangs).
+template <typename T>
+__global__ void __launch_bounds__(SF_THREADS)
+    k_exec(const Prob<T> *probs, const Pass<T> *passes, const int *pass_start, int npass, unsigned *done, ExecCtl *ctl,
+           unsigned *sticky, unsigned long long timeout_ns, IOArgs<T> io) {
+  extern __shared__ __align__(16) unsigned char sf_smem[];
+  __shared__ __align__(16) Prob<T> sP;
+  __shared__ Pass<T> sPass;
+  __shared__ int s_item, s_pass, s_ok, s_prob;
+  const int total = pass_start[npass];
+  if (threadIdx.x == 0) s_prob = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int it = (int)atomicAdd(&ctl->next, 1u);
+      s_item = it;
+      s_ok = 1;
+      if (it < total) {
+        int lo = 0, hi = npass - 1;  // last pass with start <= it
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (pass_start[mid] <= it) lo = mid;
+          else hi = mid - 1;
+        }
+        s_pass = lo;
+        sPass = passes[lo];
+        for (int d = 0; d < 2; ++d) {
+          const int dp = sPass.dep[d];
+          if (dp < 0) continue;
+          const unsigned need = (unsigned)sPass.depcnt[d];
+          const unsigned long long t0 = global_ns();
+          unsigned iters = 0;
+          while (ld_acquire(&done[dp]) < need) {
+            __nanosleep(128);
+            if (((++iters) & 255u) == 0 && (global_ns() - t0 > timeout_ns || iters > (1u << 28))) {
+              atomicCAS(&ctl->error, 0u, 6u);
+              atomicExch(&ctl->err_pass, (unsigned)lo);
+              atomicOr(sticky, 1u);
+              s_ok = 0;
+              break;
+            }
+          }
+          if (!s_ok) break;
+        }
+      }
+    }
+    __syncthreads();
+    const int it = s_item;
+    if (it >= total) break;
+    if (sPass.prob != s_prob) {
+      load_prob<T>(sP, probs + sPass.prob, io);
+      if (threadIdx.x == 0) s_prob = sPass.prob;
+    }
+    if (s_ok) run_tile<T>(sP, sPass, it - pass_start[s_pass], reinterpret_cast<cx<T> *>(sf_smem), (size_t)sPass.bufsz);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&done[s_pass], 1u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 set-up: Green's function octant and its conversion
+// ---------------------------------------------------------------------------
+// Exponential integral E1(x), x > 0, written from Abramowitz & Stegun:
+//   x <= 1:  series 5.1.11, E1 = -gamma - ln x - sum_{k>=1} (-x)^k / (k k!)
+//   x >  1:  continued fraction 5.1.22 in its even form
+//            E1 = e^-x / (x + 1 - 1/(x + 3 - 4/(x + 5 - 9/(x + 7 - ...)))),
+//            evaluated with the modified Lentz method.
+__device__ inline double sf_expint_e1(double x) {
+  const double euler = 0.57721566490153286060651209008240243;
+  if (x <= 0.0) return 0.0;
+  if (x > 700.0) return 0.0;
+  if (x <= 1.0) {
+    double sum = 0.0, term = 1.0;
+    for (int k = 1; k < 60; ++k) {
+      term *= -x / k;  // (-x)^k / k!
+      const double add = term / k;
+      sum += add;
+      if (fabs(add) < 1e-18 * fabs(sum)) break;
+    }
+    return -euler - log(x) - sum;
+  }
+  const double tiny = 1e-300;
+  double b = x + 1.0;
+  double c = 1.0 / tiny;
+  double d = 1.0 / b;
+  double h = d;
+  for (int i = 1; i < 500; ++i) {
+    const double an = -(double)i * (double)i;
+    b += 2.0;
+    d = 1.0 / (an * d + b);
+    c = b + an / c;
+    const double del = c * d;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-16) break;
+  }
+  return h * exp(-x);
+}
+
+// G octant [z][y][x] for offsets 0..n per axis (2D: nz = 0)
+__global__ void k_green_octant(double *out, int nx, int ny, int nz, double hx, double hy, double hz, double sigma,
+                               int dim) {
+  const size_t total = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+  const double pi = 3.14159265358979323846264338327950288;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % (nx + 1));
+    const size_t r1 = i / (nx + 1);
+    const int y = (int)(r1 % (ny + 1));
+    const int z = (int)(r1 / (ny + 1));
+    const double dx = x * hx, dy = y * hy, dz = z * hz;
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    double g;
+    if (dim == 3) {
+      if (r == 0.0) g = sqrt(2.0) / (4.0 * pi * sqrt(pi) * sigma);
+      else g = erf(r / (sigma * sqrt(2.0))) / (4.0 * pi * r);
+    } else {
+      const double euler = 0.57721566490153286060651209008240243;
+      if (r == 0.0) g = (0.5 * euler - log(sqrt(2.0) * sigma)) / (2.0 * pi);
+      else g = -(log(r) + 0.5 * sf_expint_e1(r * r / (2.0 * sigma * sigma))) / (2.0 * pi);
+    }
+    out[i] = g;
+  }
+}
+
+template <typename T> __global__ void k_convert_scale(T *out, const double *in, size_t n, double scale) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (T)(in[i] * scale);
+}
+
+}  // namespace sfg

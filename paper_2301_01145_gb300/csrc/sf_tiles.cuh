@@ -1,0 +1,765 @@
+// sf_tiles.cuh -- the passes of the solve, one tile at a time.
+//
+// Data flow of a 3D solve (Sec. 2.3 pencil order x -> y -> z, inverse z -> y -> x):
+//   source [c][z][y][x] --XFWD--> A [c][kx][z][y]        (x transform, transposed store)
+//   A  --YFWD-->  I1 [c][kx][z][ky]                        (y transform of contiguous rows)
+//   I1 --ZSTAGE-> I2 [f][kx][z][ky]                        (z transform, multiply by the
+//                                                           eigenvalues / Green's table,
+//                                                           operator, inverse z)
+//   I2 --YINV-->  B  [f][kx][z][y]                         (inverse y)
+//   B  --XINV-->  result [f][z][y][x]                      (inverse x, extraction, fill)
+// 2D: XFWD -> YSTAGE2 (y transform, multiply, operator, inverse y) -> XINV.
+// Complex spectra (periodic / unbounded axes) store float2/double2; real
+// spectra (Dirichlet / Neumann) store the real DST/DCT coefficients.
+#pragma once
+
+#include "sf_device.cuh"
+
+namespace sfg {
+
+__host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// lines per tile along the row / column passes
+__host__ __device__ inline int lines_per_tile(int cpath, int W) { return cpath ? W : 2 * W; }
+
+// ---------------------------------------------------------------------------
+// generic helpers working on one shared buffer of W interleaved lines
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ void zero_buf(cx<T> *a, int n) {
+  for (int e = threadIdx.x; e < n; e += blockDim.x) a[e] = czero<cx<T>>();
+}
+
+// Place data point q of source line j at its extension position(s).
+// Complex lines (periodic/unbounded) occupy a whole packed line; real lines
+// are packed two per complex line (even j -> real part, odd j -> imaginary).
+template <typename T> __device__ __forceinline__ void put_ext_c(cx<T> *a, const Axis<T> &ax, int Wp, int j, int q, cx<T> v) {
+  a[q * Wp + j] = v;  // periodic / unbounded: position q, zero padding already in place
+}
+template <typename T> __device__ __forceinline__ void put_ext_r(cx<T> *a, const Axis<T> &ax, int Wp, int j, int q, T v) {
+  T *af = reinterpret_cast<T *>(a);
+  const int l = j >> 1, part = j & 1;
+  const int m = ext_pos(ax.kind, ax.n, q);
+  af[2 * (m * Wp + l) + part] = v;
+  int sg;
+  const int mm = ext_mirror(ax.kind, ax.n, q, sg);
+  if (mm >= 0) af[2 * (mm * Wp + l) + part] = sg > 0 ? v : -v;
+}
+// value of data point q of line j after an inverse transform
+template <typename T> __device__ __forceinline__ T get_ext_r(const cx<T> *a, const Axis<T> &ax, int Wp, int j, int q) {
+  const cx<T> v = a[ext_pos(ax.kind, ax.n, q) * Wp + (j >> 1)];
+  return (j & 1) ? v.y : v.x;
+}
+
+// Real coefficient ci of real line j (packed in line j/2) from the forward FFT
+// output: Hermitian split, then division by the kind's phase.
+template <typename T> __device__ __forceinline__ T coef_r(const cx<T> *a, const Axis<T> &ax, int Wp, int j, int ci) {
+  typedef cx<T> V;
+  const int k = ci + ax.k0;
+  const int L = ax.L;
+  const int l = j >> 1;
+  const V zk = a[k * Wp + l];
+  const V zm = a[((L - k) % L) * Wp + l];
+  V e;
+  if (j & 1) {  // E_b = (Zk - conj Zm) / (2i)
+    e = mk<V>((zk.y + zm.y) * (T)0.5, -(zk.x - zm.x) * (T)0.5);
+  } else {  // E_a = (Zk + conj Zm) / 2
+    e = mk<V>((zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5);
+  }
+  const V ph = ax.phase[k];
+  return e.x * ph.x + e.y * ph.y;  // Re(e * conj(ph))
+}
+
+// Build the packed spectrum Z of lines (2l, 2l+1) from real coefficients:
+// E_k = phase_k * c_{k-k0}, Z_k = Ea + i Eb, Z_{L-k} = conj(Ea) + i conj(Eb).
+// cget(j, ci) returns the coefficient of real line j (0 if absent).
+template <typename T, typename CGet>
+__device__ __forceinline__ void build_spec_r(cx<T> *a, const Axis<T> &ax, int Wp, int W, CGet cget) {
+  typedef cx<T> V;
+  const int n = ax.n, L = ax.L;
+  const int cnt = W * (n + 1);
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int l = e % W;
+    const int k = e / W;
+    const int ci = k - ax.k0;
+    V ea = czero<V>(), eb = czero<V>();
+    if (ci >= 0 && ci < ax.ns) {
+      const V ph = ax.phase[k];
+      const T ca = cget(2 * l, ci), cb = cget(2 * l + 1, ci);
+      ea = cscale(ph, ca);
+      eb = cscale(ph, cb);
+    }
+    a[k * Wp + l] = mk<V>(ea.x - eb.y, ea.y + eb.x);
+    if (k >= 1 && k <= n - 1) a[(L - k) * Wp + l] = mk<V>(ea.x + eb.y, eb.x - ea.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// multiplier and operators
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T multiplier(const Prob<T> &P, int kx, int ky, int kz) {
+  if (P.green) {
+    int kyf = ky, kzf = kz;
+    if (P.ax[1].kind == AK_U) kyf = min(ky, P.ax[1].L - ky);
+    if (P.dim == 3) {
+      if (P.ax[2].kind == AK_U) kzf = min(kz, P.ax[2].L - kz);
+      return __ldg(&P.ghat[((size_t)kx * P.gnz + kzf) * P.gny + kyf]);
+    }
+    return __ldg(&P.ghat[(size_t)kx * P.gny + kyf]);
+  }
+  T lam = __ldg(&P.ax[0].lam[kx]) + __ldg(&P.ax[1].lam[ky]);
+  if (P.dim == 3) lam += __ldg(&P.ax[2].lam[kz]);
+  return lam == (T)0 ? (T)0 : P.mscale / lam;
+}
+
+// wavenumbers (Nyquist zeroed) and squared wavenumbers (Nyquist kept)
+template <typename T> struct Kap {
+  T x, y, z, k2;
+};
+template <typename T> __device__ __forceinline__ Kap<T> kappa(const Prob<T> &P, int kx, int ky, int kz) {
+  Kap<T> k;
+  k.x = __ldg(&P.ax[0].kap[kx]);
+  k.y = __ldg(&P.ax[1].kap[ky]);
+  k.k2 = __ldg(&P.ax[0].kap2[kx]) + __ldg(&P.ax[1].kap2[ky]);
+  if (P.dim == 3) {
+    k.z = __ldg(&P.ax[2].kap[kz]);
+    k.k2 += __ldg(&P.ax[2].kap2[kz]);
+  } else {
+    k.z = 0;
+  }
+  return k;
+}
+
+// operator output o from the spectra psi[c] (complex path, forward)
+template <typename T> __device__ __forceinline__ cx<T> op_forward(int op, int dim, int o, const Kap<T> &k, const cx<T> *ps) {
+  typedef cx<T> V;
+  switch (op) {
+    case OPK_GRAD: {
+      const T kk = o == 0 ? k.x : (o == 1 ? k.y : k.z);
+      return mul_i(cscale(ps[0], kk));
+    }
+    case OPK_DIV: {
+      V s = cadd(cscale(ps[0], k.x), cscale(ps[1], k.y));
+      if (dim == 3) s = cadd(s, cscale(ps[2], k.z));
+      return mul_i(s);
+    }
+    case OPK_CURL: {
+      if (dim == 3) {
+        if (o == 0) return mul_i(csub(cscale(ps[2], k.y), cscale(ps[1], k.z)));
+        if (o == 1) return mul_i(csub(cscale(ps[0], k.z), cscale(ps[2], k.x)));
+        return mul_i(csub(cscale(ps[1], k.x), cscale(ps[0], k.y)));
+      }
+      if (o == 0) return mul_i(cscale(ps[0], k.y));
+      return mul_i(cscale(ps[0], -k.x));
+    }
+    case OPK_NABLA: return cscale(ps[o], -k.k2);
+    default: return czero<V>();
+  }
+}
+
+// adjoint: contribution of the gradient g of operator output o to component c
+// (the per-mode conjugate transpose of op_forward)
+template <typename T> __device__ __forceinline__ cx<T> op_adjoint(int op, int dim, int o, int c, const Kap<T> &k, cx<T> g) {
+  typedef cx<T> V;
+  switch (op) {
+    case OPK_GRAD: {  // conj(i k_o) = -i k_o, onto component 0
+      const T kk = o == 0 ? k.x : (o == 1 ? k.y : k.z);
+      return c == 0 ? mul_i(cscale(g, -kk)) : czero<V>();
+    }
+    case OPK_DIV: {  // onto component c: -i k_c g
+      const T kk = c == 0 ? k.x : (c == 1 ? k.y : k.z);
+      return mul_i(cscale(g, -kk));
+    }
+    case OPK_CURL: {
+      if (dim == 3) {  // curl is self-adjoint: rows of i[k]x transposed and conjugated
+        if (o == 0) return c == 1 ? mul_i(cscale(g, k.z)) : (c == 2 ? mul_i(cscale(g, -k.y)) : czero<V>());
+        if (o == 1) return c == 0 ? mul_i(cscale(g, -k.z)) : (c == 2 ? mul_i(cscale(g, k.x)) : czero<V>());
+        return c == 0 ? mul_i(cscale(g, k.y)) : (c == 1 ? mul_i(cscale(g, -k.x)) : czero<V>());
+      }
+      // 2D: u0 = i ky psi, u1 = -i kx psi
+      return o == 0 ? mul_i(cscale(g, -k.y)) : mul_i(cscale(g, k.x));
+    }
+    case OPK_NABLA: return c == o ? cscale(g, -k.k2) : czero<V>();
+    default: return czero<V>();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// XFWD: x transform of source lines, transposed store into A[c][kx][z][y]
+// ---------------------------------------------------------------------------
+template <typename T> __device__ void tile_xfwd(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
+  typedef cx<T> V;
+  const Axis<T> &X = P.ax[0], &Y = P.ax[1], &Z = P.ax[2];
+  const int W = ps.W, Wp = ps.Wp, L = X.L;
+  const int RL = 2 * W;  // real lines per tile
+  const int nuy = P.nuy, nuz = P.nuz, nux = X.nu;
+  const int ty = cdiv(nuy, RL);
+  const int iy = t % ty;
+  const int rest = t / ty;
+  const int qz = rest % nuz;
+  const int c = rest / nuz;
+  const int qy0 = iy * RL;
+  V *a = sm, *b = sm + bufsz;
+  zero_buf<T>(a, L * Wp);
+  __syncthreads();
+  const T *src = P.in_ptr[c];
+  const int zn = P.dim == 3 ? qz + Z.u0 : 0;
+  const int ndx = X.nodes, ndy = Y.nodes;
+  if (src) {
+    const int cnt = RL * nux;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int r = e / nux;
+      const int q = e - r * nux;
+      const int qy = qy0 + r;
+      if (qy >= nuy) continue;
+      const int yn = qy + Y.u0, xn = q + X.u0;
+      T v = src[((size_t)zn * ndy + yn) * ndx + xn];
+      if (P.has_face) {  // FD2 boundary lifting (weights include 1/rhs_scale)
+        if (q == 0 && P.face[0][0]) v += P.facew[0][0] * P.face[0][0][(size_t)zn * ndy + yn];
+        if (q == nux - 1 && P.face[0][1]) v += P.facew[0][1] * P.face[0][1][(size_t)zn * ndy + yn];
+        if (qy == 0 && P.face[1][0]) v += P.facew[1][0] * P.face[1][0][(size_t)zn * ndx + xn];
+        if (qy == nuy - 1 && P.face[1][1]) v += P.facew[1][1] * P.face[1][1][(size_t)zn * ndx + xn];
+        if (P.dim == 3) {
+          if (qz == 0 && P.face[2][0]) v += P.facew[2][0] * P.face[2][0][(size_t)yn * ndx + xn];
+          if (qz == nuz - 1 && P.face[2][1]) v += P.facew[2][1] * P.face[2][1][(size_t)yn * ndx + xn];
+        }
+      }
+      if (P.nrw) {  // adjoint end-point weights of regular-Neumann axes
+        if (X.kind == AK_NR && (q == 0 || q == nux - 1)) v *= (T)2;
+        if (Y.kind == AK_NR && (qy == 0 || qy == nuy - 1)) v *= (T)2;
+        if (P.dim == 3 && Z.kind == AK_NR && (qz == 0 || qz == nuz - 1)) v *= (T)2;
+      }
+      put_ext_r<T>(a, X, Wp, r, q, v);
+    }
+  }
+  __syncthreads();
+  fft_lines<T, false>(a, b, X, W, Wp);
+  const size_t plane = (size_t)nuz * nuy;
+  if (P.cpath) {
+    V *out = reinterpret_cast<V *>(P.A);
+    const int nk = P.nsx;  // L/2 + 1
+    const int cnt = RL * nk;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int r = e % RL;
+      const int kx = e / RL;
+      const int qy = qy0 + r;
+      if (qy >= nuy) continue;
+      const int l = r >> 1;
+      const V zk = a[kx * Wp + l];
+      const V zm = a[((L - kx) % L) * Wp + l];
+      V v;
+      if (r & 1) v = mk<V>((zk.y + zm.y) * (T)0.5, -(zk.x - zm.x) * (T)0.5);
+      else v = mk<V>((zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5);
+      out[((size_t)c * nk + kx) * plane + (size_t)qz * nuy + qy] = v;
+    }
+  } else {
+    T *out = reinterpret_cast<T *>(P.A);
+    const int nk = P.nsx;
+    const int cnt = RL * nk;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int r = e % RL;
+      const int kx = e / RL;
+      const int qy = qy0 + r;
+      if (qy >= nuy) continue;
+      out[((size_t)c * nk + kx) * plane + (size_t)qz * nuy + qy] = coef_r<T>(a, X, Wp, r, kx);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// YFWD (3D): rows of A along y -> I1;  ZFWD-style forward-only store for set-up
+// ---------------------------------------------------------------------------
+template <typename T> __device__ void tile_yfwd(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
+  typedef cx<T> V;
+  const Axis<T> &Y = P.ax[1];
+  const int W = ps.W, Wp = ps.Wp, L = Y.L;
+  const int RPT = lines_per_tile(P.cpath, W);
+  const int nuy = P.nuy, nuz = P.nuz, nsx = P.nsx, nsy = P.nsy;
+  const int tz = cdiv(nuz, RPT);
+  const int iz = t % tz;
+  const int rest = t / tz;
+  const int kx = rest % nsx;
+  const int c = rest / nsx;
+  const int qz0 = iz * RPT;
+  const int nl = min(RPT, nuz - qz0);
+  V *a = sm, *b = sm + bufsz;
+  zero_buf<T>(a, L * Wp);
+  __syncthreads();
+  const size_t rowbase = ((size_t)c * nsx + kx) * nuz + qz0;  // in rows
+  if (P.cpath) {
+    const V *in = reinterpret_cast<const V *>(P.A) + rowbase * nuy;
+    const int cnt = nl * nuy;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int j = e / nuy, q = e - j * nuy;
+      put_ext_c<T>(a, Y, Wp, j, q, __ldcg(&in[(size_t)j * nuy + q]));
+    }
+  } else {
+    const T *in = reinterpret_cast<const T *>(P.A) + rowbase * nuy;
+    const int cnt = nl * nuy;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int j = e / nuy, q = e - j * nuy;
+      put_ext_r<T>(a, Y, Wp, j, q, __ldcg(&in[(size_t)j * nuy + q]));
+    }
+  }
+  __syncthreads();
+  fft_lines<T, false>(a, b, Y, W, Wp);
+  if (P.cpath) {
+    V *out = reinterpret_cast<V *>(P.I1) + rowbase * nsy;
+    const int cnt = nl * nsy;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int j = e / nsy, k = e - j * nsy;
+      __stcg(&out[(size_t)j * nsy + k], a[k * Wp + j]);
+    }
+  } else {
+    T *out = reinterpret_cast<T *>(P.I1) + rowbase * nsy;
+    const int cnt = nl * nsy;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int j = e / nsy, k = e - j * nsy;
+      __stcg(&out[(size_t)j * nsy + k], coef_r<T>(a, Y, Wp, j, k));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// YINV (3D): inverse y transform of rows of I2 -> B
+// ---------------------------------------------------------------------------
+template <typename T> __device__ void tile_yinv(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
+  typedef cx<T> V;
+  const Axis<T> &Y = P.ax[1];
+  const int W = ps.W, Wp = ps.Wp, L = Y.L;
+  const int RPT = lines_per_tile(P.cpath, W);
+  const int nuy = P.nuy, nuz = P.nuz, nsx = P.nsx, nsy = P.nsy;
+  const int tz = cdiv(nuz, RPT);
+  const int iz = t % tz;
+  const int rest = t / tz;
+  const int kx = rest % nsx;
+  const int f = rest / nsx;
+  const int qz0 = iz * RPT;
+  const int nl = min(RPT, nuz - qz0);
+  V *a = sm, *b = sm + bufsz;
+  const size_t rowbase = ((size_t)f * nsx + kx) * nuz + qz0;
+  if (P.cpath) {
+    const V *in = reinterpret_cast<const V *>(P.I2) + rowbase * nsy;
+    const int cnt = W * L;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int j = e / L, k = e - j * L;
+      a[k * Wp + j] = j < nl ? __ldcg(&in[(size_t)j * nsy + k]) : czero<V>();
+    }
+  } else {
+    const T *in = reinterpret_cast<const T *>(P.I2) + rowbase * nsy;
+    build_spec_r<T>(a, Y, Wp, W, [&](int j, int ci) -> T { return j < nl ? __ldcg(&in[(size_t)j * nsy + ci]) : (T)0; });
+  }
+  __syncthreads();
+  fft_lines<T, true>(a, b, Y, W, Wp);
+  const int cnt = nl * nuy;
+  if (P.cpath) {
+    V *out = reinterpret_cast<V *>(P.B) + rowbase * nuy;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int j = e / nuy, q = e - j * nuy;
+      __stcg(&out[(size_t)j * nuy + q], a[q * Wp + j]);
+    }
+  } else {
+    T *out = reinterpret_cast<T *>(P.B) + rowbase * nuy;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int j = e / nuy, q = e - j * nuy;
+      __stcg(&out[(size_t)j * nuy + q], get_ext_r<T>(a, Y, Wp, j, q));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// spectral processing shared by the 3D z-stage and the 2D y-stage
+// bufs[0..ncomp) hold the forward spectra of the components; bufs[ncomp] is the
+// operator buffer; *scr the FFT scratch.  kfix(l) gives (kx, ky) of line l and
+// the transform axis provides the third wavenumber from the position.
+// ---------------------------------------------------------------------------
+template <typename T, typename KOf>
+__device__ void stage_multiply_c(const Prob<T> &P, cx<T> **bufs, int nl, int W, int Wp, int L, bool zaxis, KOf kof) {
+  // psi_hat = M * f_hat for every component (complex path)
+  const int cnt = L * W;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int l = e % W, k = e / W;
+    if (l >= nl) continue;
+    int kx, ky, kz;
+    kof(l, k, kx, ky, kz);
+    const T m = multiplier<T>(P, kx, ky, kz);
+    for (int c = 0; c < P.ncomp; ++c) bufs[c][k * Wp + l] = cscale(bufs[c][k * Wp + l], m);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// ZSTAGE (3D) / YSTAGE2 (2D): transform, multiply, operator, inverse
+// ---------------------------------------------------------------------------
+// Geometry of one stage tile: nl lines of the transform axis.
+//   load(c, j, q)  -> data point q of line j of input field c (complex or real)
+//   store(f, j, q, v) writes data point q of line j of output field f
+template <typename T, bool CP, bool LINE_FAST, typename LoadC, typename LoadR, typename StoreC, typename StoreR, typename KOf>
+__device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, int nl, cx<T> *sm, size_t bufsz,
+                          LoadC loadc, LoadR loadr, StoreC storec, StoreR storer, KOf kof) {
+  typedef cx<T> V;
+  const int L = ax.L;
+  const int ncomp = P.ncomp;
+  const bool hasop = P.op != OPK_NONE;
+  V *bufs[SF_MAXF + 2];
+  for (int i = 0; i < ncomp + 1; ++i) bufs[i] = sm + (size_t)i * bufsz;
+  V *scr = sm + (size_t)(ncomp + 1) * bufsz;
+  const int nlu = ax.nu;  // data points per line
+  // ---- load + forward transform of one field into bufs[slot]
+  auto fwd_field = [&](int field, int slot) {
+    V *a = bufs[slot];
+    zero_buf<T>(a, L * Wp);
+    __syncthreads();
+    const int cnt = nl * nlu;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      int j, q;
+      if (LINE_FAST) { j = e % nl; q = e / nl; } else { q = e % nlu; j = e / nlu; }
+      if (CP) put_ext_c<T>(a, ax, Wp, j, q, loadc(field, j, q));
+      else put_ext_r<T>(a, ax, Wp, j, q, loadr(field, j, q));
+    }
+    __syncthreads();
+    fft_lines<T, false>(bufs[slot], scr, ax, W, Wp);
+  };
+  // ---- inverse transform of bufs[slot] and store as output field
+  auto inv_field = [&](int slot, int field) {
+    fft_lines<T, true>(bufs[slot], scr, ax, W, Wp);
+    const V *a = bufs[slot];
+    const int cnt = nl * nlu;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      int j, q;
+      if (LINE_FAST) { j = e % nl; q = e / nl; } else { q = e % nlu; j = e / nlu; }
+      if (CP) storec(field, j, q, a[q * Wp + j]);
+      else storer(field, j, q, get_ext_r<T>(a, ax, Wp, j, q));
+    }
+    __syncthreads();
+  };
+
+  if (CP) {
+    const int Wl = nl;  // complex lines in the tile
+    for (int c = 0; c < ncomp; ++c) fwd_field(c, c);
+    if (P.adjoint && hasop) {
+      for (int o = 0; o < P.nop; ++o) {
+        fwd_field(ncomp + o, ncomp);
+        const int cnt = L * W;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+          const int l = e % W, k = e / W;
+          if (l >= Wl) continue;
+          int kx, ky, kz;
+          kof(l, k, kx, ky, kz);
+          const Kap<T> kk = kappa<T>(P, kx, ky, kz);
+          const V g = bufs[ncomp][k * Wp + l];
+          for (int c = 0; c < ncomp; ++c)
+            bufs[c][k * Wp + l] = cadd(bufs[c][k * Wp + l], op_adjoint<T>(P.op, P.dim, o, c, kk, g));
+        }
+        __syncthreads();
+      }
+    }
+    stage_multiply_c<T>(P, bufs, Wl, W, Wp, L, true, kof);
+    __syncthreads();
+    if (!P.adjoint && hasop) {
+      for (int o = 0; o < P.nop; ++o) {
+        const int cnt = L * W;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+          const int l = e % W, k = e / W;
+          V v = czero<V>();
+          if (l < Wl) {
+            int kx, ky, kz;
+            kof(l, k, kx, ky, kz);
+            const Kap<T> kk = kappa<T>(P, kx, ky, kz);
+            V psv[3];
+            for (int c = 0; c < ncomp && c < 3; ++c) psv[c] = bufs[c][k * Wp + l];
+            v = op_forward<T>(P.op, P.dim, o, kk, psv);
+          }
+          bufs[ncomp][k * Wp + l] = v;
+        }
+        __syncthreads();
+        inv_field(ncomp, ncomp + o);
+      }
+    }
+    for (int c = 0; c < ncomp; ++c) inv_field(c, c);
+  } else {
+    // real path: two real lines per packed line; multiply coefficient-wise
+    const int Wl = cdiv(nl, 2);
+    for (int c = 0; c < ncomp; ++c) {
+      fwd_field(c, c);
+      V *a = bufs[c];
+      const int n = ax.n;
+      const int cnt = Wl * (n + 1);
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int l = e % Wl, k = e / Wl;
+        const int ci = k - ax.k0;
+        const V zk = a[k * Wp + l];
+        const V zm = a[((L - k) % L) * Wp + l];
+        V ea = mk<V>((zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5);
+        V eb = mk<V>((zk.y + zm.y) * (T)0.5, -(zk.x - zm.x) * (T)0.5);
+        T ma = 0, mb = 0;
+        V ph = czero<V>();
+        if (ci >= 0 && ci < ax.ns) {
+          ph = ax.phase[k];
+          int kx, ky, kz;
+          kof(2 * l, ci, kx, ky, kz);
+          ma = multiplier<T>(P, kx, ky, kz);
+          if (2 * l + 1 < nl) {
+            kof(2 * l + 1, ci, kx, ky, kz);
+            mb = multiplier<T>(P, kx, ky, kz);
+          }
+        }
+        const T ca = (ea.x * ph.x + ea.y * ph.y) * ma;
+        const T cb = (eb.x * ph.x + eb.y * ph.y) * mb;
+        ea = cscale(ph, ca);
+        eb = cscale(ph, cb);
+        a[k * Wp + l] = mk<V>(ea.x - eb.y, ea.y + eb.x);
+        if (k >= 1 && k <= n - 1) a[(L - k) * Wp + l] = mk<V>(ea.x + eb.y, eb.x - ea.y);
+      }
+      __syncthreads();
+      inv_field(c, c);
+    }
+  }
+}
+
+template <typename T> __device__ void tile_zstage(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
+  typedef cx<T> V;
+  const Axis<T> &Z = P.ax[2];
+  const int W = ps.W, Wp = ps.Wp;
+  const int CPT = lines_per_tile(P.cpath, W);
+  const int nsx = P.nsx, nsy = P.nsy, nuz = P.nuz;
+  const int ty = cdiv(nsy, CPT);
+  const int iy = t % ty;
+  const int kx = t / ty;
+  const int ky0 = iy * CPT;
+  const int nl = min(CPT, nsy - ky0);
+  const size_t fstride = (size_t)nsx * nuz * nsy;  // elements per field
+  const size_t base = (size_t)kx * nuz * nsy + ky0;
+  auto kof = [&](int l, int k, int &kx_, int &ky_, int &kz_) {
+    kx_ = kx;
+    ky_ = ky0 + l;
+    kz_ = k;
+  };
+  if (P.cpath) {
+    const V *in = reinterpret_cast<const V *>(P.I1);
+    V *out = reinterpret_cast<V *>(P.I2);
+    run_stage<T, true, true>(
+        P, Z, W, Wp, nl, sm, bufsz,
+        [&](int f, int j, int q) -> V { return __ldcg(&in[f * fstride + base + (size_t)q * nsy + j]); },
+        [&](int, int, int) -> T { return (T)0; },
+        [&](int f, int j, int q, V v) { __stcg(&out[f * fstride + base + (size_t)q * nsy + j], v); },
+        [&](int, int, int, T) {}, kof);
+  } else {
+    const T *in = reinterpret_cast<const T *>(P.I1);
+    T *out = reinterpret_cast<T *>(P.I2);
+    run_stage<T, false, true>(
+        P, Z, W, Wp, nl, sm, bufsz, [&](int, int, int) -> V { return czero<V>(); },
+        [&](int f, int j, int q) -> T { return __ldcg(&in[f * fstride + base + (size_t)q * nsy + j]); },
+        [&](int, int, int, V) {},
+        [&](int f, int j, int q, T v) { __stcg(&out[f * fstride + base + (size_t)q * nsy + j], v); }, kof);
+  }
+}
+
+template <typename T> __device__ void tile_ystage2(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
+  typedef cx<T> V;
+  const Axis<T> &Y = P.ax[1];
+  const int W = ps.W, Wp = ps.Wp;
+  const int RPT = lines_per_tile(P.cpath, W);
+  const int nsx = P.nsx, nuy = P.nuy;
+  const int kx0 = t * RPT;
+  const int nl = min(RPT, nsx - kx0);
+  const size_t fstride = (size_t)nsx * nuy;
+  const size_t base = (size_t)kx0 * nuy;
+  auto kof = [&](int l, int k, int &kx_, int &ky_, int &kz_) {
+    kx_ = kx0 + l;
+    ky_ = k;
+    kz_ = 0;
+  };
+  if (P.cpath) {
+    const V *in = reinterpret_cast<const V *>(P.A);
+    V *out = reinterpret_cast<V *>(P.B);
+    run_stage<T, true, false>(
+        P, Y, W, Wp, nl, sm, bufsz,
+        [&](int f, int j, int q) -> V { return __ldcg(&in[f * fstride + base + (size_t)j * nuy + q]); },
+        [&](int, int, int) -> T { return (T)0; },
+        [&](int f, int j, int q, V v) { __stcg(&out[f * fstride + base + (size_t)j * nuy + q], v); },
+        [&](int, int, int, T) {}, kof);
+  } else {
+    const T *in = reinterpret_cast<const T *>(P.A);
+    T *out = reinterpret_cast<T *>(P.B);
+    run_stage<T, false, false>(
+        P, Y, W, Wp, nl, sm, bufsz, [&](int, int, int) -> V { return czero<V>(); },
+        [&](int f, int j, int q) -> T { return __ldcg(&in[f * fstride + base + (size_t)j * nuy + q]); },
+        [&](int, int, int, V) {},
+        [&](int f, int j, int q, T v) { __stcg(&out[f * fstride + base + (size_t)j * nuy + q], v); }, kof);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// ZFWD (set-up): forward z transform of real columns of I1, coefficients to fwd_out
+// ---------------------------------------------------------------------------
+template <typename T> __device__ void tile_zfwd(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
+  typedef cx<T> V;
+  const Axis<T> &Z = P.ax[2];
+  const int W = ps.W, Wp = ps.Wp, L = Z.L;
+  const int CPT = 2 * W;
+  const int nsx = P.nsx, nsy = P.nsy, nuz = P.nuz;
+  const int ty = cdiv(nsy, CPT);
+  const int iy = t % ty;
+  const int kx = t / ty;
+  const int ky0 = iy * CPT;
+  const int nl = min(CPT, nsy - ky0);
+  V *a = sm, *b = sm + bufsz;
+  zero_buf<T>(a, L * Wp);
+  __syncthreads();
+  const T *in = reinterpret_cast<const T *>(P.I1) + (size_t)kx * nuz * nsy + ky0;
+  const int cnt = nl * nuz;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int j = e % nl, q = e / nl;
+    put_ext_r<T>(a, Z, Wp, j, q, __ldcg(&in[(size_t)q * nsy + j]));
+  }
+  __syncthreads();
+  fft_lines<T, false>(a, b, Z, W, Wp);
+  T *out = P.fwd_out + (size_t)kx * Z.ns * nsy + ky0;
+  const int cnt2 = nl * Z.ns;
+  for (int e = threadIdx.x; e < cnt2; e += blockDim.x) {
+    const int j = e % nl, k = e / nl;
+    out[(size_t)k * nsy + j] = coef_r<T>(a, Z, Wp, j, k);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// XINV: inverse x transform of 2W real lines from B (transposed read),
+// extraction and store of the result; Dirichlet x-boundary nodes filled
+// ---------------------------------------------------------------------------
+template <typename T> __device__ void tile_xinv(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
+  typedef cx<T> V;
+  const Axis<T> &X = P.ax[0], &Y = P.ax[1], &Z = P.ax[2];
+  const int W = ps.W, Wp = ps.Wp, L = X.L;
+  const int RL = 2 * W;
+  const int nuy = P.nuy, nuz = P.nuz, nux = X.nu, nsx = P.nsx;
+  const int ty = cdiv(nuy, RL);
+  const int iy = t % ty;
+  const int rest = t / ty;
+  const int qz = rest % nuz;
+  const int f = rest / nuz;
+  const int qy0 = iy * RL;
+  const int nl = min(RL, nuy - qy0);
+  V *a = sm, *stg = sm + bufsz;
+  const size_t plane = (size_t)nuz * nuy;
+  const size_t base = (size_t)f * nsx * plane + (size_t)qz * nuy + qy0;
+  // stage the transposed block [kx][r] through shared memory
+  if (P.cpath) {
+    const V *in = reinterpret_cast<const V *>(P.B);
+    const int cnt = nsx * RL;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int r = e % RL, kx = e / RL;
+      stg[e] = r < nl ? __ldcg(&in[base + (size_t)kx * plane + r]) : czero<V>();
+    }
+    __syncthreads();
+    // Z_k = A_k + i B_k (k <= L/2), Z_{L-k} = conj(A_k) + i conj(B_k); DC and Nyquist real-projected
+    const int half = L / 2;
+    const int cnt2 = W * (half + 1);
+    for (int e = threadIdx.x; e < cnt2; e += blockDim.x) {
+      const int l = e % W, k = e / W;
+      V A = stg[k * RL + 2 * l], Bv = stg[k * RL + 2 * l + 1];
+      if (k == 0 || k == half) {
+        A.y = 0;
+        Bv.y = 0;
+      }
+      a[k * Wp + l] = mk<V>(A.x - Bv.y, A.y + Bv.x);
+      if (k >= 1 && k < half) a[(L - k) * Wp + l] = mk<V>(A.x + Bv.y, Bv.x - A.y);
+    }
+  } else {
+    const T *in = reinterpret_cast<const T *>(P.B);
+    T *stgr = reinterpret_cast<T *>(stg);
+    const int cnt = nsx * RL;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int r = e % RL, kx = e / RL;
+      stgr[e] = r < nl ? __ldcg(&in[base + (size_t)kx * plane + r]) : (T)0;
+    }
+    __syncthreads();
+    build_spec_r<T>(a, X, Wp, W, [&](int j, int ci) -> T { return stgr[ci * RL + j]; });
+  }
+  __syncthreads();
+  V *scr = stg;
+  fft_lines<T, true>(a, scr, X, W, Wp);
+  T *dst = P.out_ptr[f];
+  const int zn = P.dim == 3 ? qz + Z.u0 : 0;
+  const int ndx = X.nodes, ndy = Y.nodes;
+  const bool dr = X.kind == AK_DR;
+  const int nxw = dr ? nux + 2 : nux;  // regular Dirichlet: also write the two boundary nodes
+  const int cnt = nl * nxw;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int r = e / nxw;
+    const int p = e - r * nxw;
+    const int qy = qy0 + r;
+    const int yn = qy + Y.u0;
+    int xn;
+    T v;
+    if (dr && p >= nux) {  // boundary node x = 0 or x = n
+      const int side = p - nux;
+      xn = side == 0 ? 0 : X.n;
+      v = 0;
+      if (!P.adjoint && P.face[0][side]) v = P.face[0][side][(size_t)zn * ndy + yn];
+    } else {
+      xn = p + X.u0;
+      v = get_ext_r<T>(a, X, Wp, r, p);
+      if (P.nrw) {
+        if (X.kind == AK_NR && (p == 0 || p == nux - 1)) v *= (T)0.5;
+        if (Y.kind == AK_NR && (qy == 0 || qy == nuy - 1)) v *= (T)0.5;
+        if (P.dim == 3 && Z.kind == AK_NR && (qz == 0 || qz == nuz - 1)) v *= (T)0.5;
+      }
+    }
+    dst[((size_t)zn * ndy + yn) * ndx + xn] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FILL: regular-Dirichlet boundary planes of y and z (priority z > y > x)
+// ---------------------------------------------------------------------------
+template <typename T> __device__ void tile_fill(const Prob<T> &P, const Pass<T> &ps, int t) {
+  const Axis<T> &X = P.ax[0], &Y = P.ax[1], &Z = P.ax[2];
+  const int ndx = X.nodes, ndy = Y.nodes, ndz = P.dim == 3 ? Z.nodes : 1;
+  const bool ydr = Y.kind == AK_DR, zdr = P.dim == 3 && Z.kind == AK_DR;
+  const int ny_pl = ydr ? 2 * ndz * ndx : 0;
+  const int nz_pl = zdr ? 2 * ndy * ndx : 0;
+  const int per_field = ny_pl + nz_pl;
+  const int total = per_field * P.nout;
+  const int chunk = 4096;
+  const int e0 = t * chunk;
+  for (int e = e0 + threadIdx.x; e < min(total, e0 + chunk); e += blockDim.x) {
+    const int f = e / per_field;
+    int g = e - f * per_field;
+    T *dst = P.out_ptr[f];
+    if (g < ny_pl) {  // y planes
+      const int side = g / (ndz * ndx);
+      g -= side * ndz * ndx;
+      const int zn = g / ndx, xn = g - zn * ndx;
+      if (zdr && (zn == 0 || zn == Z.n)) continue;  // owned by the z planes
+      const int yn = side == 0 ? 0 : Y.n;
+      T v = 0;
+      if (!P.adjoint && P.face[1][side]) v = P.face[1][side][(size_t)zn * ndx + xn];
+      dst[((size_t)zn * ndy + yn) * ndx + xn] = v;
+    } else {
+      g -= ny_pl;
+      const int side = g / (ndy * ndx);
+      g -= side * ndy * ndx;
+      const int yn = g / ndx, xn = g - yn * ndx;
+      const int zn = side == 0 ? 0 : Z.n;
+      T v = 0;
+      if (!P.adjoint && P.face[2][side]) v = P.face[2][side][(size_t)yn * ndx + xn];
+      dst[((size_t)zn * ndy + yn) * ndx + xn] = v;
+    }
+  }
+}
+
+// dispatch one tile of a pass
+template <typename T> __device__ void run_tile(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
+  switch (ps.kind) {
+    case PK_XFWD: tile_xfwd<T>(P, ps, t, sm, bufsz); break;
+    case PK_YFWD: tile_yfwd<T>(P, ps, t, sm, bufsz); break;
+    case PK_ZSTAGE: tile_zstage<T>(P, ps, t, sm, bufsz); break;
+    case PK_YINV: tile_yinv<T>(P, ps, t, sm, bufsz); break;
+    case PK_XINV: tile_xinv<T>(P, ps, t, sm, bufsz); break;
+    case PK_YSTAGE2: tile_ystage2<T>(P, ps, t, sm, bufsz); break;
+    case PK_FILL: tile_fill<T>(P, ps, t); break;
+    case PK_ZFWD: tile_zfwd<T>(P, ps, t, sm, bufsz); break;
+    default: break;
+  }
+}
+
+}  // namespace sfg

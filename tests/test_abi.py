@@ -1,0 +1,95 @@
+"""Host-side checks of the C ABI: the library builds, loads without a GPU and
+exports every entry point declared in include/*.h; the Python binding's
+descriptor layout matches the header; argument errors are reported without
+touching a device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2301_01145_gb300 import _lib
+    return _lib.load()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(sf_[a-z0-9_]+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("sf_plan_create", "sf_set_source", "sf_set_boundary", "sf_solve", "sf_get_output",
+                     "sf_solve_adjoint", "sf_batch_create", "sf_batch_solve", "sf_plan_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol():
+    from paper_2301_01145_gb300 import _lib
+    assert set(declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_descriptor_layout_matches_header():
+    # offsets follow the C layout of sf_plan_desc (int32 and double members)
+    from paper_2301_01145_gb300._lib import sf_plan_desc
+    off = {f: getattr(sf_plan_desc, f).offset for f, _ in sf_plan_desc._fields_}
+    assert off["dim"] == 0 and off["n"] == 4 and off["lo"] == 16 and off["hi"] == 40
+    assert off["bc"] == 64 and off["grid"] == 88 and off["green_sigma"] == 104
+    assert ctypes.sizeof(sf_plan_desc) == 136
+
+
+def test_status_strings_and_version(lib):
+    assert lib.sf_status_string(0) == b"SF_OK"
+    assert lib.sf_status_string(-6) == b"SF_ERR_TIMEOUT"
+    assert lib.sf_version().startswith(b"sailfish-gb300")
+
+
+@pytest.mark.parametrize("mutate,expect", [
+    (dict(dim=4), -1),
+    (dict(ncomp=0), -1),
+    (dict(n=(10, 10, 10)), -2),        # FFT length 20 is not 2^p or 3*2^p
+    (dict(bc=("P", "D", "P")), -2),    # periodic mixed with Dirichlet
+    (dict(bc=(("D", "N"), "D", "D")), -2),  # different faces on one axis
+    (dict(rhs_scale=0.0), -1),
+    (dict(bc="UUU", grid="regular"), -2),
+    (dict(bc="UUU", sigma=0.0), -1),
+    (dict(op="CURL", ncomp=1), -1),
+    (dict(op="GRAD", bc="DDD"), -2),
+])
+def test_descriptor_validation_without_gpu(lib, mutate, expect):
+    from paper_2301_01145_gb300 import _lib
+    args = dict(dim=3, n=(16, 16, 16), lo=(0, 0, 0), hi=(1, 1, 1), bc="PPP", grid="staggered", eig="PS",
+                op="NONE", sigma=0.1, ncomp=1, prec="f32", rhs_scale=1.0)
+    args.update(mutate)
+    bc = args.pop("bc")
+    bc = list(bc) if isinstance(bc, str) else list(bc)
+    d = _lib.make_desc(args.pop("dim"), args.pop("n"), args.pop("lo"), args.pop("hi"), bc, **args)
+    h = ctypes.c_void_p()
+    st = lib.sf_plan_create(ctypes.byref(h), ctypes.byref(d), None)
+    assert st == expect, lib.sf_last_error()
+    assert not h.value
+    assert lib.sf_last_error()
+
+
+def test_null_arguments(lib):
+    assert lib.sf_plan_create(None, None, None) == -1
+    assert lib.sf_solve(None) == -1
+    assert lib.sf_plan_destroy(None) == 0
