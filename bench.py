@@ -1,0 +1,338 @@
+"""Benchmark: 3D unbounded vector Poisson solve (Hockney-Eastwood, G2 kernel) with curl.
+
+Workload: lap(psi) = -omega on a 256^3 cell-centred grid of [-0.5, 0.5]^3,
+3 components, doubled to 512^3 by zero padding, sigma = 2h, outputs psi and
+u = curl(psi) (FP32 bulk arithmetic, FP64-built tables).  omega is a seeded
+Gaussian vortex ring (radius 0.25, core 0.05, random axis).
+
+One step = one full solve (forward transforms, Green's multiply, curl,
+inverse transforms, extraction) through the C ABI on device-resident buffers.
+The metric is grid points per second (256^3 output points per solve).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank solves its own copy (independent replicas,
+no collective in the data path); the reported value is the total over ranks
+divided by the slowest rank's time.  --impl reference times the FP64 CPU
+oracle on a reduced grid of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid points/s per solve (3D unbounded 256^3 vector, FP32 vs FP64) and % HBM roofline"
+UNIT = "grid points/s"
+N = 256
+NCOMP = 3
+HBM_FALLBACK = 6800.0
+
+
+def algorithmic_bytes(n: int, elem: int = 4):
+    """Bytes per solve of the method (see the roofline model of the design notes).
+
+    B_io:     read omega (3 fields), write psi and u (6 fields), read the Green's octant once.
+    B_method: B_io plus one HBM round trip of the half-spectrum after the x
+              transform (3 fields forward, 6 fields inverse): [n+1][n][n] complex each.
+    """
+    field = n ** 3 * elem
+    green = (n + 1) ** 3 * elem
+    b_io = 3 * field + 6 * field + green
+    half = (n + 1) * n * n * 2 * elem
+    b_method = b_io + 2 * 3 * half + 2 * 6 * half
+    return b_io, b_method
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0: float, t1: float):
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ts, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((ts, parts))
+        inside = [r for ts, r in rows if t0 - 0.06 <= ts <= t1 + 0.06] or [r for _, r in rows[-3:]]
+        if not inside:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in inside if num(r[1]) is not None]
+        mx = [num(r[2]) for r in inside if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inside)}
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """FP64 CPU oracle on a reduced grid of the same workload (host cores)."""
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    import workloads
+    from oracle.desc import Desc
+
+    n = args.ref_n
+    d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, op="CURL", ncomp=3, rhs_scale=-1.0,
+             sigma=2.0 / n)
+    omega = workloads.vortex_ring(n)["omega"]
+    g_hat = oracle.green_hat(d)  # plan set-up, outside the timed region (Sec. 2.4.4)
+    for _ in range(args.warmup):
+        oracle.solve_unbounded(d, omega, g_hat)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve_unbounded(d, omega, g_hat)
+    dt = time.perf_counter() - t0
+    value = n ** 3 * args.steps / dt
+    sample = f"oracle solve of the same workload at {n}^3 (padded {2 * n}^3), psi + curl, FP64, one process"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"3D unbounded vector Poisson (psi, u = curl psi), sampled at {n}^3", "grid": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(n: int):
+    import numpy as np
+
+    import oracle
+    import workloads
+    from oracle.desc import Desc
+
+    d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, op="CURL", ncomp=3, rhs_scale=-1.0,
+             sigma=2.0 / n)
+    omega = workloads.vortex_ring(n)["omega"]
+    g_hat = oracle.green_hat(d)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.solve_unbounded(d, omega, g_hat)
+        reps += 1
+        if time.perf_counter() - t0 > 8.0 or reps >= 5:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n ** 3 * reps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} oracle solve(s) of the same workload at {n}^3 (padded {2 * n}^3), psi + curl, "
+                      f"FP64, single-threaded numpy, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--ref-n", type=int, default=24)
+    ap.add_argument("--cpu-n", type=int, default=48)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--unfused", action="store_true")
+    ap.add_argument("--n", type=int, default=N)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    import paper_2301_01145_gb300 as sf
+    import workloads
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ge.build()
+    n = args.n
+    h = 1.0 / n
+    ring = workloads.vortex_ring(n)
+    omega = torch.tensor(ring["omega"], dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    plan = sf.Plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=2 * h, rhs_scale=-1.0,
+                   prec="f32", fused=not args.unfused)
+    psi, u = plan.empty_outputs()
+    for _ in range(args.warmup):
+        plan.execute(omega, psi, u)
+    plan.sync()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.15)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.execute(omega, psi, u)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier()
+    clocks = sampler.stop(t_wall0, t_wall1)
+    plan.sync()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    points = n ** 3
+    value = points * world / (ms * 1e-3)
+    launches = plan.launches() * args.steps
+
+    # roofline of the dominant (and, fused, only) kernel: the persistent executor
+    peak, peak_kind = read_peaks()
+    b_io, b_method = algorithmic_bytes(n)
+    achieved = b_method / (ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "bytes_model": "B_method", "algorithmic_bytes": b_method,
+            "b_io_bytes": b_io, "b_io_frac": b_io / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_kind}
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hf = omega.cpu().pin_memory()
+        hpsi = torch.empty(psi.shape, dtype=psi.dtype).pin_memory()
+        hu = torch.empty(u.shape, dtype=u.dtype).pin_memory()
+        ksteps = max(3, min(args.steps, 30))
+        plan.solve_host(hf, hpsi, hu)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            plan.solve_host(hf, hpsi, hu)
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": points * world * ksteps / dt, "unit": UNIT, "h2d_bytes_per_step": hf.numel() * 4,
+               "d2h_bytes_per_step": (hpsi.numel() + hu.numel()) * 4, "steps": ksteps}
+
+    # FP64 plain GPU solve of the same workload (comparison the metric names)
+    fp64 = None
+    if not args.no_fp64:
+        p64 = sf.Plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=2 * h, rhs_scale=-1.0,
+                      prec="f64")
+        o64 = omega.double()
+        psi64, u64 = p64.empty_outputs()
+        p64.execute(o64, psi64, u64)
+        p64.sync()
+        k64 = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k64):
+            p64.execute(o64, psi64, u64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        rel = float(((psi.double() - psi64).norm() / psi64.norm()).item())
+        relu = float(((u.double() - u64).norm() / u64.norm()).item())
+        fp64 = {"value": points / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                "f32_rel_l2_vs_f64": {"psi": rel, "u": relu}}
+        p64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_n)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "3D unbounded vector Poisson lap(psi) = -omega, 256^3 cell-centred on "
+                                       "[-0.5,0.5]^3 padded to 512^3, G2 kernel sigma=2h, outputs psi and "
+                                       "u = curl(psi); seeded Gaussian vortex ring",
+                           "grid": n, "ncomp": NCOMP, "precision": "fp32 bulk, fp64-built tables",
+                           "mode": "unfused passes" if args.unfused else "one persistent launch",
+                           "l2": "inputs larger than L2 (201 MB source, 403 MB outputs, 2.4 GB workspace)",
+                           "parallelism": f"replicas x{world}"},
+                "gpu_launches": launches, "roofline": roof, "clocks": clocks, "e2e": e2e, "fp64": fp64,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -64,6 +64,7 @@ typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
 
 /* Plan flags (sf_plan_desc.flags). */
 #define SF_FLAG_UNFUSED 1u /* one kernel launch per pass instead of one persistent launch */
+#define SF_FLAG_GENERIC 2u /* always use the general shared-memory FFT engine (no register fast path) */
 
 /*
  * Problem description (Sec. 2.4 solver options, Sec. 2.5.1 Table 1).

@@ -94,3 +94,97 @@ def solve_unbounded(desc: Desc, f: np.ndarray, g_hat: np.ndarray = None):
     psi = fft.idftn(psi_hat, axes).real[keep]
     op_out = None if op_hat is None else fft.idftn(op_hat, axes).real[keep]
     return psi, op_out
+
+
+# ---------------------------------------------------------------------------
+# one output point at a time (for grids too large for the full oracle)
+# ---------------------------------------------------------------------------
+# The doubled-domain solve equals psi_i = -s h^d sum_j G(x_i - x_j) f_j.  An
+# operator applied after the convolution acts on the 2N-periodic solution, so
+# d_a psi = -s h^d sum_j K_a(i - j) f_j with K_a = (spectral derivative along a
+# of the periodic G table).  K_a is odd in its own offset and even in the
+# others, so it is tabulated on [0, N] x [0, 2N) x [0, N] (own axis full) with
+# the oracle's DFT along that axis; each requested point is then a direct sum.
+
+def derivative_tables(desc: Desc):
+    """K_a on the half-octant, list over axes a; entry [a] has axis a of length 2N."""
+    _check(desc)
+    dim = desc.dim
+    tabs = []
+    for a in range(dim):
+        r2 = 0.0
+        for ax in range(dim):
+            M = 2 * desc.n[ax]
+            if ax == a:
+                m = np.arange(M)
+                d = np.minimum(m, M - m) * desc.h(ax)
+            else:
+                d = np.arange(desc.n[ax] + 1) * desc.h(ax)
+            r2 = r2 + ops._bcast(d * d, dim, ax)
+        g = green(dim, np.sqrt(r2), desc.sigma)
+        nax = dim - 1 - a
+        M = 2 * desc.n[a]
+        mult = ops.deriv_multiplier(M, M * desc.h(a))
+        shape = [1] * dim
+        shape[nax] = -1
+        k = fft.idft(mult.reshape(shape) * fft.dft(g, nax), nax).real
+        tabs.append(k)
+    return tabs
+
+
+def _gather(tab, dim, offs, a):
+    """tab at signed offsets offs[ax] (arrays broadcasting over sources)."""
+    idx = []
+    for ax in reversed(range(dim)):
+        o = offs[ax]
+        if ax == a:
+            M = tab.shape[dim - 1 - ax]
+            idx.append(np.mod(o, M))
+        else:
+            idx.append(np.abs(o))
+    return tab[tuple(idx)]
+
+
+def sample_points(desc: Desc, f: np.ndarray, points, tables=None):
+    """psi and op_out at the given output points (list of (x, y[, z]) indices).
+
+    Returns (psi [npts][ncomp], op [npts][nop] or None).
+    """
+    _check(desc)
+    dim = desc.dim
+    f = np.asarray(f, dtype=np.float64)
+    if f.ndim == dim:
+        f = f[None]
+    ncomp = f.shape[0]
+    hd = 1.0
+    for ax in range(dim):
+        hd *= desc.h(ax)
+    scale = -desc.rhs_scale * hd
+    src = [np.arange(desc.n[ax]) for ax in range(dim)]
+    if desc.op not in ("NONE",) and desc.op != "NABLA" and tables is None:
+        tables = derivative_tables(desc)
+    psi_out, op_out = [], []
+    for p in points:
+        offs = []
+        r2 = 0.0
+        for ax in range(dim):
+            o = p[ax] - src[ax]
+            o = ops._bcast(o, dim, ax)
+            offs.append(o)
+            r2 = r2 + (o * desc.h(ax)) ** 2
+        g = green(dim, np.sqrt(r2), desc.sigma)
+        psi_out.append([scale * np.sum(g * f[c]) for c in range(ncomp)])
+        if desc.op in ("GRAD", "DIV", "CURL"):
+            K = [_gather(tables[a], dim, offs, a) for a in range(dim)]
+            dpsi = [[scale * np.sum(K[a] * f[c]) for a in range(dim)] for c in range(ncomp)]  # d_a psi_c
+            if desc.op == "GRAD":
+                op_out.append([dpsi[0][a] for a in range(dim)])
+            elif desc.op == "DIV":
+                op_out.append([sum(dpsi[a][a] for a in range(dim))])
+            elif dim == 3:
+                op_out.append([dpsi[2][1] - dpsi[1][2], dpsi[0][2] - dpsi[2][0], dpsi[1][0] - dpsi[0][1]])
+            else:
+                op_out.append([dpsi[0][1], -dpsi[0][0]])
+    psi_arr = np.array(psi_out)
+    op_arr = np.array(op_out) if op_out else None
+    return psi_arr, op_arr

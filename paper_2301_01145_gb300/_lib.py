@@ -26,6 +26,7 @@ OP = {"NONE": 0, "GRAD": 1, "DIV": 2, "CURL": 3, "NABLA": 4}
 EIG = {"PS": 0, "FD2": 1}
 PREC = {"f32": 0, "f64": 1}
 FLAG_UNFUSED = 1
+FLAG_GENERIC = 2
 
 
 class SolverError(RuntimeError):

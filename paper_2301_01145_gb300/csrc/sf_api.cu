@@ -10,12 +10,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "../../include/sailfish_gb300.h"
-#include "sf_kernels.cuh"
+#include "sf_fast.cuh"
 
 using namespace sfg;
 
@@ -325,6 +326,119 @@ sf_status launch_list(ExecList<T> &ex, const Prob<T> *d_probs, bool fused, cudaS
   return SF_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// fast path (register warp FFT) for equal-length periodic/unbounded 3D FP32 solves
+// ---------------------------------------------------------------------------
+struct FastList {
+  std::vector<FPass> passes;
+  std::vector<int> start;
+  FPass *d_passes = nullptr;
+  int *d_start = nullptr;
+  unsigned *d_done = nullptr;
+  int total = 0;
+};
+
+// slab pipeline: YF(s), ZS(s-1), YI(s-2) per step; rings of nslot slabs for I1/I2
+template <typename T>
+void build_fast_list(const Prob<T> &Q, int S, int nslot, int L, FastList &fl) {
+  const int nslab = cdiv(Q.nsx, S);
+  std::vector<int> iyf(nslab, -1), izs(nslab, -1), iyi(nslab, -1);
+  auto push = [&](int kind, int s) {
+    FPass p{};
+    p.kind = kind;
+    p.kx0 = s * S;
+    p.nkx = std::min(S, Q.nsx - s * S);
+    p.slot = s % nslot;
+    p.dep[0] = p.dep[1] = -1;
+    if (kind == FK_YF) {
+      p.ntiles = Q.nin * p.nkx * cdiv(Q.nuz, 16);
+      if (s >= nslot) p.dep[0] = izs[s - nslot];
+    } else if (kind == FK_ZS) {
+      p.ntiles = p.nkx * (L / 8);
+      p.dep[0] = iyf[s];
+      if (s >= nslot) p.dep[1] = iyi[s - nslot];
+    } else {
+      p.ntiles = Q.nout * p.nkx * cdiv(Q.nuz, 8);
+      p.dep[0] = izs[s];
+    }
+    for (int d = 0; d < 2; ++d) p.depcnt[d] = p.dep[d] >= 0 ? fl.passes[p.dep[d]].ntiles : 0;
+    fl.passes.push_back(p);
+    const int idx = (int)fl.passes.size() - 1;
+    if (kind == FK_YF) iyf[s] = idx;
+    else if (kind == FK_ZS) izs[s] = idx;
+    else iyi[s] = idx;
+  };
+  for (int step = 0; step < nslab + 2; ++step) {
+    if (step < nslab) push(FK_YF, step);
+    if (step - 1 >= 0 && step - 1 < nslab) push(FK_ZS, step - 1);
+    if (step - 2 >= 0 && step - 2 < nslab) push(FK_YI, step - 2);
+  }
+  fl.start.assign(fl.passes.size() + 1, 0);
+  for (size_t i = 0; i < fl.passes.size(); ++i) fl.start[i + 1] = fl.start[i] + fl.passes[i].ntiles;
+  fl.total = fl.start.back();
+}
+
+template <typename T> sf_status upload_fast(FastList &fl, DevMem<T> &mem) {
+  void *p;
+  SF_TRY(mem.alloc(&p, fl.passes.size() * sizeof(FPass)));
+  fl.d_passes = (FPass *)p;
+  SF_TRY(mem.alloc(&p, fl.start.size() * sizeof(int)));
+  fl.d_start = (int *)p;
+  SF_TRY(mem.alloc(&p, fl.passes.size() * sizeof(unsigned)));
+  fl.d_done = (unsigned *)p;
+  SF_CK(cudaMemcpy(fl.d_passes, fl.passes.data(), fl.passes.size() * sizeof(FPass), cudaMemcpyHostToDevice));
+  SF_CK(cudaMemcpy(fl.d_start, fl.start.data(), fl.start.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return SF_OK;
+}
+
+template <int E> size_t fast_x_smem() { return (size_t)(fast_wsm_elems<E>() + (16 * E + 1) * 17) * sizeof(float2); }
+template <int E> size_t fast_yz_smem(int nuz) {
+  return (size_t)(fast_wsm_elems<E>() + std::max(32 * E * 17, nuz * 9)) * sizeof(float2);
+}
+
+template <int E> sf_status fast_attrs() {
+  static bool done = false;
+  if (done) return SF_OK;
+  SF_CK(cudaFuncSetAttribute(k_fx<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  SF_CK(cudaFuncSetAttribute(k_fxi<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  SF_CK(cudaFuncSetAttribute(k_fyz<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  done = true;
+  return SF_OK;
+}
+
+// enqueue the fast path: k_fx (front), k_fyz (front), k_fxi (back)
+template <int E>
+sf_status launch_fast(const Prob<float> &Q, const Prob<float> *d_prob, const FastGeo &g, FastList &fl, bool front,
+                      bool back, cudaStream_t st, ExecCtl *ctl, unsigned *sticky, const IOArgs<float> &io,
+                      int *launches) {
+  SF_TRY(fast_attrs<E>());
+  const size_t smx = fast_x_smem<E>();
+  if (front) {
+    k_fx<E><<<Q.nin * Q.nuz * cdiv(Q.nuy, 16), SF_FAST_THREADS, smx, st>>>(d_prob, io);
+    SF_CK(cudaGetLastError());
+    SF_CK(cudaMemsetAsync(fl.d_done, 0, fl.passes.size() * sizeof(unsigned), st));
+    SF_CK(cudaMemsetAsync(ctl, 0, sizeof(ExecCtl), st));
+    int dev = 0, nsm = 0, per = 0;
+    SF_CK(cudaGetDevice(&dev));
+    SF_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smyz = fast_yz_smem<E>(Q.nuz);
+    SF_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fyz<E>, SF_FAST_THREADS, smyz));
+    if (per < 1) return fail(SF_ERR_CUDA, "fast executor does not fit on an SM");
+    const int grid = std::min(fl.total, nsm * per);
+    k_fyz<E><<<grid, SF_FAST_THREADS, smyz, st>>>(d_prob, g, fl.d_passes, fl.d_start, (int)fl.passes.size(),
+                                                  fl.d_done, ctl, sticky, kTimeoutNs, io);
+    SF_CK(cudaGetLastError());
+    if (launches) *launches += 2;
+  }
+  if (back) {
+    k_fxi<E><<<Q.nout * Q.nuz * cdiv(Q.nuy, 16), SF_FAST_THREADS, smx, st>>>(d_prob, io);
+    SF_CK(cudaGetLastError());
+    if (launches) *launches += 1;
+  }
+  return SF_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -357,6 +471,9 @@ template <typename T> struct PlanImpl : sf_plan_s {
   const T *faces[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
   size_t ws_bytes = 0;
   size_t field_elems = 0, op_elems = 0;
+  int fastE = 0;  // 8 or 16: register fast path with L = 32 E; 0: generic engine
+  FastGeo geo{};
+  FastList fl_fwd, fl_adj;
   void *st_in = nullptr, *st_psi = nullptr, *st_op = nullptr;  // host-solve staging
 
   bool fused() const { return !(d.flags & SF_FLAG_UNFUSED); }
@@ -380,8 +497,12 @@ template <typename T> struct PlanImpl : sf_plan_s {
   sf_status init(const sf_plan_desc &desc, cudaStream_t st);
   sf_status build_green();
 
+  sf_status run_fast(const Prob<T> &Q, const Prob<T> *dq, FastList &fl, bool front, bool back, const IOArgs<T> &io,
+                     int *launches);
+
   sf_status solve_part(bool front, bool back, const void *f, void *psi, void *op, int *launches) override {
     IOArgs<T> io = io_forward(f, psi, op);
+    if (fastE) return run_fast(P, d_probs, fl_fwd, front, back, io, launches);
     if (front && back) return launch_list<T>(ex_all, d_probs, fused(), stream, ctl, sticky, io, launches);
     if (front) return launch_list<T>(ex_front, d_probs, fused(), stream, ctl, sticky, io, launches);
     return launch_list<T>(ex_back, d_probs, fused(), stream, ctl, sticky, io, launches);
@@ -394,6 +515,7 @@ template <typename T> struct PlanImpl : sf_plan_s {
     for (int o = 0; o < P.nop; ++o) io.in[P.ncomp + o] = go ? (const T *)go + o * field_elems : nullptr;
     for (int c = 0; c < P.ncomp; ++c) io.out[c] = (T *)gf + c * field_elems;
     io.has_face = 0;
+    if (fastE) return run_fast(PA, d_probs + 1, fl_adj, true, true, io, nullptr);
     return launch_list<T>(ex_adj, d_probs + 1, fused(), stream, ctl, sticky, io, nullptr);
   }
 
@@ -452,6 +574,17 @@ template <typename T> struct PlanImpl : sf_plan_s {
     return sync();
   }
 };
+
+template <typename T>
+sf_status PlanImpl<T>::run_fast(const Prob<T> &, const Prob<T> *, FastList &, bool, bool, const IOArgs<T> &, int *) {
+  return fail(SF_ERR_UNSUPPORTED, "fast path is FP32 only");
+}
+template <>
+sf_status PlanImpl<float>::run_fast(const Prob<float> &Q, const Prob<float> *dq, FastList &fl, bool front, bool back,
+                                    const IOArgs<float> &io, int *launches) {
+  if (fastE == 16) return launch_fast<16>(Q, dq, geo, fl, front, back, stream, ctl, sticky, io, launches);
+  return launch_fast<8>(Q, dq, geo, fl, front, back, stream, ctl, sticky, io, launches);
+}
 
 static int axis_kind(int bc, int grid) {
   const bool stag = grid == SF_GRID_STAGGERED;
@@ -588,7 +721,19 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   const int nf = p.ncomp + p.nop;
   const size_t esz = p.cpath ? sizeof(cx<T>) : sizeof(T);
   const size_t eA = (size_t)nf * p.nsx * p.nuz * p.nuy;
-  const size_t eI = d.dim == 3 ? (size_t)nf * p.nsx * p.nuz * p.nsy : 0;
+  size_t eI = d.dim == 3 ? (size_t)nf * p.nsx * p.nuz * p.nsy : 0;
+  // register fast path: FP32, 3D, periodic/unbounded, one FFT length L = 256 or 512 on all axes
+  if (sizeof(T) == 4 && d.dim == 3 && p.cpath && !(d.flags & SF_FLAG_GENERIC) && p.ax[0].L == p.ax[1].L &&
+      p.ax[1].L == p.ax[2].L && (p.ax[0].L == 512 || p.ax[0].L == 256)) {
+    fastE = p.ax[0].L / 32;
+    const char *env = getenv("SF_SLAB_PLANES");
+    int S = env ? atoi(env) : 2;
+    if (S < 1) S = 1;
+    geo.S = fused() ? std::min(S, p.nsx) : p.nsx;
+    geo.nslot = fused() ? 2 : 1;
+    geo.nfmax = nf;
+    eI = (size_t)geo.nslot * nf * geo.S * p.ax[1].L * p.nuz;
+  }
   SF_TRY(mem.alloc(&p.A, eA * esz));
   SF_TRY(mem.alloc(&p.B, eA * esz));
   if (eI) {
@@ -653,6 +798,13 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   SF_TRY(ex_all.upload(mem));
   SF_TRY(ex_adj.upload(mem));
   launches_per_exec = fused() ? 1 : (int)ex_all.passes.size();
+  if (fastE) {
+    build_fast_list<T>(P, geo.S, geo.nslot, p.ax[1].L, fl_fwd);
+    build_fast_list<T>(PA, geo.S, geo.nslot, p.ax[1].L, fl_adj);
+    SF_TRY(upload_fast<T>(fl_fwd, mem));
+    SF_TRY(upload_fast<T>(fl_adj, mem));
+    launches_per_exec = 3;
+  }
   return SF_OK;
 }
 
@@ -747,7 +899,16 @@ template <typename T> struct BatchImpl : sf_plan_s {
     is_batch = true;
     for (int i = 0; i < n; ++i) plans.push_back(static_cast<PlanImpl<T> *>(ps[i]));
     probs.resize(n);
-    for (int i = 0; i < n; ++i) probs[i] = plans[i]->P;
+    for (int i = 0; i < n; ++i) {
+      probs[i] = plans[i]->P;
+      if (plans[i]->fastE) {
+        // the batch runs the general engine: give register-path plans full-size intermediates
+        const Prob<T> &q = probs[i];
+        const size_t eI = (size_t)(q.ncomp + q.nop) * q.nsx * q.nuz * q.nsy * sizeof(cx<T>);
+        SF_TRY(mem.alloc(&probs[i].I1, eI));
+        SF_TRY(mem.alloc(&probs[i].I2, eI));
+      }
+    }
     // level-synchronous order: every problem's pass j before any pass j+1, so a
     // problem's dependency is (almost always) complete when its next pass starts
     std::vector<std::vector<int>> kinds(n);

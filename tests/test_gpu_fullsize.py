@@ -1,0 +1,158 @@
+"""GPU parity at the benchmark sizes, in the launch configuration the benchmark times.
+
+  * C1 (64^3 periodic FP64) is covered element by element in test_gpu_parity.py.
+  * C2 (257^3 regular nodes, Dirichlet/Neumann/Dirichlet, FD2, inhomogeneous
+    faces, FP32): the full oracle is affordable, element by element.
+  * C3 (256^3 unbounded, 3 components, curl, FP32, register fast path with
+    the slab-pipelined executor): psi and u at sampled output points computed
+    one by one by the oracle's direct sums.
+  * The register fast path (L = 256, 512) against the oracle at 128^3, and
+    against the general engine on whole fields (forward and adjoint).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import unbounded
+from oracle.desc import Desc
+from tests.gpu_helpers import TOL, gpu_plan, oracle_desc, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built(gpu_available):
+    import __graft_entry__ as g
+    g.build()
+
+
+def sample_idx(n, count, seed):
+    rng = np.random.default_rng(seed)
+    pts = [tuple(int(v) for v in rng.integers(0, n, size=3)) for _ in range(count)]
+    return pts + [(0, 0, 0), (n - 1, n - 1, n - 1), (n // 2, n // 2, n // 2)]
+
+
+def check_samples(got_psi, got_op, ref_psi, ref_op, pts, tol):
+    """pointwise error at the samples relative to each field's RMS on the GPU grid"""
+    for c in range(got_psi.shape[0]):
+        rms = float(np.sqrt(np.mean(got_psi[c] ** 2)))
+        for i, p in enumerate(pts):
+            err = abs(got_psi[c][p[2], p[1], p[0]] - ref_psi[i][c])
+            assert err <= tol * rms, f"psi[{c}] at {p}: {err:.3e} vs rms {rms:.3e}"
+    if got_op is not None:
+        for c in range(got_op.shape[0]):
+            rms = float(np.sqrt(np.mean(got_op[c] ** 2)))
+            for i, p in enumerate(pts):
+                err = abs(got_op[c][p[2], p[1], p[0]] - ref_op[i][c])
+                assert err <= tol * rms, f"op[{c}] at {p}: {err:.3e} vs rms {rms:.3e}"
+
+
+def test_c2_fullsize_elementwise():
+    n = 256
+    man = workloads.manufactured(seed_index=1)
+    case = workloads.bounded_case(man, (n, n, n), ("D", "N", "D"), False)
+    plan = gpu_plan(3, (n,) * 3, (0,) * 3, (1,) * 3, "DND", grid="regular", eig="FD2", prec="f32")
+    for (ax, side), g in case["faces"].items():
+        plan.set_boundary(ax, side, to_dev(g, "f32"))
+    psi = plan(to_dev(case["f"][None], "f32"))
+    plan.sync()
+    d = Desc(3, (n,) * 3, (0,) * 3, (1,) * 3, ("D", "N", "D"), False, "FD2")
+    ref, _ = oracle.solve(d, case["f"], case["faces"])
+    assert rel_l2(to_np(psi)[0], ref[0]) <= TOL["f32"]
+    # and the discretisation error of the FD2 solve is the expected O(h^2) size
+    assert np.max(np.abs(to_np(psi)[0] - case["psi_exact"])) < 2e-3
+    plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("f64", 1e-10)])
+def test_c3_fullsize_sampled(prec, tol):
+    n = 256
+    ring = workloads.vortex_ring(n)
+    plan = gpu_plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=2.0 / n,
+                    rhs_scale=-1.0, prec=prec)
+    psi, u = plan(to_dev(ring["omega"], prec))
+    plan.sync()
+    gp, gu = to_np(psi), to_np(u)
+    plan.close()
+    d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, op="CURL", ncomp=3, rhs_scale=-1.0,
+             sigma=2.0 / n)
+    pts = sample_idx(n, 9, 7)
+    # points near the ring core where the fields are largest
+    pts += [(int(np.argmax(np.abs(gu[0])) % n), int(np.argmax(np.abs(gu[0])) // n % n),
+             int(np.argmax(np.abs(gu[0])) // (n * n)))]
+    ref_psi, ref_u = unbounded.sample_points(d, ring["omega"], pts)
+    check_samples(gp, gu, ref_psi, ref_u, pts, tol)
+
+
+def test_fast_path_128_vs_oracle_samples():
+    n = 128
+    blobs = workloads.gaussian_blobs(n)
+    plan = gpu_plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=2.0 / n, rhs_scale=-1.0)
+    psi, u = plan(to_dev(blobs["omega"], "f32"))
+    plan.sync()
+    d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, op="CURL", ncomp=3, rhs_scale=-1.0,
+             sigma=2.0 / n)
+    pts = sample_idx(n, 12, 3)
+    ref_psi, ref_u = unbounded.sample_points(d, blobs["omega"], pts)
+    check_samples(to_np(psi), to_np(u), ref_psi, ref_u, pts, 1e-5)
+    plan.close()
+
+
+def test_fast_path_periodic_256_vs_oracle():
+    n = 256
+    rng = np.random.default_rng(5)
+    f = workloads.lowpass_noise((n, n, n), 77)[None]
+    out = {}
+    plan = gpu_plan(3, (n,) * 3, (0,) * 3, (1.0, 2.0, 1.5), "PPP", eig="FD2")
+    got = to_np(plan(to_dev(f, "f32")))
+    plan.sync()
+    plan.close()
+    d = oracle_desc(3, (n,) * 3, (0,) * 3, (1.0, 2.0, 1.5), "PPP", "staggered", "FD2")
+    ref, _ = oracle.solve(d, f)
+    assert rel_l2(got[0], ref[0]) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("n,op,ncomp", [(128, "CURL", 3), (128, "GRAD", 1), (128, "DIV", 3), (128, "NABLA", 1),
+                                        (256, "CURL", 3), (128, "NONE", 2)])
+@pytest.mark.parametrize("fused", [True, False])
+def test_fast_vs_general_engine(n, op, ncomp, fused):
+    import paper_2301_01145_gb300 as sf
+    rng = np.random.default_rng(n + ncomp)
+    f = to_dev(rng.normal(size=(ncomp, n, n, n)), "f32")
+    res = []
+    for generic in (False, True):
+        plan = sf.Plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op=op, ncomp=ncomp, sigma=2.0 / n,
+                       rhs_scale=-1.0, fused=fused, generic=generic)
+        out = plan(f)
+        plan.sync()
+        res.append([to_np(o) for o in (out if isinstance(out, tuple) else (out,))])
+        plan.close()
+    for a, b in zip(res[0], res[1]):
+        for c in range(a.shape[0]):
+            assert rel_l2(a[c], b[c]) <= 2e-6
+
+
+def test_fast_adjoint_vs_general_and_dot_product():
+    import paper_2301_01145_gb300 as sf
+    n = 128
+    rng = np.random.default_rng(17)
+    x = to_dev(rng.normal(size=(3, n, n, n)), "f32")
+    gp = to_dev(rng.normal(size=(3, n, n, n)), "f32")
+    gu = to_dev(rng.normal(size=(3, n, n, n)), "f32")
+    outs = []
+    for generic in (False, True):
+        plan = sf.Plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=2.0 / n,
+                       rhs_scale=-1.0, generic=generic)
+        psi, u = plan(x)
+        gf = plan.adjoint(gp, gu)
+        plan.sync()
+        lhs = float((psi.double() * gp.double()).sum() + (u.double() * gu.double()).sum())
+        rhs = float((x.double() * gf.double()).sum())
+        assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+        outs.append(to_np(gf))
+        plan.close()
+    for c in range(3):
+        assert rel_l2(outs[0][c], outs[1][c]) <= 2e-6

@@ -157,3 +157,24 @@ def test_nabla_returns_source_ps_periodic():
     f = rng.normal(size=d.shape())
     _, lap = oracle.solve(d, f)
     np.testing.assert_allclose(lap[0], f - f.mean(), atol=1e-11)
+
+
+@pytest.mark.parametrize("op,ncomp,dim", [("CURL", 3, 3), ("GRAD", 1, 3), ("DIV", 3, 3), ("CURL", 1, 2),
+                                          ("NONE", 2, 3)])
+def test_sampled_points_match_full_oracle(op, ncomp, dim):
+    # the point-wise evaluation used at full size equals the full doubled-domain solve
+    from oracle import unbounded
+    n = (10, 8, 6)[:dim]
+    d = Desc(dim, n, (-0.5,) * dim, (0.5, 0.4, 0.3)[:dim], ("U",) * dim, True, op=op, ncomp=ncomp,
+             rhs_scale=-1.0, sigma=0.12)
+    rng = np.random.default_rng(9)
+    f = rng.normal(size=(ncomp,) + d.shape())
+    psi, opo = oracle.solve(d, f)
+    pts = [tuple(rng.integers(0, n[a]) for a in range(dim)) for _ in range(6)] + [tuple(0 for _ in n),
+                                                                                 tuple(m - 1 for m in n)]
+    ps, os_ = unbounded.sample_points(d, f, pts)
+    for i, p in enumerate(pts):
+        idx = tuple(reversed(p))
+        np.testing.assert_allclose(ps[i], psi[(slice(None),) + idx], rtol=1e-11, atol=1e-13)
+        if opo is not None:
+            np.testing.assert_allclose(os_[i], opo[(slice(None),) + idx], rtol=1e-10, atol=1e-12)
