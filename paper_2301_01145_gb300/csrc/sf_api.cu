@@ -352,14 +352,14 @@ void build_fast_list(const Prob<T> &Q, int S, int nslot, int L, FastList &fl) {
     p.slot = s % nslot;
     p.dep[0] = p.dep[1] = -1;
     if (kind == FK_YF) {
-      p.ntiles = Q.nin * p.nkx * cdiv(Q.nuz, 16);
+      p.ntiles = fast_tiles_yf(Q, p.nkx);
       if (s >= nslot) p.dep[0] = izs[s - nslot];
     } else if (kind == FK_ZS) {
-      p.ntiles = p.nkx * (L / 8);
+      p.ntiles = fast_tiles_zs(p.nkx, L);
       p.dep[0] = iyf[s];
       if (s >= nslot) p.dep[1] = iyi[s - nslot];
     } else {
-      p.ntiles = Q.nout * p.nkx * cdiv(Q.nuz, 8);
+      p.ntiles = fast_tiles_yi(Q, p.nkx);
       p.dep[0] = izs[s];
     }
     for (int d = 0; d < 2; ++d) p.depcnt[d] = p.dep[d] >= 0 ? fl.passes[p.dep[d]].ntiles : 0;
@@ -389,53 +389,6 @@ template <typename T> sf_status upload_fast(FastList &fl, DevMem<T> &mem) {
   fl.d_done = (unsigned *)p;
   SF_CK(cudaMemcpy(fl.d_passes, fl.passes.data(), fl.passes.size() * sizeof(FPass), cudaMemcpyHostToDevice));
   SF_CK(cudaMemcpy(fl.d_start, fl.start.data(), fl.start.size() * sizeof(int), cudaMemcpyHostToDevice));
-  return SF_OK;
-}
-
-template <int E> size_t fast_x_smem() { return (size_t)(fast_wsm_elems<E>() + (16 * E + 1) * 17) * sizeof(float2); }
-template <int E> size_t fast_yz_smem(int nuz) {
-  return (size_t)(fast_wsm_elems<E>() + std::max(32 * E * 17, nuz * 9)) * sizeof(float2);
-}
-
-template <int E> sf_status fast_attrs() {
-  static bool done = false;
-  if (done) return SF_OK;
-  SF_CK(cudaFuncSetAttribute(k_fx<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  SF_CK(cudaFuncSetAttribute(k_fxi<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  SF_CK(cudaFuncSetAttribute(k_fyz<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  done = true;
-  return SF_OK;
-}
-
-// enqueue the fast path: k_fx (front), k_fyz (front), k_fxi (back)
-template <int E>
-sf_status launch_fast(const Prob<float> &Q, const Prob<float> *d_prob, const FastGeo &g, FastList &fl, bool front,
-                      bool back, cudaStream_t st, ExecCtl *ctl, unsigned *sticky, const IOArgs<float> &io,
-                      int *launches) {
-  SF_TRY(fast_attrs<E>());
-  const size_t smx = fast_x_smem<E>();
-  if (front) {
-    k_fx<E><<<Q.nin * Q.nuz * cdiv(Q.nuy, 16), SF_FAST_THREADS, smx, st>>>(d_prob, io);
-    SF_CK(cudaGetLastError());
-    SF_CK(cudaMemsetAsync(fl.d_done, 0, fl.passes.size() * sizeof(unsigned), st));
-    SF_CK(cudaMemsetAsync(ctl, 0, sizeof(ExecCtl), st));
-    int dev = 0, nsm = 0, per = 0;
-    SF_CK(cudaGetDevice(&dev));
-    SF_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const size_t smyz = fast_yz_smem<E>(Q.nuz);
-    SF_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fyz<E>, SF_FAST_THREADS, smyz));
-    if (per < 1) return fail(SF_ERR_CUDA, "fast executor does not fit on an SM");
-    const int grid = std::min(fl.total, nsm * per);
-    k_fyz<E><<<grid, SF_FAST_THREADS, smyz, st>>>(d_prob, g, fl.d_passes, fl.d_start, (int)fl.passes.size(),
-                                                  fl.d_done, ctl, sticky, kTimeoutNs, io);
-    SF_CK(cudaGetLastError());
-    if (launches) *launches += 2;
-  }
-  if (back) {
-    k_fxi<E><<<Q.nout * Q.nuz * cdiv(Q.nuy, 16), SF_FAST_THREADS, smx, st>>>(d_prob, io);
-    SF_CK(cudaGetLastError());
-    if (launches) *launches += 1;
-  }
   return SF_OK;
 }
 
@@ -582,8 +535,24 @@ sf_status PlanImpl<T>::run_fast(const Prob<T> &, const Prob<T> *, FastList &, bo
 template <>
 sf_status PlanImpl<float>::run_fast(const Prob<float> &Q, const Prob<float> *dq, FastList &fl, bool front, bool back,
                                     const IOArgs<float> &io, int *launches) {
-  if (fastE == 16) return launch_fast<16>(Q, dq, geo, fl, front, back, stream, ctl, sticky, io, launches);
-  return launch_fast<8>(Q, dq, geo, fl, front, back, stream, ctl, sticky, io, launches);
+  FastLaunch L{};
+  L.d_prob = dq;
+  L.h_prob = &Q;
+  L.geo = geo;
+  L.d_passes = fl.d_passes;
+  L.d_start = fl.d_start;
+  L.d_done = fl.d_done;
+  L.npass = (int)fl.passes.size();
+  L.total = fl.total;
+  L.ctl = ctl;
+  L.sticky = sticky;
+  L.timeout_ns = kTimeoutNs;
+  L.front = front;
+  L.back = back;
+  L.stream = stream;
+  const int e = fastE == 16 ? sf_fast_launch_e16(L, io, launches) : sf_fast_launch_e8(L, io, launches);
+  if (e) return fail(SF_ERR_CUDA, std::string("fast path launch: ") + cudaGetErrorString((cudaError_t)e));
+  return SF_OK;
 }
 
 static int axis_kind(int bc, int grid) {
@@ -701,6 +670,33 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
     }
   }
   p.mscale = (T)(d.rhs_scale / prodL);
+  // operator coefficient table (Sec. 2.4.3): output o = sum_c coef(o, c) psi_c
+  for (int o = 0; o < 3; ++o)
+    for (int c = 0; c < 3; ++c) p.opc[o][c] = p.opa[o][c] = 0;
+  auto deriv = [&](int o, int c, int sign, int axis) {
+    p.opc[o][c] = sign;
+    p.opa[o][c] = axis;
+  };
+  switch (d.op) {
+    case SF_OP_GRAD:
+      for (int a = 0; a < d.dim; ++a) deriv(a, 0, 1, a);
+      break;
+    case SF_OP_DIV:
+      for (int a = 0; a < d.dim; ++a) deriv(0, a, 1, a);
+      break;
+    case SF_OP_CURL:
+      if (d.dim == 3) {
+        deriv(0, 2, 1, 1); deriv(0, 1, -1, 2);
+        deriv(1, 0, 1, 2); deriv(1, 2, -1, 0);
+        deriv(2, 1, 1, 0); deriv(2, 0, -1, 1);
+      } else {
+        deriv(0, 0, 1, 1); deriv(1, 0, -1, 0);
+      }
+      break;
+    case SF_OP_NABLA:
+      for (int c = 0; c < d.ncomp; ++c) p.opc[c][c] = 2;
+      break;
+  }
   derive_extents<T>(p);
   field_elems = (size_t)p.ax[0].nodes * p.ax[1].nodes * (d.dim == 3 ? p.ax[2].nodes : 1);
   // FD2 lifting weights (Sec. 2.5.2 boundary weighting; divided by rhs_scale
@@ -868,6 +864,13 @@ template <typename T> sf_status PlanImpl<T>::build_green() {
   const double scale = -d.rhs_scale * hd / prodL;
   sfg::k_convert_scale<T><<<1024, 256, 0, stream>>>((T *)gh, (const double *)out, cnt, scale);
   SF_CK(cudaGetLastError());
+  if (fastE && dim == 3) {
+    void *ght;
+    SF_TRY(mem.alloc(&ght, cnt * sizeof(T)));
+    sfg::k_transpose_green<T><<<1024, 256, 0, stream>>>((T *)ght, (const T *)gh, nx + 1, nz + 1, ny + 1);
+    SF_CK(cudaGetLastError());
+    P.ghat_t = (const T *)ght;
+  }
   SF_CK(cudaStreamSynchronize(stream));
   P.ghat = (const T *)gh;
   return SF_OK;

@@ -200,6 +200,8 @@ template <typename T> struct Prob {
   int nin, nout;  // fields entering the x transform / leaving the stage
   int cpath;      // 1: periodic/unbounded (complex spectra); 0: Dirichlet/Neumann (real)
   int op;         // OpKind
+  int opc[3][3];  // operator coefficient of component c in output o: 0, +-1 (+-i kappa_axis), 2 (-|kappa|^2)
+  int opa[3][3];  // axis of the derivative coefficient
   int green;      // 1: multiply by the Green's table
   int adjoint;    // 1: transposed solve
   int nrw;        // adjoint: apply regular-Neumann end-point weights
@@ -212,7 +214,8 @@ template <typename T> struct Prob {
   T facew[3][2];
   int has_face;
   void *A, *I1, *I2, *B;
-  const T *ghat;  // unbounded: [kx][kz][ky] octant (3D) / [kx][ky] (2D), pre-scaled
+  const T *ghat;    // unbounded: [kx][kz][ky] octant (3D) / [kx][ky] (2D), pre-scaled
+  const T *ghat_t;  // the same table as [kx][ky][kz] (register fast path)
   T *fwd_out;     // set-up: forward-only output
   // derived extents
   int nsx, nuy, nuz, nsy, nsz;

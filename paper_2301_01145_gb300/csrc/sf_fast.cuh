@@ -1,5 +1,6 @@
-// sf_fast.cuh -- register-resident fast path for periodic / unbounded 3D solves
-// whose three axes share one FFT length L = 32*E (E = 8 or 16, i.e. L = 256 or 512).
+// sf_fast.cuh -- register-resident fast path for periodic / unbounded 3D FP32
+// solves whose three axes share one FFT length L = 32*E (E = 8 or 16, i.e.
+// L = 256 or 512).
 //
 // Warp FFT.  One warp owns one line of L points; thread t holds x[t + 32 r],
 // r < E.  The transform is the four-step split L = E x 32:
@@ -12,14 +13,17 @@
 // X[k1 + E (j + E bitrev_G(q))].  The inverse runs the transposed network
 // (decimation in time over lanes, conjugate twiddles) from the k layout back
 // to the natural layout.  Only __syncwarp is needed inside a transform.
+// For the doubled (unbounded) axes the upper half of every forward input is
+// zero and only the lower half of every inverse output is kept: the first /
+// last E-point DFT is then evaluated in a pruned form.
 //
-// Pass structure (all global accesses are contiguous rows or >= 64-byte
-// chunks of a shared-memory transpose):
-//   k_fx   source rows along x  -> A  [c][kx][z][y]      (16 y per chunk)
-//   YF     rows of A along y    -> I1 [c][kx][ky][z]     (16 z per chunk)
+// Pass structure (every global access is a contiguous row or a >= 64-byte
+// chunk of a shared-memory transpose):
+//   k_fx   source rows along x  -> A  [c][kx][z][y]     (transposed store, 16 y per chunk)
+//   YF     rows of A along y    -> I1 [c][kx][ky][z]    (transposed store, 16 z per chunk)
 //   ZS     rows of I1 along z: forward, multiply, operator, inverse
-//                               -> I2 [f][kx][z][ky]     (8 ky per chunk)
-//   YI     rows of I2 along ky  -> B  [f][kx][z][y]      (contiguous rows)
+//                               -> I2 [f][kx][ky][z]    (direct row store)
+//   YI     columns of I2 along ky (transposed load) -> B [f][kx][z][y] (direct row store)
 //   k_fxi  B transposed back    -> result rows along x
 // YF/ZS/YI run in one persistent kernel over slabs of S kx-planes; I1 and I2
 // are rings of two slabs so that they stay resident in L2 while the slab
@@ -55,12 +59,84 @@ template <int E> __device__ __forceinline__ int klayout(int lane, int j) {
   return k1 + E * (j + E * bitrev_lanes(q, G));
 }
 
-template <typename T, int E>
+// ---- pruned E-point DFTs ----------------------------------------------------
+// dft4 of (a0, a1, 0, 0)
+template <bool INV, typename V> __device__ __forceinline__ void dft4_2in(V a0, V a1, V &y0, V &y1, V &y2, V &y3) {
+  const V m = mul_mi<INV>(a1);
+  y0 = cadd(a0, a1);
+  y1 = cadd(a0, m);
+  y2 = csub(a0, a1);
+  y3 = csub(a0, m);
+}
+
+// inputs x[E/2 .. E) are zero
+template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfin(V *x) {
+  if (E == 16) {
+    V f[16];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) dft4_2in<INV>(x[s], x[s + 4], f[s * 4 + 0], f[s * 4 + 1], f[s * 4 + 2], f[s * 4 + 3]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      V t0 = f[k1];
+      V t1 = w16<INV>(f[4 + k1], k1);
+      V t2 = w16<INV>(f[8 + k1], 2 * k1);
+      V t3 = w16<INV>(f[12 + k1], 3 * k1);
+      dft4v<INV>(t0, t1, t2, t3);
+      x[k1] = t0; x[k1 + 4] = t1; x[k1 + 8] = t2; x[k1 + 12] = t3;
+    }
+  } else {  // E == 8
+    V e0, e1, e2, e3, o0, o1, o2, o3;
+    dft4_2in<INV>(x[0], x[2], e0, e1, e2, e3);
+    dft4_2in<INV>(x[1], x[3], o0, o1, o2, o3);
+    o1 = w8<INV>(o1, 1);
+    o2 = w8<INV>(o2, 2);
+    o3 = w8<INV>(o3, 3);
+    x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
+    x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
+    x[2] = cadd(e2, o2); x[6] = csub(e2, o2);
+    x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
+  }
+}
+
+// only outputs y[0 .. E/2) are needed
+template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfout(V *x) {
+  if (E == 16) {
+    V f[16];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      V a0 = x[s], a1 = x[s + 4], a2 = x[s + 8], a3 = x[s + 12];
+      dft4v<INV>(a0, a1, a2, a3);
+      f[s * 4 + 0] = a0; f[s * 4 + 1] = a1; f[s * 4 + 2] = a2; f[s * 4 + 3] = a3;
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      const V t0 = f[k1];
+      const V t1 = w16<INV>(f[4 + k1], k1);
+      const V t2 = w16<INV>(f[8 + k1], 2 * k1);
+      const V t3 = w16<INV>(f[12 + k1], 3 * k1);
+      x[k1] = cadd(cadd(t0, t2), cadd(t1, t3));
+      x[k1 + 4] = cadd(csub(t0, t2), mul_mi<INV>(csub(t1, t3)));
+    }
+  } else {
+    V e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+    V o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+    dft4v<INV>(e0, e1, e2, e3);
+    dft4v<INV>(o0, o1, o2, o3);
+    x[0] = cadd(e0, o0);
+    x[1] = cadd(e1, w8<INV>(o1, 1));
+    x[2] = cadd(e2, w8<INV>(o2, 2));
+    x[3] = cadd(e3, w8<INV>(o3, 3));
+  }
+}
+
+// ---- warp FFTs -------------------------------------------------------------
+template <typename T, int E, bool HALFIN>
 __device__ __forceinline__ void wfft_fwd(cx<T> *v, cx<T> *wsm, const cx<T> *__restrict__ tw) {
   typedef cx<T> V;
   constexpr int L = 32 * E, G = 32 / E;
   const int t = threadIdx.x & 31;
-  dftR<E, false>(v);
+  if (HALFIN) dft_halfin<E, false>(v);
+  else dftR<E, false>(v);
 #pragma unroll
   for (int k1 = 1; k1 < E; ++k1) v[k1] = cmul(v[k1], __ldg(&tw[t * k1]));
 #pragma unroll
@@ -75,17 +151,25 @@ __device__ __forceinline__ void wfft_fwd(cx<T> *v, cx<T> *wsm, const cx<T> *__re
   for (int j = 1; j < E; ++j) v[j] = cmul(v[j], __ldg(&tw[q * j * E]));
 #pragma unroll
   for (int m = G / 2; m >= 1; m >>= 1) {
-    const V w = __ldg(&tw[(q & (m - 1)) * (L / (2 * m))]);
     const bool hi = (q & m) != 0;
+    if (m == 1) {  // twiddle W_2^0 = 1
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const V p = shfl_xor_c(v[j], m);
-      v[j] = hi ? cmul(csub(p, v[j]), w) : cadd(v[j], p);
+      for (int j = 0; j < E; ++j) {
+        const V p = shfl_xor_c(v[j], m);
+        v[j] = hi ? csub(p, v[j]) : cadd(v[j], p);
+      }
+    } else {
+      const V w = __ldg(&tw[(q & (m - 1)) * (L / (2 * m))]);
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const V p = shfl_xor_c(v[j], m);
+        v[j] = hi ? cmul(csub(p, v[j]), w) : cadd(v[j], p);
+      }
     }
   }
 }
 
-template <typename T, int E>
+template <typename T, int E, bool HALFOUT>
 __device__ __forceinline__ void wfft_inv(cx<T> *v, cx<T> *wsm, const cx<T> *__restrict__ tw) {
   typedef cx<T> V;
   constexpr int L = 32 * E, G = 32 / E;
@@ -93,12 +177,20 @@ __device__ __forceinline__ void wfft_inv(cx<T> *v, cx<T> *wsm, const cx<T> *__re
   const int k1 = t / G, q = t % G;
 #pragma unroll
   for (int m = 1; m < G; m <<= 1) {
-    const V w = __ldg(&tw[(q & (m - 1)) * (L / (2 * m))]);
     const bool hi = (q & m) != 0;
+    if (m == 1) {
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const V p = shfl_xor_c(v[j], m);
-      v[j] = hi ? csub(p, cmulc(v[j], w)) : cadd(v[j], cmulc(p, w));
+      for (int j = 0; j < E; ++j) {
+        const V p = shfl_xor_c(v[j], m);
+        v[j] = hi ? csub(p, v[j]) : cadd(v[j], p);
+      }
+    } else {
+      const V w = __ldg(&tw[(q & (m - 1)) * (L / (2 * m))]);
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const V p = shfl_xor_c(v[j], m);
+        v[j] = hi ? csub(p, cmulc(v[j], w)) : cadd(v[j], cmulc(p, w));
+      }
     }
   }
 #pragma unroll
@@ -112,7 +204,8 @@ __device__ __forceinline__ void wfft_inv(cx<T> *v, cx<T> *wsm, const cx<T> *__re
   __syncwarp();
 #pragma unroll
   for (int kk = 1; kk < E; ++kk) v[kk] = cmulc(v[kk], __ldg(&tw[t * kk]));
-  dftR<E, true>(v);
+  if (HALFOUT) dft_halfout<E, true>(v);
+  else dftR<E, true>(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -130,17 +223,29 @@ struct FPass {
 };
 
 struct FastGeo {
-  int S;        // planes per ring slot
-  int nslot;    // ring slots
-  int nfmax;    // fields per slot
+  int S;      // planes per ring slot
+  int nslot;  // ring slots
+  int nfmax;  // fields per slot
 };
 
 template <int E> __host__ __device__ constexpr int fast_wsm_elems() { return 8 * E * 33; }
 
+// tiles of the YZ passes (the device decoders below use the same geometry)
+#define SF_YF_ROWS 16  // z rows per YF tile
+#define SF_ZS_ROWS 8   // ky rows per ZS tile (one per warp)
+#define SF_YI_COLS 16  // z columns per YI tile
+template <typename T> __host__ __device__ inline int fast_tiles_yf(const Prob<T> &Q, int nkx) {
+  return Q.nin * nkx * cdiv(Q.nuz, SF_YF_ROWS);
+}
+__host__ __device__ inline int fast_tiles_zs(int nkx, int L) { return nkx * (L / SF_ZS_ROWS); }
+template <typename T> __host__ __device__ inline int fast_tiles_yi(const Prob<T> &Q, int nkx) {
+  return Q.nout * nkx * cdiv(Q.nuz, SF_YI_COLS);
+}
+
 // ---------------------------------------------------------------------------
 // XFWD: 16 source lines (8 packed pairs, one per warp) -> A[c][kx][z][y]
 // ---------------------------------------------------------------------------
-template <int E>
+template <int E, bool PAD>
 __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs, IOArgs<float> io) {
   typedef cx<float> V;
   constexpr int L = 32 * E;
@@ -162,6 +267,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs
   const int c = rest / nuz;
   const int y0 = iy * 16;
   const int la = y0 + 2 * warp, lb = la + 1;
+  if (c >= P.nin) return;
   const float *src = P.in_ptr[c];
   V v[E];
   {
@@ -171,14 +277,14 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs
     for (int r = 0; r < E; ++r) {
       const int pos = t + 32 * r;
       float a = 0.f, b = 0.f;
-      if (src && pos < nux) {
+      if ((!PAD || r < E / 2) && src && pos < nux) {
         if (la < nuy) a = __ldcs(&src[rowa + pos]);
         if (lb < nuy) b = __ldcs(&src[rowb + pos]);
       }
       v[r] = mk<V>(a, b);
     }
   }
-  wfft_fwd<float, E>(v, wsm, X.tw);
+  wfft_fwd<float, E, PAD>(v, wsm, X.tw);
   // natural order in the warp buffer (one pad slot per 32) for the Hermitian split
 #pragma unroll
   for (int j = 0; j < E; ++j) {
@@ -207,7 +313,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs
 // ---------------------------------------------------------------------------
 // XINV: B[f][kx][z][y0..y0+16) -> 16 result lines along x
 // ---------------------------------------------------------------------------
-template <int E>
+template <int E, bool PAD>
 __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *probs, IOArgs<float> io) {
   typedef cx<float> V;
   constexpr int L = 32 * E;
@@ -228,6 +334,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *prob
   const int qz = rest % nuz;
   const int f = rest / nuz;
   const int y0 = iy * 16;
+  if (f >= P.nout) return;
   const V *in = reinterpret_cast<const V *>(P.B);
   const size_t plane = (size_t)nuz * nuy;
   const int half = L / 2;
@@ -255,13 +362,13 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *prob
       v[j] = mk<V>(A.x + B.y, B.x - A.y);
     }
   }
-  wfft_inv<float, E>(v, wsm, X.tw);
+  wfft_inv<float, E, PAD>(v, wsm, X.tw);
   const int la = y0 + 2 * warp, lb = la + 1;
   float *dst = P.out_ptr[f];
   const size_t rowa = ((size_t)qz * Y.nodes + la) * X.nodes;
   const size_t rowb = rowa + X.nodes;
 #pragma unroll
-  for (int r = 0; r < E; ++r) {
+  for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
     const int pos = t + 32 * r;
     if (pos < nux) {
       if (la < nuy) __stcs(&dst[rowa + pos], v[r].x);
@@ -274,19 +381,21 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *prob
 // YZ tiles
 // ---------------------------------------------------------------------------
 // YF: 16 rows (consecutive z, fixed c and kx) of A along y -> I1 slot [c][kxl][ky][z]
-template <int E>
-__device__ void fast_yf(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile, cx<float> *wsm, cx<float> *T) {
+template <int E, bool PAD>
+__device__ __forceinline__ void fast_yf(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
+                                        cx<float> *wsm, cx<float> *T) {
   typedef cx<float> V;
   constexpr int L = 32 * E;
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   const int nuy = P.nuy, nuz = P.nuz, nsx = P.nsx;
-  const int tz = cdiv(nuz, 16);
+  const int tz = cdiv(nuz, SF_YF_ROWS);
   const int iz = tile % tz;
   const int rest = tile / tz;
   const int kxl = rest % ps.nkx;
   const int c = rest / ps.nkx;
   const int kx = ps.kx0 + kxl;
-  const int z0 = iz * 16;
+  const int z0 = iz * SF_YF_ROWS;
+  if (c >= P.nin) return;  // tile outside the pass (uniform over the block)
   const V *A = reinterpret_cast<const V *>(P.A);
 #pragma unroll 1
   for (int h = 0; h < 2; ++h) {
@@ -297,9 +406,9 @@ __device__ void fast_yf(const Prob<float> &P, const FastGeo &g, const FPass &ps,
 #pragma unroll
     for (int r = 0; r < E; ++r) {
       const int pos = t + 32 * r;
-      v[r] = (z < nuz && pos < nuy) ? __ldcs(&src[pos]) : czero<V>();
+      v[r] = ((!PAD || r < E / 2) && z < nuz && pos < nuy) ? __ldcs(&src[pos]) : czero<V>();
     }
-    wfft_fwd<float, E>(v, wsm, P.ax[1].tw);
+    wfft_fwd<float, E, PAD>(v, wsm, P.ax[1].tw);
 #pragma unroll
     for (int j = 0; j < E; ++j) T[klayout<E>(t, j) * 17 + row] = v[j];
   }
@@ -313,120 +422,172 @@ __device__ void fast_yf(const Prob<float> &P, const FastGeo &g, const FPass &ps,
   }
 }
 
-// ZS: 8 rows (consecutive ky, fixed kx) of I1 along z: forward, multiply, operator, inverse -> I2 slot
-template <int E>
-__device__ void fast_zs(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile, cx<float> *wsm, cx<float> *T) {
+// multiplier of the fast path: Green's table in [kx][ky'][kz'] order (kz fastest) or eigenvalue sum
+__device__ __forceinline__ float fast_mult(const Prob<float> &P, int kx, int ky, int kz) {
+  if (P.green) {
+    const int L = P.ax[2].L;
+    const int kyf = min(ky, P.ax[1].L - ky);
+    const int kzf = min(kz, L - kz);
+    return __ldg(&P.ghat_t[((size_t)kx * P.gny + kyf) * P.gnz + kzf]);
+  }
+  return multiplier<float>(P, kx, ky, kz);
+}
+
+// coefficient of component c in operator output o at wavenumber (kx, ky, kz):
+//   sign * i * kappa_axis   (first derivatives),  or  -|kappa|^2  (Laplacian)
+__device__ __forceinline__ cx<float> op_coef(const Prob<float> &P, int o, int c, float kx, float ky, float kz, float k2) {
+  const int code = P.opc[o][c];  // 0: none, +-1: +-i kappa_axis, 2: -|kappa|^2
+  if (code == 0) return czero<cx<float>>();
+  if (code == 2) return mk<cx<float>>(-k2, 0.f);
+  const int ax = P.opa[o][c];
+  const float kk = ax == 0 ? kx : (ax == 1 ? ky : kz);
+  return mk<cx<float>>(0.f, code > 0 ? kk : -kk);
+}
+
+// ZS: 8 rows (consecutive ky, fixed kx) of I1 along z: forward, multiply,
+// operator, inverse -> I2 rows.  Templated on the component count so that the
+// spectra stay in registers; no block-wide synchronisation.
+template <int E, int NC, bool PAD>
+__device__ __forceinline__ void fast_zs(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
+                                        cx<float> *wsm) {
   typedef cx<float> V;
   constexpr int L = 32 * E;
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   const int nuz = P.nuz;
-  const int nty = L / 8;
+  const int nty = L / SF_ZS_ROWS;
   const int iy = tile % nty;
   const int kxl = tile / nty;
   const int kx = ps.kx0 + kxl;
-  const int ky0 = iy * 8;
-  const int ky = ky0 + warp;
-  const int ncomp = P.ncomp, nop = P.nop;
-  const size_t slotI1 = (size_t)ps.slot * g.nfmax * g.S * L * nuz;
-  const V *I1 = reinterpret_cast<const V *>(P.I1) + slotI1;
-  V *I2 = reinterpret_cast<V *>(P.I2) + slotI1;
-  const Axis<float> &Z = P.ax[2];
-  auto load_fwd = [&](int field, V *v) {
-    const V *src = I1 + (((size_t)field * g.S + kxl) * L + ky) * nuz;
+  const int ky = iy * SF_ZS_ROWS + warp;
+  if (kxl >= ps.nkx) return;
+  const int nop = P.nop;
+  const size_t slot = (size_t)ps.slot * g.nfmax * g.S * L * nuz;
+  const V *I1 = reinterpret_cast<const V *>(P.I1) + slot;
+  V *I2 = reinterpret_cast<V *>(P.I2) + slot;
+  const V *tz = P.ax[2].tw;
+  V sp[NC][E];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const V *src = I1 + (((size_t)c * g.S + kxl) * L + ky) * nuz;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
       const int pos = t + 32 * r;
-      v[r] = pos < nuz ? __ldcg(&src[pos]) : czero<V>();
+      sp[c][r] = ((!PAD || r < E / 2) && pos < nuz) ? __ldcg(&src[pos]) : czero<V>();
     }
-    wfft_fwd<float, E>(v, wsm, Z.tw);
-  };
-  auto inv_store = [&](int field, V *v) {
-    wfft_inv<float, E>(v, wsm, Z.tw);
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int z = t + 32 * r;
-      if (z < nuz) T[z * 9 + warp] = v[r];
-    }
-    __syncthreads();
-    V *dst = I2 + (((size_t)field * g.S + kxl) * nuz) * L + ky0;
-    const int cnt = nuz * 8;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int l = e & 7, z = e >> 3;
-      __stcg(&dst[(size_t)z * L + l], T[z * 9 + l]);
-    }
-    __syncthreads();
-  };
-  V ps_[3][E];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    if (c < ncomp) load_fwd(c, ps_[c]);
-  if (P.adjoint && nop) {
+    wfft_fwd<float, E, PAD>(sp[c], wsm, tz);
+  }
+  const bool hasop = nop > 0;
+  const float kxv = hasop ? __ldg(&P.ax[0].kap[kx]) : 0.f;
+  const float kyv = hasop ? __ldg(&P.ax[1].kap[ky]) : 0.f;
+  const float k2xy = hasop ? __ldg(&P.ax[0].kap2[kx]) + __ldg(&P.ax[1].kap2[ky]) : 0.f;
+  if (P.adjoint) {
     for (int o = 0; o < nop; ++o) {
       V gv[E];
-      load_fwd(ncomp + o, gv);
+      const V *src = I1 + (((size_t)(NC + o) * g.S + kxl) * L + ky) * nuz;
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        const int pos = t + 32 * r;
+        gv[r] = ((!PAD || r < E / 2) && pos < nuz) ? __ldcg(&src[pos]) : czero<V>();
+      }
+      wfft_fwd<float, E, PAD>(gv, wsm, tz);
 #pragma unroll
       for (int j = 0; j < E; ++j) {
-        const Kap<float> kk = kappa<float>(P, kx, ky, klayout<E>(t, j));
-        for (int c = 0; c < 3; ++c)
-          if (c < ncomp) ps_[c][j] = cadd(ps_[c][j], op_adjoint<float>(P.op, 3, o, c, kk, gv[j]));
+        const int kz = klayout<E>(t, j);
+        const float kzv = __ldg(&P.ax[2].kap[kz]);
+        const float k2 = k2xy + __ldg(&P.ax[2].kap2[kz]);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)  // conjugate transpose of the operator
+          sp[c][j] = cadd(sp[c][j], cmulc(gv[j], op_coef(P, o, c, kxv, kyv, kzv, k2)));
       }
     }
   }
 #pragma unroll
   for (int j = 0; j < E; ++j) {
-    const float m = multiplier<float>(P, kx, ky, klayout<E>(t, j));
-    for (int c = 0; c < 3; ++c)
-      if (c < ncomp) ps_[c][j] = cscale(ps_[c][j], m);
+    const float m = fast_mult(P, kx, ky, klayout<E>(t, j));
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sp[c][j] = cscale(sp[c][j], m);
   }
   if (!P.adjoint) {
     for (int o = 0; o < nop; ++o) {
       V u[E];
 #pragma unroll
       for (int j = 0; j < E; ++j) {
-        const Kap<float> kk = kappa<float>(P, kx, ky, klayout<E>(t, j));
-        V pv[3];
-        for (int c = 0; c < 3; ++c) pv[c] = c < ncomp ? ps_[c][j] : czero<V>();
-        u[j] = op_forward<float>(P.op, 3, o, kk, pv);
+        const int kz = klayout<E>(t, j);
+        const float kzv = __ldg(&P.ax[2].kap[kz]);
+        const float k2 = k2xy + __ldg(&P.ax[2].kap2[kz]);
+        V acc = czero<V>();
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc = cadd(acc, cmul(sp[c][j], op_coef(P, o, c, kxv, kyv, kzv, k2)));
+        u[j] = acc;
       }
-      inv_store(ncomp + o, u);
+      wfft_inv<float, E, PAD>(u, wsm, tz);
+      V *dst = I2 + (((size_t)(NC + o) * g.S + kxl) * L + ky) * nuz;
+#pragma unroll
+      for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
+        const int z = t + 32 * r;
+        if (z < nuz) __stcg(&dst[z], u[r]);
+      }
     }
   }
-  for (int c = 0; c < 3; ++c)
-    if (c < ncomp) inv_store(c, ps_[c]);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    wfft_inv<float, E, PAD>(sp[c], wsm, tz);
+    V *dst = I2 + (((size_t)c * g.S + kxl) * L + ky) * nuz;
+#pragma unroll
+    for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
+      const int z = t + 32 * r;
+      if (z < nuz) __stcg(&dst[z], sp[c][r]);
+    }
+  }
 }
 
-// YI: 8 rows (consecutive z, fixed f and kx) of I2 along ky -> B rows along y
-template <int E>
-__device__ void fast_yi(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile, cx<float> *wsm) {
+// YI: 16 z-columns (fixed f and kx) of I2 [f][kxl][ky][z], transposed through
+// shared memory, inverse y transform per column -> B rows along y
+template <int E, bool PAD>
+__device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
+                                        cx<float> *wsm, cx<float> *T) {
   typedef cx<float> V;
   constexpr int L = 32 * E;
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   const int nuy = P.nuy, nuz = P.nuz, nsx = P.nsx;
-  const int tz = cdiv(nuz, 8);
+  const int tz = cdiv(nuz, SF_YI_COLS);
   const int iz = tile % tz;
   const int rest = tile / tz;
   const int kxl = rest % ps.nkx;
   const int f = rest / ps.nkx;
   const int kx = ps.kx0 + kxl;
-  const int z = iz * 8 + warp;
-  if (z >= nuz) return;
+  const int z0 = iz * SF_YI_COLS;
+  if (f >= P.nout) return;
   const size_t slot = (size_t)ps.slot * g.nfmax * g.S * L * nuz;
-  const V *src = reinterpret_cast<const V *>(P.I2) + slot + (((size_t)f * g.S + kxl) * nuz + z) * L;
-  V v[E];
+  const V *src = reinterpret_cast<const V *>(P.I2) + slot + (((size_t)f * g.S + kxl) * L) * nuz + z0;
+  const int cnt = L * 16;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int l = e & 15, ky = e >> 4;
+    T[ky * 17 + l] = (z0 + l < nuz) ? __ldcg(&src[(size_t)ky * nuz + l]) : czero<V>();
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int col = 2 * warp + h;
+    const int z = z0 + col;
+    V v[E];
 #pragma unroll
-  for (int j = 0; j < E; ++j) v[j] = __ldcg(&src[klayout<E>(t, j)]);
-  wfft_inv<float, E>(v, wsm, P.ax[1].tw);
-  V *dst = reinterpret_cast<V *>(P.B) + (((size_t)f * nsx + kx) * nuz + z) * nuy;
+    for (int j = 0; j < E; ++j) v[j] = T[klayout<E>(t, j) * 17 + col];
+    wfft_inv<float, E, PAD>(v, wsm, P.ax[1].tw);
+    if (z < nuz) {
+      V *dst = reinterpret_cast<V *>(P.B) + (((size_t)f * nsx + kx) * nuz + z) * nuy;
 #pragma unroll
-  for (int r = 0; r < E; ++r) {
-    const int y = t + 32 * r;
-    if (y < nuy) dst[y] = v[r];
+      for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
+        const int y = t + 32 * r;
+        if (y < nuy) __stcs(&dst[y], v[r]);
+      }
+    }
   }
 }
 
 // persistent YZ executor over the slab work list (same queue / bounded-wait
 // protocol as k_exec)
-template <int E>
+template <int E, int NC, bool PAD>
 __global__ void __launch_bounds__(SF_FAST_THREADS)
     k_fyz(const Prob<float> *probs, FastGeo g, const FPass *passes, const int *pass_start, int npass, unsigned *done,
           ExecCtl *ctl, unsigned *sticky, unsigned long long timeout_ns, IOArgs<float> io) {
@@ -478,11 +639,10 @@ __global__ void __launch_bounds__(SF_FAST_THREADS)
     if (it >= total) break;
     if (s_ok) {
       const int tile = it - pass_start[s_pass];
-      switch (sPass.kind) {
-        case FK_YF: fast_yf<E>(sP, g, sPass, tile, wsm, T); break;
-        case FK_ZS: fast_zs<E>(sP, g, sPass, tile, wsm, T); break;
-        default: fast_yi<E>(sP, g, sPass, tile, wsm); break;
-      }
+      const int kind = sPass.kind;
+      if (kind == FK_YF) fast_yf<E, PAD>(sP, g, sPass, tile, wsm, T);
+      else if (kind == FK_ZS) fast_zs<E, NC, PAD>(sP, g, sPass, tile, wsm);
+      else fast_yi<E, PAD>(sP, g, sPass, tile, wsm, T);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -490,6 +650,84 @@ __global__ void __launch_bounds__(SF_FAST_THREADS)
       atomicAdd(&done[s_pass], 1u);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// host side: launch of the three fast-path kernels (one instantiation per E)
+// ---------------------------------------------------------------------------
+struct FastLaunch {
+  const Prob<float> *d_prob;
+  const Prob<float> *h_prob;
+  FastGeo geo;
+  const FPass *d_passes;
+  const int *d_start;
+  unsigned *d_done;
+  int npass, total;
+  ExecCtl *ctl;
+  unsigned *sticky;
+  unsigned long long timeout_ns;
+  bool front, back;
+  cudaStream_t stream;
+};
+
+// defined in sf_fast8.cu / sf_fast16.cu; return a cudaError_t value
+int sf_fast_launch_e8(const FastLaunch &fl, const IOArgs<float> &io, int *launches);
+int sf_fast_launch_e16(const FastLaunch &fl, const IOArgs<float> &io, int *launches);
+
+template <int E> size_t fast_x_smem() { return (size_t)(fast_wsm_elems<E>() + (16 * E + 1) * 17) * sizeof(float2); }
+template <int E> size_t fast_yz_smem() { return (size_t)(fast_wsm_elems<E>() + 32 * E * 17) * sizeof(float2); }
+
+template <int E, int NC, bool PAD> int fast_launch_yz(const FastLaunch &fl, const IOArgs<float> &io) {
+  static bool attr = false;
+  const size_t smyz = fast_yz_smem<E>();
+  cudaError_t e;
+  if (!attr) {
+    e = cudaFuncSetAttribute(k_fyz<E, NC, PAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smyz);
+    if (e != cudaSuccess) return (int)e;
+    attr = true;
+  }
+  int dev = 0, nsm = 0, per = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fyz<E, NC, PAD>, SF_FAST_THREADS, smyz)) != cudaSuccess)
+    return (int)e;
+  if (per < 1) return (int)cudaErrorLaunchOutOfResources;
+  const int grid = fl.total < nsm * per ? fl.total : nsm * per;
+  k_fyz<E, NC, PAD><<<grid, SF_FAST_THREADS, smyz, fl.stream>>>(fl.d_prob, fl.geo, fl.d_passes, fl.d_start, fl.npass,
+                                                              fl.d_done, fl.ctl, fl.sticky, fl.timeout_ns, io);
+  return (int)cudaGetLastError();
+}
+
+template <int E, bool PAD> int fast_launch_all(const FastLaunch &fl, const IOArgs<float> &io, int *launches) {
+  const Prob<float> &Q = *fl.h_prob;
+  const size_t smx = fast_x_smem<E>();
+  static bool attr = false;
+  cudaError_t e;
+  if (!attr) {
+    if ((e = cudaFuncSetAttribute(k_fx<E, PAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess)
+      return (int)e;
+    if ((e = cudaFuncSetAttribute(k_fxi<E, PAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess)
+      return (int)e;
+    attr = true;
+  }
+  if (fl.front) {
+    k_fx<E, PAD><<<Q.nin * Q.nuz * cdiv(Q.nuy, 16), SF_FAST_THREADS, smx, fl.stream>>>(fl.d_prob, io);
+    if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    if ((e = cudaMemsetAsync(fl.d_done, 0, fl.npass * sizeof(unsigned), fl.stream)) != cudaSuccess) return (int)e;
+    if ((e = cudaMemsetAsync(fl.ctl, 0, sizeof(ExecCtl), fl.stream)) != cudaSuccess) return (int)e;
+    int r;
+    if (Q.ncomp == 3) r = fast_launch_yz<E, 3, PAD>(fl, io);
+    else if (Q.ncomp == 2) r = fast_launch_yz<E, 2, PAD>(fl, io);
+    else r = fast_launch_yz<E, 1, PAD>(fl, io);
+    if (r) return r;
+    if (launches) *launches += 2;
+  }
+  if (fl.back) {
+    k_fxi<E, PAD><<<Q.nout * Q.nuz * cdiv(Q.nuy, 16), SF_FAST_THREADS, smx, fl.stream>>>(fl.d_prob, io);
+    if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    if (launches) *launches += 1;
+  }
+  return 0;
 }
 
 }  // namespace sfg

@@ -167,7 +167,7 @@ __device__ inline double sf_expint_e1(double x) {
 }
 
 // G octant [z][y][x] for offsets 0..n per axis (2D: nz = 0)
-__global__ void k_green_octant(double *out, int nx, int ny, int nz, double hx, double hy, double hz, double sigma,
+static __global__ void k_green_octant(double *out, int nx, int ny, int nz, double hx, double hy, double hz, double sigma,
                                int dim) {
   const size_t total = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
   const double pi = 3.14159265358979323846264338327950288;
@@ -188,6 +188,18 @@ __global__ void k_green_octant(double *out, int nx, int ny, int nz, double hx, d
       else g = -(log(r) + 0.5 * sf_expint_e1(r * r / (2.0 * sigma * sigma))) / (2.0 * pi);
     }
     out[i] = g;
+  }
+}
+
+// [kx][kz][ky] -> [kx][ky][kz] (set-up only)
+template <typename T> __global__ void k_transpose_green(T *out, const T *in, int nkx, int nkz, int nky) {
+  const size_t total = (size_t)nkx * nkz * nky;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int ky = (int)(i % nky);
+    const size_t r = i / nky;
+    const int kz = (int)(r % nkz);
+    const int kx = (int)(r / nkz);
+    out[((size_t)kx * nky + ky) * nkz + kz] = in[i];
   }
 }
 

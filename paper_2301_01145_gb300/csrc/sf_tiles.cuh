@@ -198,6 +198,7 @@ template <typename T> __device__ void tile_xfwd(const Prob<T> &P, const Pass<T> 
   const int qz = rest % nuz;
   const int c = rest / nuz;
   const int qy0 = iy * RL;
+  if (c >= P.nin) return;  // tile outside the pass (uniform over the block)
   V *a = sm, *b = sm + bufsz;
   zero_buf<T>(a, L * Wp);
   __syncthreads();
@@ -280,6 +281,7 @@ template <typename T> __device__ void tile_yfwd(const Prob<T> &P, const Pass<T> 
   const int kx = rest % nsx;
   const int c = rest / nsx;
   const int qz0 = iz * RPT;
+  if (c >= P.nin) return;
   const int nl = min(RPT, nuz - qz0);
   V *a = sm, *b = sm + bufsz;
   zero_buf<T>(a, L * Wp);
@@ -334,6 +336,7 @@ template <typename T> __device__ void tile_yinv(const Prob<T> &P, const Pass<T> 
   const int kx = rest % nsx;
   const int f = rest / nsx;
   const int qz0 = iz * RPT;
+  if (f >= P.nout) return;
   const int nl = min(RPT, nuz - qz0);
   V *a = sm, *b = sm + bufsz;
   const size_t rowbase = ((size_t)f * nsx + kx) * nuz + qz0;
@@ -526,6 +529,7 @@ template <typename T> __device__ void tile_zstage(const Prob<T> &P, const Pass<T
   const int kx = t / ty;
   const int ky0 = iy * CPT;
   const int nl = min(CPT, nsy - ky0);
+  if (kx >= nsx) return;
   const size_t fstride = (size_t)nsx * nuz * nsy;  // elements per field
   const size_t base = (size_t)kx * nuz * nsy + ky0;
   auto kof = [&](int l, int k, int &kx_, int &ky_, int &kz_) {
@@ -638,6 +642,7 @@ template <typename T> __device__ void tile_xinv(const Prob<T> &P, const Pass<T> 
   const int f = rest / nuz;
   const int qy0 = iy * RL;
   const int nl = min(RL, nuy - qy0);
+  if (f >= P.nout) return;
   V *a = sm, *stg = sm + bufsz;
   const size_t plane = (size_t)nuz * nuy;
   const size_t base = (size_t)f * nsx * plane + (size_t)qz * nuy + qy0;

@@ -300,7 +300,7 @@ def lowpass_noise(shape: Tuple[int, ...], seed: int, cutoff: float = 0.25) -> np
         grids.append((k ** 2).reshape(sh))
     k2 = sum(grids)
     X = np.where(k2 <= cutoff * cutoff, X, 0.0)
-    return np.fft.irfftn(X, s=shape)
+    return np.fft.irfftn(X, s=shape, axes=tuple(range(len(shape))))
 
 
 def random_field(shape: Tuple[int, ...], seed: int) -> np.ndarray:
