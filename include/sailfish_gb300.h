@@ -193,6 +193,15 @@ sf_status sf_sync(sf_plan p);
 /* Kernel launches one sf_execute / sf_batch_solve enqueues (for accounting). */
 int sf_plan_launches(sf_plan p);
 
+/* Tracing of the last persistent-executor launch of a plan (waits for the
+ * plan's stream).  For each of up to 8 pass kinds k (register path: 0 = y
+ * forward, 1 = z stage, 2 = y inverse; general engine: the pass kind of the
+ * tile): out[3k] = summed tile time (ns, over all CTAs), out[3k+1] = summed
+ * time spent waiting for dependencies (ns), out[3k+2] = tiles.  out must hold
+ * 24 doubles.  The paper times the solve steps separately (Sec. 5.3); this is
+ * the per-pass breakdown of the GPU schedule. */
+sf_status sf_plan_stats(sf_plan p, double out[24]);
+
 /* Release a plan or batch and its device memory (waits for its stream). */
 sf_status sf_plan_destroy(sf_plan p);
 

@@ -16,7 +16,7 @@ from typing import Optional, Sequence
 from . import _lib
 from ._lib import SolverError  # noqa: F401
 from ._lib import (sf_batch_create, sf_batch_solve, sf_execute, sf_get_output, sf_plan_create,  # noqa: F401
-                   sf_plan_destroy, sf_plan_launches, sf_plan_query, sf_set_boundary, sf_set_source, sf_solve,
+                   sf_plan_destroy, sf_plan_launches, sf_plan_query, sf_plan_stats, sf_set_boundary, sf_set_source, sf_solve,
                    sf_solve_adjoint, sf_solve_host, sf_sync, sf_version)
 
 
@@ -94,6 +94,9 @@ class Plan:
 
     def launches(self) -> int:
         return sf_plan_launches(self.handle)
+
+    def stats(self):
+        return sf_plan_stats(self.handle)
 
     def _check_input(self, f):
         if tuple(f.shape) != tuple(self.in_shape) or f.dtype != self.dtype or not f.is_cuda or not f.is_contiguous():

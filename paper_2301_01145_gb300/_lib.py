@@ -72,6 +72,7 @@ SIGNATURES = {
     "sf_batch_solve": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p)]),
     "sf_sync": (c_int, [c_void_p]),
     "sf_plan_launches": (c_int, [c_void_p]),
+    "sf_plan_stats": (c_int, [c_void_p, POINTER(c_double)]),
     "sf_plan_destroy": (c_int, [c_void_p]),
     "sf_status_string": (c_char_p, [c_int]),
     "sf_last_error": (c_char_p, []),
@@ -210,6 +211,13 @@ def sf_sync(plan):
 
 def sf_plan_launches(plan) -> int:
     return int(load().sf_plan_launches(plan))
+
+
+def sf_plan_stats(plan):
+    """Per pass kind: (busy ns, dependency-wait ns, tiles) of the last executor launch."""
+    out = (c_double * 24)()
+    _check(load().sf_plan_stats(plan, out), "sf_plan_stats")
+    return [(out[3 * k], out[3 * k + 1], int(out[3 * k + 2])) for k in range(8)]
 
 
 def sf_plan_destroy(plan):

@@ -339,10 +339,14 @@ struct FastList {
   int total = 0;
 };
 
-// slab pipeline: YF(s), ZS(s-1), YI(s-2) per step; rings of nslot slabs for I1/I2
+// slab pipeline with stage lag D: step t issues YF(t), ZS(t-D), YI(t-2D).  The
+// I1 / I2 rings have nslot = D + 1 slabs, so a slot is rewritten only after the
+// pass that reads it was issued at least one step earlier (dependency edges
+// below); every dependency points to an earlier item of the list.
 template <typename T>
 void build_fast_list(const Prob<T> &Q, int S, int nslot, int L, FastList &fl) {
   const int nslab = cdiv(Q.nsx, S);
+  const int D = nslot > 1 ? nslot - 1 : 1;
   std::vector<int> iyf(nslab, -1), izs(nslab, -1), iyi(nslab, -1);
   auto push = [&](int kind, int s) {
     FPass p{};
@@ -369,10 +373,10 @@ void build_fast_list(const Prob<T> &Q, int S, int nslot, int L, FastList &fl) {
     else if (kind == FK_ZS) izs[s] = idx;
     else iyi[s] = idx;
   };
-  for (int step = 0; step < nslab + 2; ++step) {
+  for (int step = 0; step < nslab + 2 * D; ++step) {
     if (step < nslab) push(FK_YF, step);
-    if (step - 1 >= 0 && step - 1 < nslab) push(FK_ZS, step - 1);
-    if (step - 2 >= 0 && step - 2 < nslab) push(FK_YI, step - 2);
+    if (step - D >= 0 && step - D < nslab) push(FK_ZS, step - D);
+    if (step - 2 * D >= 0 && step - 2 * D < nslab) push(FK_YI, step - 2 * D);
   }
   fl.start.assign(fl.passes.size() + 1, 0);
   for (size_t i = 0; i < fl.passes.size(); ++i) fl.start[i + 1] = fl.start[i] + fl.passes[i].ntiles;
@@ -409,6 +413,7 @@ struct sf_plan_s {
   virtual sf_status query(size_t in_shape[4], size_t out_shape[4], size_t op_shape[4], size_t *ws) = 0;
   virtual sf_status set_face(int axis, int side, const void *p) = 0;
   virtual sf_status host_solve(const void *hf, void *hpsi, void *hop) = 0;
+  virtual ExecCtl *exec_ctl() = 0;
   const void *src = nullptr;
   bool solved = false;
 };
@@ -512,6 +517,8 @@ template <typename T> struct PlanImpl : sf_plan_s {
     faces[axis][side] = (const T *)p;
     return SF_OK;
   }
+
+  ExecCtl *exec_ctl() override { return ctl; }
 
   sf_status host_solve(const void *hf, void *hpsi, void *hop) override {
     const size_t fb = field_elems * sizeof(T);
@@ -723,10 +730,13 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
       p.ax[1].L == p.ax[2].L && (p.ax[0].L == 512 || p.ax[0].L == 256)) {
     fastE = p.ax[0].L / 32;
     const char *env = getenv("SF_SLAB_PLANES");
-    int S = env ? atoi(env) : 2;
+    int S = env ? atoi(env) : 4;
     if (S < 1) S = 1;
+    const char *envl = getenv("SF_SLAB_LAG");
+    int lag = envl ? atoi(envl) : 1;
+    if (lag < 1) lag = 1;
     geo.S = fused() ? std::min(S, p.nsx) : p.nsx;
-    geo.nslot = fused() ? 2 : 1;
+    geo.nslot = fused() ? lag + 1 : 1;
     geo.nfmax = nf;
     eI = (size_t)geo.nslot * nf * geo.S * p.ax[1].L * p.nuz;
   }
@@ -1010,6 +1020,7 @@ template <typename T> struct BatchImpl : sf_plan_s {
   }
   sf_status query(size_t *, size_t *, size_t *, size_t *) override { return fail(SF_ERR_STATE, "query a member plan"); }
   sf_status set_face(int, int, const void *) override { return fail(SF_ERR_STATE, "not available on a batch"); }
+  ExecCtl *exec_ctl() override { return ctl; }
   sf_status host_solve(const void *, void *, void *) override { return fail(SF_ERR_STATE, "not available on a batch"); }
 };
 
@@ -1169,6 +1180,19 @@ sf_status sf_sync(sf_plan p) {
 }
 
 int sf_plan_launches(sf_plan p) { return p ? p->launches_per_exec : 0; }
+
+sf_status sf_plan_stats(sf_plan p, double out[24]) {
+  if (!p || !out) return fail(SF_ERR_ARG, "null argument");
+  SF_CK(cudaStreamSynchronize(p->stream));
+  ExecCtl c;
+  SF_CK(cudaMemcpy(&c, p->exec_ctl(), sizeof(ExecCtl), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 8; ++k) {
+    out[3 * k] = (double)c.busy_ns[k];
+    out[3 * k + 1] = (double)c.wait_ns[k];
+    out[3 * k + 2] = (double)c.tiles[k];
+  }
+  return SF_OK;
+}
 
 sf_status sf_plan_destroy(sf_plan p) {
   if (!p) return SF_OK;

@@ -241,6 +241,10 @@ struct ExecCtl {
   unsigned int error;     // SF_ERR_* code of the first failure (0 = ok)
   unsigned int err_pass;  // pass that timed out
   unsigned int pad;
+  // tracing: per pass kind (index = kind, up to 8 kinds), summed over CTAs, nanoseconds
+  unsigned long long busy_ns[8];  // time between the start and the end of a tile
+  unsigned long long wait_ns[8];  // time spent waiting for dependencies before a tile
+  unsigned long long tiles[8];
 };
 
 // ---------------------------------------------------------------------------

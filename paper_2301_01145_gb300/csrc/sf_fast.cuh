@@ -130,82 +130,111 @@ template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfo
 }
 
 // ---- warp FFTs -------------------------------------------------------------
-template <typename T, int E, bool HALFIN>
-__device__ __forceinline__ void wfft_fwd(cx<T> *v, cx<T> *wsm, const cx<T> *__restrict__ tw) {
+// M independent lines per warp, interleaved step by step so that their
+// dependency chains overlap (wsm: M consecutive buffers of E*33 elements).
+template <typename T, int E, bool HALFIN, int M>
+__device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const cx<T> *__restrict__ tw) {
   typedef cx<T> V;
   constexpr int L = 32 * E, G = 32 / E;
   const int t = threadIdx.x & 31;
-  if (HALFIN) dft_halfin<E, false>(v);
-  else dftR<E, false>(v);
 #pragma unroll
-  for (int k1 = 1; k1 < E; ++k1) v[k1] = cmul(v[k1], __ldg(&tw[t * k1]));
+  for (int m = 0; m < M; ++m) {
+    if (HALFIN) dft_halfin<E, false>(v[m]);
+    else dftR<E, false>(v[m]);
+  }
 #pragma unroll
-  for (int k1 = 0; k1 < E; ++k1) wsm[k1 * 33 + t] = v[k1];
+  for (int k1 = 1; k1 < E; ++k1) {
+    const V w = __ldg(&tw[t * k1]);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m][k1] = cmul(v[m][k1], w);
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) wsm[m * E * 33 + k1 * 33 + t] = v[m][k1];
   __syncwarp();
   const int k1 = t / G, q = t % G;
 #pragma unroll
-  for (int s = 0; s < E; ++s) v[s] = wsm[k1 * 33 + G * s + q];
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[m][s] = wsm[m * E * 33 + k1 * 33 + G * s + q];
   __syncwarp();
-  dftR<E, false>(v);
 #pragma unroll
-  for (int j = 1; j < E; ++j) v[j] = cmul(v[j], __ldg(&tw[q * j * E]));
+  for (int m = 0; m < M; ++m) dftR<E, false>(v[m]);
 #pragma unroll
-  for (int m = G / 2; m >= 1; m >>= 1) {
-    const bool hi = (q & m) != 0;
-    if (m == 1) {  // twiddle W_2^0 = 1
+  for (int j = 1; j < E; ++j) {
+    const V w = __ldg(&tw[q * j * E]);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m][j] = cmul(v[m][j], w);
+  }
+#pragma unroll
+  for (int mm = G / 2; mm >= 1; mm >>= 1) {
+    const float sg = (q & mm) ? -1.f : 1.f;  // hi lane: partner - mine, lo lane: mine + partner
+    const V w = __ldg(&tw[(q & (mm - 1)) * (L / (2 * mm))]);
+#pragma unroll
+    for (int m = 0; m < M; ++m)
 #pragma unroll
       for (int j = 0; j < E; ++j) {
-        const V p = shfl_xor_c(v[j], m);
-        v[j] = hi ? csub(p, v[j]) : cadd(v[j], p);
+        const V p = shfl_xor_c(v[m][j], mm);
+        V r = mk<V>(fmaf(sg, v[m][j].x, p.x), fmaf(sg, v[m][j].y, p.y));
+        if (mm > 1 && (q & mm)) r = cmul(r, w);
+        v[m][j] = r;
       }
-    } else {
-      const V w = __ldg(&tw[(q & (m - 1)) * (L / (2 * m))]);
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const V p = shfl_xor_c(v[j], m);
-        v[j] = hi ? cmul(csub(p, v[j]), w) : cadd(v[j], p);
-      }
-    }
   }
 }
 
-template <typename T, int E, bool HALFOUT>
-__device__ __forceinline__ void wfft_inv(cx<T> *v, cx<T> *wsm, const cx<T> *__restrict__ tw) {
+template <typename T, int E, bool HALFOUT, int M>
+__device__ __forceinline__ void wfft_inv_m(cx<T> (&v)[M][E], cx<T> *wsm, const cx<T> *__restrict__ tw) {
   typedef cx<T> V;
   constexpr int L = 32 * E, G = 32 / E;
   const int t = threadIdx.x & 31;
   const int k1 = t / G, q = t % G;
 #pragma unroll
-  for (int m = 1; m < G; m <<= 1) {
-    const bool hi = (q & m) != 0;
-    if (m == 1) {
+  for (int mm = 1; mm < G; mm <<= 1) {
+    const bool hi = (q & mm) != 0;
+    const float sg = hi ? -1.f : 1.f;
+    const V w = __ldg(&tw[(q & (mm - 1)) * (L / (2 * mm))]);
+#pragma unroll
+    for (int m = 0; m < M; ++m)
 #pragma unroll
       for (int j = 0; j < E; ++j) {
-        const V p = shfl_xor_c(v[j], m);
-        v[j] = hi ? csub(p, v[j]) : cadd(v[j], p);
+        // pair (a = lo value, b = hi value): lo <- a + conj(w) b, hi <- a - conj(w) b.
+        // The hi lane twiddles its own value before the exchange.
+        V mine = v[m][j];
+        if (mm > 1 && hi) mine = cmulc(mine, w);
+        const V p = shfl_xor_c(mine, mm);
+        v[m][j] = mk<V>(fmaf(sg, mine.x, p.x), fmaf(sg, mine.y, p.y));  // hi: p - mine, lo: p + mine
       }
-    } else {
-      const V w = __ldg(&tw[(q & (m - 1)) * (L / (2 * m))]);
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const V p = shfl_xor_c(v[j], m);
-        v[j] = hi ? csub(p, cmulc(v[j], w)) : cadd(v[j], cmulc(p, w));
-      }
-    }
   }
 #pragma unroll
-  for (int j = 1; j < E; ++j) v[j] = cmulc(v[j], __ldg(&tw[q * j * E]));
-  dftR<E, true>(v);
+  for (int j = 1; j < E; ++j) {
+    const V w = __ldg(&tw[q * j * E]);
 #pragma unroll
-  for (int s = 0; s < E; ++s) wsm[k1 * 33 + G * s + q] = v[s];
+    for (int m = 0; m < M; ++m) v[m][j] = cmulc(v[m][j], w);
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) dftR<E, true>(v[m]);
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int s = 0; s < E; ++s) wsm[m * E * 33 + k1 * 33 + G * s + q] = v[m][s];
   __syncwarp();
 #pragma unroll
-  for (int kk = 0; kk < E; ++kk) v[kk] = wsm[kk * 33 + t];
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int kk = 0; kk < E; ++kk) v[m][kk] = wsm[m * E * 33 + kk * 33 + t];
   __syncwarp();
 #pragma unroll
-  for (int kk = 1; kk < E; ++kk) v[kk] = cmulc(v[kk], __ldg(&tw[t * kk]));
-  if (HALFOUT) dft_halfout<E, true>(v);
-  else dftR<E, true>(v);
+  for (int kk = 1; kk < E; ++kk) {
+    const V w = __ldg(&tw[t * kk]);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m][kk] = cmulc(v[m][kk], w);
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    if (HALFOUT) dft_halfout<E, true>(v[m]);
+    else dftR<E, true>(v[m]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -228,7 +257,8 @@ struct FastGeo {
   int nfmax;  // fields per slot
 };
 
-template <int E> __host__ __device__ constexpr int fast_wsm_elems() { return 8 * E * 33; }
+#define SF_YZ_MAXM 3  // interleaved lines per warp in the YZ executor
+template <int E, int M> __host__ __device__ constexpr int fast_wsm_elems() { return 8 * M * E * 33; }
 
 // tiles of the YZ passes (the device decoders below use the same geometry)
 #define SF_YF_ROWS 16  // z rows per YF tile
@@ -254,7 +284,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs
   load_prob<float>(sP, probs, io);
   const Prob<float> &P = sP;
   V *wsm_all = reinterpret_cast<V *>(fsm);
-  V *T = wsm_all + fast_wsm_elems<E>();
+  V *T = wsm_all + fast_wsm_elems<E, 1>();
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   V *wsm = wsm_all + warp * E * 33;
   const Axis<float> &X = P.ax[0], &Y = P.ax[1];
@@ -269,7 +299,8 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs
   const int la = y0 + 2 * warp, lb = la + 1;
   if (c >= P.nin) return;
   const float *src = P.in_ptr[c];
-  V v[E];
+  V vv[1][E];
+  V *v = vv[0];
   {
     const size_t rowa = ((size_t)qz * Y.nodes + la) * X.nodes;
     const size_t rowb = rowa + X.nodes;
@@ -284,7 +315,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs
       v[r] = mk<V>(a, b);
     }
   }
-  wfft_fwd<float, E, PAD>(v, wsm, X.tw);
+  wfft_fwd_m<float, E, PAD, 1>(vv, wsm, X.tw);
   // natural order in the warp buffer (one pad slot per 32) for the Hermitian split
 #pragma unroll
   for (int j = 0; j < E; ++j) {
@@ -322,7 +353,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *prob
   load_prob<float>(sP, probs, io);
   const Prob<float> &P = sP;
   V *wsm_all = reinterpret_cast<V *>(fsm);
-  V *T = wsm_all + fast_wsm_elems<E>();
+  V *T = wsm_all + fast_wsm_elems<E, 1>();
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   V *wsm = wsm_all + warp * E * 33;
   const Axis<float> &X = P.ax[0], &Y = P.ax[1];
@@ -338,14 +369,26 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *prob
   const V *in = reinterpret_cast<const V *>(P.B);
   const size_t plane = (size_t)nuz * nuy;
   const int half = L / 2;
-  const int cnt = (half + 1) * 16;
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const int l = e & 15, kx = e >> 4;
-    T[kx * 17 + l] = (y0 + l < nuy) ? __ldcs(&in[((size_t)f * nsx + kx) * plane + (size_t)qz * nuy + y0 + l])
-                                    : czero<V>();
+  {
+    constexpr int CNT = (16 * E + 1) * 16;
+    constexpr int PER = (CNT + SF_FAST_THREADS - 1) / SF_FAST_THREADS;
+    V tmp[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + i * SF_FAST_THREADS;
+      const int l = e & 15, kx = e >> 4;
+      tmp[i] = (e < CNT && y0 + l < nuy) ? __ldcs(&in[((size_t)f * nsx + kx) * plane + (size_t)qz * nuy + y0 + l])
+                                         : czero<V>();
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + i * SF_FAST_THREADS;
+      if (e < CNT) T[(e >> 4) * 17 + (e & 15)] = tmp[i];
+    }
   }
   __syncthreads();
-  V v[E];
+  V vv[1][E];
+  V *v = vv[0];
 #pragma unroll
   for (int j = 0; j < E; ++j) {
     const int k = klayout<E>(t, j);
@@ -362,7 +405,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *prob
       v[j] = mk<V>(A.x + B.y, B.x - A.y);
     }
   }
-  wfft_inv<float, E, PAD>(v, wsm, X.tw);
+  wfft_inv_m<float, E, PAD, 1>(vv, wsm, X.tw);
   const int la = y0 + 2 * warp, lb = la + 1;
   float *dst = P.out_ptr[f];
   const size_t rowa = ((size_t)qz * Y.nodes + la) * X.nodes;
@@ -397,21 +440,22 @@ __device__ __forceinline__ void fast_yf(const Prob<float> &P, const FastGeo &g, 
   const int z0 = iz * SF_YF_ROWS;
   if (c >= P.nin) return;  // tile outside the pass (uniform over the block)
   const V *A = reinterpret_cast<const V *>(P.A);
-#pragma unroll 1
+  V v[2][E];
+#pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const int row = 2 * warp + h;
-    const int z = z0 + row;
-    V v[E];
+    const int z = z0 + 2 * warp + h;
     const V *src = A + (((size_t)c * nsx + kx) * nuz + z) * nuy;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
       const int pos = t + 32 * r;
-      v[r] = ((!PAD || r < E / 2) && z < nuz && pos < nuy) ? __ldcs(&src[pos]) : czero<V>();
+      v[h][r] = ((!PAD || r < E / 2) && z < nuz && pos < nuy) ? __ldcs(&src[pos]) : czero<V>();
     }
-    wfft_fwd<float, E, PAD>(v, wsm, P.ax[1].tw);
-#pragma unroll
-    for (int j = 0; j < E; ++j) T[klayout<E>(t, j) * 17 + row] = v[j];
   }
+  wfft_fwd_m<float, E, PAD, 2>(v, wsm, P.ax[1].tw);
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int j = 0; j < E; ++j) T[klayout<E>(t, j) * 17 + 2 * warp + h] = v[h][j];
   __syncthreads();
   V *I1 = reinterpret_cast<V *>(P.I1) + (size_t)ps.slot * g.nfmax * g.S * L * nuz;
   const size_t base = (((size_t)c * g.S + kxl) * L) * nuz + z0;
@@ -447,7 +491,8 @@ __device__ __forceinline__ cx<float> op_coef(const Prob<float> &P, int o, int c,
 // ZS: 8 rows (consecutive ky, fixed kx) of I1 along z: forward, multiply,
 // operator, inverse -> I2 rows.  Templated on the component count so that the
 // spectra stay in registers; no block-wide synchronisation.
-template <int E, int NC, bool PAD>
+// OPS = 1: 3D curl written out (u = i kappa x psi); OPS = 0: coefficient table (any operator or none)
+template <int E, int NC, bool PAD, int OPS>
 __device__ __forceinline__ void fast_zs(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
                                         cx<float> *wsm) {
   typedef cx<float> V;
@@ -474,22 +519,23 @@ __device__ __forceinline__ void fast_zs(const Prob<float> &P, const FastGeo &g, 
       const int pos = t + 32 * r;
       sp[c][r] = ((!PAD || r < E / 2) && pos < nuz) ? __ldcg(&src[pos]) : czero<V>();
     }
-    wfft_fwd<float, E, PAD>(sp[c], wsm, tz);
   }
+  wfft_fwd_m<float, E, PAD, NC>(sp, wsm, tz);
   const bool hasop = nop > 0;
   const float kxv = hasop ? __ldg(&P.ax[0].kap[kx]) : 0.f;
   const float kyv = hasop ? __ldg(&P.ax[1].kap[ky]) : 0.f;
   const float k2xy = hasop ? __ldg(&P.ax[0].kap2[kx]) + __ldg(&P.ax[1].kap2[ky]) : 0.f;
   if (P.adjoint) {
     for (int o = 0; o < nop; ++o) {
-      V gv[E];
+      V gvv[1][E];
+      V *gv = gvv[0];
       const V *src = I1 + (((size_t)(NC + o) * g.S + kxl) * L + ky) * nuz;
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         const int pos = t + 32 * r;
         gv[r] = ((!PAD || r < E / 2) && pos < nuz) ? __ldcg(&src[pos]) : czero<V>();
       }
-      wfft_fwd<float, E, PAD>(gv, wsm, tz);
+      wfft_fwd_m<float, E, PAD, 1>(gvv, wsm, tz);
 #pragma unroll
       for (int j = 0; j < E; ++j) {
         const int kz = klayout<E>(t, j);
@@ -509,18 +555,32 @@ __device__ __forceinline__ void fast_zs(const Prob<float> &P, const FastGeo &g, 
   }
   if (!P.adjoint) {
     for (int o = 0; o < nop; ++o) {
-      V u[E];
+      V uu[1][E];
+      V *u = uu[0];
+      if (OPS == 1 && NC == 3) {
+        // u_o = i (kappa x psi)_o with the wavenumber pair of output o
 #pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const int kz = klayout<E>(t, j);
-        const float kzv = __ldg(&P.ax[2].kap[kz]);
-        const float k2 = k2xy + __ldg(&P.ax[2].kap2[kz]);
-        V acc = czero<V>();
+        for (int j = 0; j < E; ++j) {
+          const float kzv = __ldg(&P.ax[2].kap[klayout<E>(t, j)]);
+          V d;
+          if (o == 0) d = csub(cscale(sp[2 % NC][j], kyv), cscale(sp[1 % NC][j], kzv));
+          else if (o == 1) d = csub(cscale(sp[0][j], kzv), cscale(sp[2 % NC][j], kxv));
+          else d = csub(cscale(sp[1 % NC][j], kxv), cscale(sp[0][j], kyv));
+          u[j] = mul_i(d);
+        }
+      } else {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc = cadd(acc, cmul(sp[c][j], op_coef(P, o, c, kxv, kyv, kzv, k2)));
-        u[j] = acc;
+        for (int j = 0; j < E; ++j) {
+          const int kz = klayout<E>(t, j);
+          const float kzv = __ldg(&P.ax[2].kap[kz]);
+          const float k2 = k2xy + __ldg(&P.ax[2].kap2[kz]);
+          V acc = czero<V>();
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc = cadd(acc, cmul(sp[c][j], op_coef(P, o, c, kxv, kyv, kzv, k2)));
+          u[j] = acc;
+        }
       }
-      wfft_inv<float, E, PAD>(u, wsm, tz);
+      wfft_inv_m<float, E, PAD, 1>(uu, wsm, tz);
       V *dst = I2 + (((size_t)(NC + o) * g.S + kxl) * L + ky) * nuz;
 #pragma unroll
       for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
@@ -529,9 +589,9 @@ __device__ __forceinline__ void fast_zs(const Prob<float> &P, const FastGeo &g, 
       }
     }
   }
+  wfft_inv_m<float, E, PAD, NC>(sp, wsm, tz);
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    wfft_inv<float, E, PAD>(sp[c], wsm, tz);
     V *dst = I2 + (((size_t)c * g.S + kxl) * L + ky) * nuz;
 #pragma unroll
     for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
@@ -560,26 +620,38 @@ __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, 
   if (f >= P.nout) return;
   const size_t slot = (size_t)ps.slot * g.nfmax * g.S * L * nuz;
   const V *src = reinterpret_cast<const V *>(P.I2) + slot + (((size_t)f * g.S + kxl) * L) * nuz + z0;
-  const int cnt = L * 16;
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const int l = e & 15, ky = e >> 4;
-    T[ky * 17 + l] = (z0 + l < nuz) ? __ldcg(&src[(size_t)ky * nuz + l]) : czero<V>();
+  // L*16 elements, 2E per thread: all loads issued before any use
+  {
+    constexpr int PER = L * 16 / SF_FAST_THREADS;
+    V tmp[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + i * SF_FAST_THREADS;
+      const int l = e & 15, ky = e >> 4;
+      tmp[i] = (z0 + l < nuz) ? __ldcg(&src[(size_t)ky * nuz + l]) : czero<V>();
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + i * SF_FAST_THREADS;
+      T[(e >> 4) * 17 + (e & 15)] = tmp[i];
+    }
   }
   __syncthreads();
-#pragma unroll 1
-  for (int h = 0; h < 2; ++h) {
-    const int col = 2 * warp + h;
-    const int z = z0 + col;
-    V v[E];
+  V v[2][E];
 #pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = T[klayout<E>(t, j) * 17 + col];
-    wfft_inv<float, E, PAD>(v, wsm, P.ax[1].tw);
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[h][j] = T[klayout<E>(t, j) * 17 + 2 * warp + h];
+  wfft_inv_m<float, E, PAD, 2>(v, wsm, P.ax[1].tw);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int z = z0 + 2 * warp + h;
     if (z < nuz) {
       V *dst = reinterpret_cast<V *>(P.B) + (((size_t)f * nsx + kx) * nuz + z) * nuy;
 #pragma unroll
       for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
         const int y = t + 32 * r;
-        if (y < nuy) __stcs(&dst[y], v[r]);
+        if (y < nuy) __stcs(&dst[y], v[h][r]);
       }
     }
   }
@@ -587,7 +659,7 @@ __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, 
 
 // persistent YZ executor over the slab work list (same queue / bounded-wait
 // protocol as k_exec)
-template <int E, int NC, bool PAD>
+template <int E, int NC, bool PAD, int OPS>
 __global__ void __launch_bounds__(SF_FAST_THREADS)
     k_fyz(const Prob<float> *probs, FastGeo g, const FPass *passes, const int *pass_start, int npass, unsigned *done,
           ExecCtl *ctl, unsigned *sticky, unsigned long long timeout_ns, IOArgs<float> io) {
@@ -598,23 +670,29 @@ __global__ void __launch_bounds__(SF_FAST_THREADS)
   __shared__ int s_item, s_pass, s_ok;
   load_prob<float>(sP, probs, io);
   V *wsm_all = reinterpret_cast<V *>(fsm);
-  V *T = wsm_all + fast_wsm_elems<E>();
-  V *wsm = wsm_all + (threadIdx.x >> 5) * E * 33;
-  const int total = pass_start[npass];
+  V *T = wsm_all + fast_wsm_elems<E, SF_YZ_MAXM>();
+  V *wsm = wsm_all + (threadIdx.x >> 5) * SF_YZ_MAXM * E * 33;
+  // pass start table cached in shared memory (after the tile buffer)
+  int *s_start = reinterpret_cast<int *>(T + 32 * E * 17);
+  for (int i = threadIdx.x; i <= npass; i += blockDim.x) s_start[i] = pass_start[i];
+  __syncthreads();
+  const int total = s_start[npass];
+  int next_it = 0;  // thread 0: item claimed one iteration ahead (queue round trip overlaps a tile)
+  int cur = 0;      // thread 0: pass of the last item (items arrive in increasing order)
+  unsigned long long t_wait0 = 0, t_busy0 = 0;  // thread 0: tracing timestamps
+  if (threadIdx.x == 0) next_it = (int)atomicAdd(&ctl->next, 1u);
   for (;;) {
     if (threadIdx.x == 0) {
-      const int it = (int)atomicAdd(&ctl->next, 1u);
+      const int it = next_it;
+      if (it < total) next_it = (int)atomicAdd(&ctl->next, 1u);
       s_item = it;
       s_ok = 1;
       if (it < total) {
-        int lo = 0, hi = npass - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (pass_start[mid] <= it) lo = mid;
-          else hi = mid - 1;
-        }
+        while (s_start[cur + 1] <= it) ++cur;
+        const int lo = cur;
         s_pass = lo;
         sPass = passes[lo];
+        t_wait0 = global_ns();
         for (int d = 0; d < 2 && s_ok; ++d) {
           const int dp = sPass.dep[d];
           if (dp < 0) continue;
@@ -634,20 +712,26 @@ __global__ void __launch_bounds__(SF_FAST_THREADS)
         }
       }
     }
+    if (threadIdx.x == 0 && s_item < total) {
+      t_busy0 = global_ns();
+      atomicAdd(&ctl->wait_ns[sPass.kind], t_busy0 - t_wait0);
+    }
     __syncthreads();
     const int it = s_item;
     if (it >= total) break;
     if (s_ok) {
-      const int tile = it - pass_start[s_pass];
+      const int tile = it - s_start[s_pass];
       const int kind = sPass.kind;
       if (kind == FK_YF) fast_yf<E, PAD>(sP, g, sPass, tile, wsm, T);
-      else if (kind == FK_ZS) fast_zs<E, NC, PAD>(sP, g, sPass, tile, wsm);
+      else if (kind == FK_ZS) fast_zs<E, NC, PAD, OPS>(sP, g, sPass, tile, wsm);
       else fast_yi<E, PAD>(sP, g, sPass, tile, wsm, T);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
       atomicAdd(&done[s_pass], 1u);
+      atomicAdd(&ctl->busy_ns[sPass.kind], global_ns() - t_busy0);
+      atomicAdd(&ctl->tiles[sPass.kind], 1ull);
     }
   }
 }
@@ -674,26 +758,32 @@ struct FastLaunch {
 int sf_fast_launch_e8(const FastLaunch &fl, const IOArgs<float> &io, int *launches);
 int sf_fast_launch_e16(const FastLaunch &fl, const IOArgs<float> &io, int *launches);
 
-template <int E> size_t fast_x_smem() { return (size_t)(fast_wsm_elems<E>() + (16 * E + 1) * 17) * sizeof(float2); }
-template <int E> size_t fast_yz_smem() { return (size_t)(fast_wsm_elems<E>() + 32 * E * 17) * sizeof(float2); }
+template <int E> size_t fast_x_smem() { return (size_t)(fast_wsm_elems<E, 1>() + (16 * E + 1) * 17) * sizeof(float2); }
+#define SF_FAST_MAXPASS 2048
+template <int E> size_t fast_yz_smem() {
+  return (size_t)(fast_wsm_elems<E, SF_YZ_MAXM>() + 32 * E * 17) * sizeof(float2) + (SF_FAST_MAXPASS + 1) * sizeof(int);
+}
 
-template <int E, int NC, bool PAD> int fast_launch_yz(const FastLaunch &fl, const IOArgs<float> &io) {
+template <int E, int NC, bool PAD, int OPS> int fast_launch_yz(const FastLaunch &fl, const IOArgs<float> &io) {
   static bool attr = false;
   const size_t smyz = fast_yz_smem<E>();
   cudaError_t e;
   if (!attr) {
-    e = cudaFuncSetAttribute(k_fyz<E, NC, PAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smyz);
+    e = cudaFuncSetAttribute(k_fyz<E, NC, PAD, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smyz);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_fyz<E, NC, PAD, OPS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return (int)e;
     attr = true;
   }
   int dev = 0, nsm = 0, per = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fyz<E, NC, PAD>, SF_FAST_THREADS, smyz)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fyz<E, NC, PAD, OPS>, SF_FAST_THREADS, smyz)) != cudaSuccess)
     return (int)e;
   if (per < 1) return (int)cudaErrorLaunchOutOfResources;
+  if (fl.npass > SF_FAST_MAXPASS) return (int)cudaErrorInvalidValue;
   const int grid = fl.total < nsm * per ? fl.total : nsm * per;
-  k_fyz<E, NC, PAD><<<grid, SF_FAST_THREADS, smyz, fl.stream>>>(fl.d_prob, fl.geo, fl.d_passes, fl.d_start, fl.npass,
+  k_fyz<E, NC, PAD, OPS><<<grid, SF_FAST_THREADS, smyz, fl.stream>>>(fl.d_prob, fl.geo, fl.d_passes, fl.d_start, fl.npass,
                                                               fl.d_done, fl.ctl, fl.sticky, fl.timeout_ns, io);
   return (int)cudaGetLastError();
 }
@@ -708,6 +798,10 @@ template <int E, bool PAD> int fast_launch_all(const FastLaunch &fl, const IOArg
       return (int)e;
     if ((e = cudaFuncSetAttribute(k_fxi<E, PAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess)
       return (int)e;
+    if ((e = cudaFuncSetAttribute(k_fx<E, PAD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+      return (int)e;
+    if ((e = cudaFuncSetAttribute(k_fxi<E, PAD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+      return (int)e;
     attr = true;
   }
   if (fl.front) {
@@ -716,9 +810,10 @@ template <int E, bool PAD> int fast_launch_all(const FastLaunch &fl, const IOArg
     if ((e = cudaMemsetAsync(fl.d_done, 0, fl.npass * sizeof(unsigned), fl.stream)) != cudaSuccess) return (int)e;
     if ((e = cudaMemsetAsync(fl.ctl, 0, sizeof(ExecCtl), fl.stream)) != cudaSuccess) return (int)e;
     int r;
-    if (Q.ncomp == 3) r = fast_launch_yz<E, 3, PAD>(fl, io);
-    else if (Q.ncomp == 2) r = fast_launch_yz<E, 2, PAD>(fl, io);
-    else r = fast_launch_yz<E, 1, PAD>(fl, io);
+    if (Q.ncomp == 3 && Q.op == OPK_CURL) r = fast_launch_yz<E, 3, PAD, 1>(fl, io);
+    else if (Q.ncomp == 3) r = fast_launch_yz<E, 3, PAD, 0>(fl, io);
+    else if (Q.ncomp == 2) r = fast_launch_yz<E, 2, PAD, 0>(fl, io);
+    else r = fast_launch_yz<E, 1, PAD, 0>(fl, io);
     if (r) return r;
     if (launches) *launches += 2;
   }

@@ -76,12 +76,14 @@ __global__ void __launch_bounds__(SF_THREADS)
   __shared__ Pass<T> sPass;
   __shared__ int s_item, s_pass, s_ok, s_prob;
   const int total = pass_start[npass];
+  unsigned long long t_wait0 = 0, t_busy0 = 0;  // thread 0: tracing timestamps
   if (threadIdx.x == 0) s_prob = -1;
   for (;;) {
     if (threadIdx.x == 0) {
       const int it = (int)atomicAdd(&ctl->next, 1u);
       s_item = it;
       s_ok = 1;
+      t_wait0 = global_ns();
       if (it < total) {
         int lo = 0, hi = npass - 1;  // last pass with start <= it
         while (lo < hi) {
@@ -111,6 +113,10 @@ __global__ void __launch_bounds__(SF_THREADS)
         }
       }
     }
+    if (threadIdx.x == 0 && s_item < total) {
+      t_busy0 = global_ns();
+      atomicAdd(&ctl->wait_ns[sPass.kind & 7], t_busy0 - t_wait0);
+    }
     __syncthreads();
     const int it = s_item;
     if (it >= total) break;
@@ -123,6 +129,8 @@ __global__ void __launch_bounds__(SF_THREADS)
     if (threadIdx.x == 0) {
       __threadfence();
       atomicAdd(&done[s_pass], 1u);
+      atomicAdd(&ctl->busy_ns[sPass.kind & 7], global_ns() - t_busy0);
+      atomicAdd(&ctl->tiles[sPass.kind & 7], 1ull);
     }
   }
 }
