@@ -187,6 +187,100 @@ def cpu_baseline(n: int):
                       f"FP64, single-threaded numpy, {dt:.1f} s"}
 
 
+def _events_time(fn, steps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_other(args):
+    """Timing line for the configurations other than the headline one."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    import paper_2301_01145_gb300 as sf
+    import workloads
+
+    ge.build()
+    stream = torch.cuda.current_stream()
+    dev = lambda a, dt=torch.float32: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    line = {"unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    if args.workload == "c1":
+        pm = workloads.periodic_modes(64)
+        plan = sf.Plan(3, (64,) * 3, (0,) * 3, (2 * math.pi,) * 3, "PPP", eig="PS", prec="f64")
+        f = dev(pm.f[None], torch.float64)
+        psi, _ = plan.empty_outputs()
+        step = lambda: plan.execute(f, psi)
+        points, dtype = 64 ** 3, "f64"
+        cfg = {"workload": "3D periodic scalar Poisson 64^3 cell-centred on [0,2pi)^3, pseudo-spectral, "
+                           "sum of 8 seeded sine modes", "grid": 64}
+    elif args.workload == "c2":
+        n = 256
+        man = workloads.manufactured(seed_index=1)
+        case = workloads.bounded_case(man, (n, n, n), ("D", "N", "D"), False)
+        plan = sf.Plan(3, (n,) * 3, (0,) * 3, (1,) * 3, "DND", grid="regular", eig="FD2", prec="f32")
+        faces = {k: dev(v) for k, v in case["faces"].items()}
+        for (ax, side), g in faces.items():
+            plan.set_boundary(ax, side, g)
+        f = dev(case["f"][None])
+        psi, _ = plan.empty_outputs()
+        step = lambda: plan.execute(f, psi)
+        points, dtype = n ** 3, "f32"
+        cfg = {"workload": "3D Dirichlet/Neumann/Dirichlet Poisson, 256^3 cells regular grid on the unit cube, "
+                           "FD2 eigenvalues, inhomogeneous faces (manufactured sin/cos solution)", "grid": n}
+    elif args.workload == "c5":
+        from paper_2301_01145_gb300.autograd import poisson_solve
+        n = 128
+        data = workloads.gaussian_blobs(n)
+        plan = sf.Plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=2.0 / n,
+                       rhs_scale=-1.0)
+        om = dev(data["omega"])
+        w = dev(data["w"])
+
+        def step():
+            x = om.detach().requires_grad_(True)
+            psi, u = poisson_solve(x, plan)
+            L = (w[None] * u * u).sum()
+            L.backward()
+
+        points, dtype = n ** 3, "f32"
+        cfg = {"workload": "differentiable 3D unbounded curl solve 128^3 (padded 256^3), loss sum w|u|^2, "
+                           "forward + adjoint backward per step", "grid": n}
+    else:  # c4
+        probs = workloads.batch_problems(512)
+        plans, fs, ps = [], [], []
+        for bp in probs:
+            dim = bp.dim
+            plans.append(sf.Plan(dim, bp.n_cells, (-0.5,) * dim, (0.5,) * dim, bp.bc * dim,
+                                 grid="staggered" if bp.staggered else "regular", eig="PS",
+                                 sigma=2.0 / max(bp.n_cells) if bp.bc == "U" else 0.0,
+                                 rhs_scale=-1.0 if bp.bc == "U" else 1.0, generic=True))
+            fs.append(dev(workloads.lowpass_noise(tuple(reversed(bp.node_counts())), bp.seed)[None]))
+            ps.append(plans[-1].empty_outputs()[0])
+        batch = sf.Batch(plans)
+        step = lambda: batch.solve(fs, ps)
+        points, dtype = sum(bp.out_points() for bp in probs), "f32"
+        cfg = {"workload": "512 uneven problems in one persistent launch (CUDA graph): 2D 64^2..1024^2, 3D "
+                           "32^3..128^3, periodic/Dirichlet/Neumann/unbounded, regular/staggered, low-pass "
+                           "N(0,1) sources", "problems": 512, "points_per_step": points}
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = _events_time(step, args.steps, stream)
+    line.update({"metric": f"grid points/s ({args.workload})", "value": points / (ms * 1e-3), "ms_per_step": ms,
+                 "dtype": dtype, "config": cfg})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -200,10 +294,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--unfused", action="store_true")
     ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c3 (default): the headline 256^3 unbounded curl solve; the others time the remaining "
+                         "configurations (64^3 periodic FP64, 256^3 mixed D/N FD2, 512-problem batch, "
+                         "differentiable 128^3) and print their own line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "c3":
+        return run_other(args)
 
     import numpy as np
     import torch

@@ -105,6 +105,14 @@ typedef struct {
   int32_t prec;
   double rhs_scale;
   uint32_t flags;
+  /* tuning knobs (0 = library default), chosen by the autotuner:
+   *   tune_radix  largest radix of the general FFT engine (2, 4, 8 or 16)
+   *   tune_tile   largest number of packed lines per tile of the general engine (1..16, power of 2)
+   *   tune_slab   kx planes per slab of the register fast path's pipeline (>= 1) */
+  int32_t tune_radix;
+  int32_t tune_tile;
+  int32_t tune_slab;
+  int32_t reserved;
 } sf_plan_desc;
 
 /*
@@ -201,6 +209,15 @@ int sf_plan_launches(sf_plan p);
  * 24 doubles.  The paper times the solve steps separately (Sec. 5.3); this is
  * the per-pass breakdown of the GPU schedule. */
 sf_status sf_plan_stats(sf_plan p, double out[24]);
+
+/* Self-test of the bounded waits of the persistent scheduler: launches a
+ * two-pass work list whose second pass depends on a tile count the first pass
+ * can never reach (a flag nothing sets), with the given wait limit in
+ * milliseconds, on cuda_stream.  Every wait gives up after the limit, the
+ * kernel exits normally and the status word is read back: the call returns
+ * SF_ERR_TIMEOUT when the failure was detected as designed (SF_OK would mean
+ * the wait did not give up).  No work is done on user data. */
+sf_status sf_selftest_timeout(int timeout_ms, void *cuda_stream);
 
 /* Release a plan or batch and its device memory (waits for its stream). */
 sf_status sf_plan_destroy(sf_plan p);

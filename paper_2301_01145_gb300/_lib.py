@@ -51,6 +51,10 @@ class sf_plan_desc(ctypes.Structure):
         ("prec", c_int32),
         ("rhs_scale", c_double),
         ("flags", c_uint32),
+        ("tune_radix", c_int32),
+        ("tune_tile", c_int32),
+        ("tune_slab", c_int32),
+        ("reserved", c_int32),
     ]
 
 
@@ -72,6 +76,7 @@ SIGNATURES = {
     "sf_batch_solve": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p)]),
     "sf_sync": (c_int, [c_void_p]),
     "sf_plan_launches": (c_int, [c_void_p]),
+    "sf_selftest_timeout": (c_int, [c_int, c_void_p]),
     "sf_plan_stats": (c_int, [c_void_p, POINTER(c_double)]),
     "sf_plan_destroy": (c_int, [c_void_p]),
     "sf_status_string": (c_char_p, [c_int]),
@@ -103,7 +108,7 @@ def _check(status: int, where: str):
 
 
 def make_desc(dim, n, lo, hi, bc, grid="staggered", eig="PS", op="NONE", sigma=0.0, ncomp=1, prec="f32",
-              rhs_scale=1.0, flags=0) -> sf_plan_desc:
+              rhs_scale=1.0, flags=0, tune_radix=0, tune_tile=0, tune_slab=0) -> sf_plan_desc:
     d = sf_plan_desc()
     d.dim = dim
     for a in range(3):
@@ -123,6 +128,10 @@ def make_desc(dim, n, lo, hi, bc, grid="staggered", eig="PS", op="NONE", sigma=0
     d.prec = PREC[prec]
     d.rhs_scale = float(rhs_scale)
     d.flags = int(flags)
+    d.tune_radix = int(tune_radix)
+    d.tune_tile = int(tune_tile)
+    d.tune_slab = int(tune_slab)
+    d.reserved = 0
     return d
 
 
@@ -222,6 +231,11 @@ def sf_plan_stats(plan):
 
 def sf_plan_destroy(plan):
     _check(load().sf_plan_destroy(plan), "sf_plan_destroy")
+
+
+def sf_selftest_timeout(timeout_ms: int, stream=None) -> int:
+    """Status of the scheduler's bounded-wait self-test (SF_ERR_TIMEOUT = -6 expected)."""
+    return int(load().sf_selftest_timeout(int(timeout_ms), _stream(stream)))
 
 
 def sf_version() -> str:

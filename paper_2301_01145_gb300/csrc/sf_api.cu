@@ -53,17 +53,19 @@ bool valid_len(int L) {
   return (m & (m - 1)) == 0;
 }
 
-// radix plan: one radix-3 stage if needed, then radix-16 stages, then 2/4/8
-int radix_plan(int L, int *rad) {
+// radix plan: one radix-3 stage if needed, then stages of the largest radix
+// allowed (16 by default), then the remainder (2, 4 or 8)
+int radix_plan(int L, int *rad, int maxr) {
+  if (maxr != 2 && maxr != 4 && maxr != 8) maxr = 16;
   int n = 0;
   int m = L;
   if (m % 3 == 0) {
     rad[n++] = 3;
     m /= 3;
   }
-  while (m >= 16) {
-    rad[n++] = 16;
-    m /= 16;
+  while (m >= maxr) {
+    rad[n++] = maxr;
+    m /= maxr;
   }
   if (m > 1) rad[n++] = m;
   return n;
@@ -76,7 +78,7 @@ struct AxisHost {
 };
 
 // per-axis transform geometry and tables (Table 1; Sec. 2.4.3 wavenumbers)
-AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, bool cpath) {
+AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, bool cpath, int maxr = 16) {
   AxisHost a{};
   a.kind = kind;
   a.n = n;
@@ -92,7 +94,7 @@ AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, b
   }
   if (cpath) a.ns = is_x ? a.L / 2 + 1 : a.L;
   else a.ns = a.nu;
-  a.nst = radix_plan(a.L, a.radix);
+  a.nst = radix_plan(a.L, a.radix, maxr);
   const int L = a.L;
   a.tw.resize(2 * (size_t)L);
   for (int j = 0; j < L; ++j) {
@@ -216,7 +218,7 @@ template <typename T> int pass_tiles(const Prob<T> &P, const Pass<T> &ps) {
 
 // choose the tile width W (packed lines) for a pass: largest power of two that
 // fits the shared-memory budget and does not exceed the lines available
-template <typename T> void size_pass(const Prob<T> &P, Pass<T> &ps) {
+template <typename T> void size_pass(const Prob<T> &P, Pass<T> &ps, int wcap) {
   int L = 0, nbuf = 2, lines = 1;
   switch (ps.kind) {
     case PK_XFWD: L = P.ax[0].L; lines = cdiv(P.nuy, 2); break;
@@ -229,6 +231,8 @@ template <typename T> void size_pass(const Prob<T> &P, Pass<T> &ps) {
     case PK_FILL: ps.W = 1; ps.Wp = 1; ps.nbuf = 0; ps.bufsz = 0; return;
   }
   int W = kMaxW;
+  if (wcap >= 1 && wcap < kMaxW)
+    while (W > wcap) W >>= 1;
   while (W > 1 && W / 2 >= lines) W >>= 1;
   for (;; W >>= 1) {
     const int Wp = W > 1 ? W + 1 : 1;
@@ -251,12 +255,13 @@ template <typename T> struct ExecList {
   unsigned *d_done = nullptr;
   size_t smem = 0;
   int total = 0;
+  int wcap = 0;  // tile-width cap (tuning)
 
   void add(const Prob<T> &P, int kind, int prob, int dep0 = -1, int dep1 = -1) {
     Pass<T> ps{};
     ps.kind = kind;
     ps.prob = prob;
-    size_pass<T>(P, ps);
+    size_pass<T>(P, ps, wcap);
     ps.ntiles = pass_tiles<T>(P, ps);
     ps.dep[0] = dep0;
     ps.dep[1] = dep1;
@@ -620,6 +625,11 @@ static sf_status validate(const sf_plan_desc &d) {
     if (d.op == SF_OP_CURL && d.ncomp != (d.dim == 3 ? 3 : 1)) return fail(SF_ERR_ARG, "CURL needs ncomp 3 (3D) or 1 (2D)");
   }
   if (d.ncomp + op_outputs(d.op, d.dim, d.ncomp) > SF_MAXF) return fail(SF_ERR_ARG, "too many fields");
+  if (!(d.tune_radix == 0 || d.tune_radix == 2 || d.tune_radix == 4 || d.tune_radix == 8 || d.tune_radix == 16))
+    return fail(SF_ERR_ARG, "tune_radix must be 0, 2, 4, 8 or 16");
+  if (d.tune_tile < 0 || d.tune_tile > 16 || (d.tune_tile & (d.tune_tile - 1)))
+    return fail(SF_ERR_ARG, "tune_tile must be 0 or a power of two up to 16");
+  if (d.tune_slab < 0) return fail(SF_ERR_ARG, "tune_slab must be >= 0");
   return SF_OK;
 }
 
@@ -653,7 +663,7 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   AxisHost ah[3];
   for (int a = 0; a < 3; ++a) {
     if (a < d.dim) {
-      ah[a] = build_axis(axis_kind(d.bc[a][0], d.grid), d.n[a], d.lo[a], d.hi[a], d.eig, a == 0, p.cpath);
+      ah[a] = build_axis(axis_kind(d.bc[a][0], d.grid), d.n[a], d.lo[a], d.hi[a], d.eig, a == 0, p.cpath, d.tune_radix);
       prodL *= ah[a].L;
       hd *= ah[a].h;
     } else {  // unused z axis of a 2D problem: a trivial periodic axis of one point
@@ -729,12 +739,8 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   if (sizeof(T) == 4 && d.dim == 3 && p.cpath && !(d.flags & SF_FLAG_GENERIC) && p.ax[0].L == p.ax[1].L &&
       p.ax[1].L == p.ax[2].L && (p.ax[0].L == 512 || p.ax[0].L == 256)) {
     fastE = p.ax[0].L / 32;
-    const char *env = getenv("SF_SLAB_PLANES");
-    int S = env ? atoi(env) : 4;
-    if (S < 1) S = 1;
-    const char *envl = getenv("SF_SLAB_LAG");
-    int lag = envl ? atoi(envl) : 1;
-    if (lag < 1) lag = 1;
+    int S = d.tune_slab > 0 ? d.tune_slab : 4;
+    const int lag = 1;
     geo.S = fused() ? std::min(S, p.nsx) : p.nsx;
     geo.nslot = fused() ? lag + 1 : 1;
     geo.nfmax = nf;
@@ -789,6 +795,7 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
     ex.add(Q, PK_XINV, 0, dep);
     if (Q.fill_count) ex.add(Q, PK_FILL, 0);
   };
+  ex_front.wcap = ex_back.wcap = ex_all.wcap = ex_adj.wcap = d.tune_tile;
   front(ex_front, P);
   back(ex_back, P, -1);
   front(ex_all, P);
@@ -929,6 +936,7 @@ template <typename T> struct BatchImpl : sf_plan_s {
       for (auto &p : plans[i]->ex_all.passes) kinds[i].push_back(p.kind);
     }
     std::vector<int> last(n, -1);
+    ex.wcap = plans[0]->d.tune_tile;
     size_t maxlen = 0;
     for (auto &k : kinds) maxlen = std::max(maxlen, k.size());
     for (size_t lvl = 0; lvl < maxlen; ++lvl) {
@@ -1180,6 +1188,56 @@ sf_status sf_sync(sf_plan p) {
 }
 
 int sf_plan_launches(sf_plan p) { return p ? p->launches_per_exec : 0; }
+
+sf_status sf_selftest_timeout(int timeout_ms, void *cuda_stream) {
+  if (timeout_ms < 1 || timeout_ms > 10000) return fail(SF_ERR_ARG, "timeout_ms must be in [1, 10000]");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  SF_TRY(set_kernel_attrs<float>());
+  DevMem<float> mem;
+  // a problem whose only passes are empty fills (no user data touched)
+  Prob<float> q{};
+  q.dim = 2;
+  q.ncomp = q.nin = q.nout = 1;
+  q.fill_count = 0;
+  for (int a = 0; a < 3; ++a) {
+    q.ax[a].kind = AK_P;
+    q.ax[a].n = q.ax[a].nodes = q.ax[a].nu = q.ax[a].L = q.ax[a].ns = 1;
+  }
+  void *tmp;
+  SF_TRY(mem.alloc(&tmp, sizeof(Prob<float>)));
+  SF_CK(cudaMemcpy(tmp, &q, sizeof(Prob<float>), cudaMemcpyHostToDevice));
+  const Prob<float> *dq = (const Prob<float> *)tmp;
+  ExecList<float> ex;
+  for (int i = 0; i < 2; ++i) {
+    Pass<float> ps{};
+    ps.kind = PK_FILL;
+    ps.ntiles = 4;
+    ps.W = ps.Wp = 1;
+    ps.dep[0] = ps.dep[1] = -1;
+    ex.passes.push_back(ps);
+  }
+  ex.passes[1].dep[0] = 0;
+  ex.passes[1].depcnt[0] = ex.passes[0].ntiles + 1;  // unreachable
+  SF_TRY(ex.upload(mem));
+  ExecCtl *ctl;
+  unsigned *sticky;
+  SF_TRY(mem.alloc(&tmp, sizeof(ExecCtl)));
+  ctl = (ExecCtl *)tmp;
+  SF_TRY(mem.alloc(&tmp, sizeof(unsigned)));
+  sticky = (unsigned *)tmp;
+  SF_CK(cudaMemsetAsync(sticky, 0, sizeof(unsigned), st));
+  SF_CK(cudaMemsetAsync(ex.d_done, 0, ex.passes.size() * sizeof(unsigned), st));
+  SF_CK(cudaMemsetAsync(ctl, 0, sizeof(ExecCtl), st));
+  IOArgs<float> io{};
+  k_exec<float><<<4, SF_THREADS, 0, st>>>(dq, ex.d_passes, ex.d_start, (int)ex.passes.size(), ex.d_done, ctl, sticky,
+                                          (unsigned long long)timeout_ms * 1000000ull, io);
+  SF_CK(cudaGetLastError());
+  SF_CK(cudaStreamSynchronize(st));
+  unsigned s = 0;
+  SF_CK(cudaMemcpy(&s, sticky, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (s) return fail(SF_ERR_TIMEOUT, "scheduler wait gave up as designed");
+  return SF_OK;
+}
 
 sf_status sf_plan_stats(sf_plan p, double out[24]) {
   if (!p || !out) return fail(SF_ERR_ARG, "null argument");

@@ -47,13 +47,24 @@ def test_binding_covers_every_symbol():
     assert set(declared_functions()) <= set(_lib.SIGNATURES)
 
 
-def test_descriptor_layout_matches_header():
-    # offsets follow the C layout of sf_plan_desc (int32 and double members)
+def test_descriptor_layout_matches_header(tmp_path):
+    # offsets and size of sf_plan_desc as the C compiler lays it out vs the ctypes mirror
+    import shutil
+    import subprocess
     from paper_2301_01145_gb300._lib import sf_plan_desc
-    off = {f: getattr(sf_plan_desc, f).offset for f, _ in sf_plan_desc._fields_}
-    assert off["dim"] == 0 and off["n"] == 4 and off["lo"] == 16 and off["hi"] == 40
-    assert off["bc"] == 64 and off["grid"] == 88 and off["green_sigma"] == 104
-    assert ctypes.sizeof(sf_plan_desc) == 136
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in sf_plan_desc._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join(f'printf("%zu\\n", offsetof(sf_plan_desc, {f}));' for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "sailfish_gb300.h"\n'
+                   'int main(void){' + body + 'printf("%zu\\n", sizeof(sf_plan_desc)); return 0;}\n')
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[:-1] == [getattr(sf_plan_desc, f).offset for f in fields]
+    assert out[-1] == ctypes.sizeof(sf_plan_desc)
 
 
 def test_status_strings_and_version(lib):
@@ -73,6 +84,9 @@ def test_status_strings_and_version(lib):
     (dict(bc="UUU", sigma=0.0), -1),
     (dict(op="CURL", ncomp=1), -1),
     (dict(op="GRAD", bc="DDD"), -2),
+    (dict(tune_radix=3), -1),
+    (dict(tune_tile=3), -1),
+    (dict(tune_slab=-1), -1),
 ])
 def test_descriptor_validation_without_gpu(lib, mutate, expect):
     from paper_2301_01145_gb300 import _lib
