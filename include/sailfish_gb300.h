@@ -210,6 +210,27 @@ int sf_plan_launches(sf_plan p);
  * the per-pass breakdown of the GPU schedule. */
 sf_status sf_plan_stats(sf_plan p, double out[24]);
 
+/* A bounded solve that allocates nothing, for callers that cannot call
+ * cudaMalloc (code inside host callbacks or driver hooks that must not
+ * allocate, real-time loops that forbid allocation after start-up, processes
+ * whose device memory is owned by another allocator).  There is no
+ * counterpart in the paper: it is the plan-based solve (sf_plan_create +
+ * sf_execute) without a plan, restricted to what fits a fixed workspace.
+ *   d        problem description; FP32, one component, no operator, periodic /
+ *            Dirichlet / Neumann axes only (homogeneous boundaries), 2D or 3D.
+ *   dev_f    device source, dev_psi device result (layouts as for sf_execute).
+ * Workspace and tables live in one file-scope device array of 64 MiB that
+ * every GPU loading this library holds until the process exits.  A problem
+ * whose workspace does not fit returns SF_ERR_ARG (use sf_plan_create); other
+ * unsupported options return SF_ERR_UNSUPPORTED.  No cudaMalloc, cudaFree or
+ * other allocation is made.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and must come before any stream
+ * capture; the call is not thread-safe.  All calls share the array and it
+ * keeps the last call's contents: calls that may overlap on the GPU (other
+ * streams, other threads) race and corrupt each other's results.  Work is
+ * enqueued on cuda_stream; the result is ready when that stream reaches it. */
+sf_status sf_solve_static(const sf_plan_desc *d, const void *dev_f, void *dev_psi, void *cuda_stream);
+
 /* Self-test of the bounded waits of the persistent scheduler: launches a
  * two-pass work list whose second pass depends on a tile count the first pass
  * can never reach (a flag nothing sets), with the given wait limit in

@@ -77,6 +77,7 @@ SIGNATURES = {
     "sf_sync": (c_int, [c_void_p]),
     "sf_plan_launches": (c_int, [c_void_p]),
     "sf_selftest_timeout": (c_int, [c_int, c_void_p]),
+    "sf_solve_static": (c_int, [POINTER(sf_plan_desc), c_void_p, c_void_p, c_void_p]),
     "sf_plan_stats": (c_int, [c_void_p, POINTER(c_double)]),
     "sf_plan_destroy": (c_int, [c_void_p]),
     "sf_status_string": (c_char_p, [c_int]),
@@ -231,6 +232,13 @@ def sf_plan_stats(plan):
 
 def sf_plan_destroy(plan):
     _check(load().sf_plan_destroy(plan), "sf_plan_destroy")
+
+
+def sf_solve_static(desc: sf_plan_desc, f, psi, stream=None):
+    """Allocation-free solve into the library's fixed device workspace (see the header)."""
+    st = int(load().sf_solve_static(ctypes.byref(desc), _ptr(f), _ptr(psi), _stream(stream)))
+    if st != SF_OK:
+        raise SolverError(st, "sf_solve_static", "see sailfish_gb300.h: FP32, scalar, P/D/N axes, workspace <= 64 MiB")
 
 
 def sf_selftest_timeout(timeout_ms: int, stream=None) -> int:
