@@ -54,7 +54,7 @@ class sf_plan_desc(ctypes.Structure):
         ("tune_radix", c_int32),
         ("tune_tile", c_int32),
         ("tune_slab", c_int32),
-        ("reserved", c_int32),
+        ("tune_lag", c_int32),
     ]
 
 
@@ -109,7 +109,7 @@ def _check(status: int, where: str):
 
 
 def make_desc(dim, n, lo, hi, bc, grid="staggered", eig="PS", op="NONE", sigma=0.0, ncomp=1, prec="f32",
-              rhs_scale=1.0, flags=0, tune_radix=0, tune_tile=0, tune_slab=0) -> sf_plan_desc:
+              rhs_scale=1.0, flags=0, tune_radix=0, tune_tile=0, tune_slab=0, tune_lag=0) -> sf_plan_desc:
     d = sf_plan_desc()
     d.dim = dim
     for a in range(3):
@@ -132,7 +132,7 @@ def make_desc(dim, n, lo, hi, bc, grid="staggered", eig="PS", op="NONE", sigma=0
     d.tune_radix = int(tune_radix)
     d.tune_tile = int(tune_tile)
     d.tune_slab = int(tune_slab)
-    d.reserved = 0
+    d.tune_lag = int(tune_lag)
     return d
 
 

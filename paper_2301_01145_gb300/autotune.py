@@ -21,7 +21,7 @@ from typing import Dict, Iterable, List, Optional
 
 from . import Batch, Plan
 
-KNOBS = ("tune_radix", "tune_tile", "tune_slab", "fused")
+KNOBS = ("tune_radix", "tune_tile", "tune_slab", "tune_lag", "fused")
 
 
 def cache_path() -> str:
@@ -56,8 +56,8 @@ def candidates(problem: Dict) -> List[Dict]:
     cands = [dict(tune_radix=0, tune_tile=0, tune_slab=0, fused=True)]
     for r, t in itertools.product((16, 8, 4), (16, 8, 4)):
         cands.append(dict(tune_radix=r, tune_tile=t, tune_slab=0, fused=True))
-    for sl in (2, 4, 8, 16):
-        cands.append(dict(tune_radix=0, tune_tile=0, tune_slab=sl, fused=True))
+    for sl, lag in itertools.product((2, 4, 8, 16), (1, 2)):
+        cands.append(dict(tune_radix=0, tune_tile=0, tune_slab=sl, tune_lag=lag, fused=True))
     cands.append(dict(tune_radix=0, tune_tile=0, tune_slab=0, fused=False))
     uniq, seen = [], set()
     for c in cands:

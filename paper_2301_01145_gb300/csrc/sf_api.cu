@@ -364,7 +364,7 @@ void build_fast_list(const Prob<T> &Q, int S, int nslot, int L, FastList &fl) {
       p.ntiles = fast_tiles_yf(Q, p.nkx);
       if (s >= nslot) p.dep[0] = izs[s - nslot];
     } else if (kind == FK_ZS) {
-      p.ntiles = fast_tiles_zs(p.nkx, L);
+      p.ntiles = fast_tiles_zs(p.nkx, L) * (fast_split_curl(Q) ? 3 : 1);
       p.dep[0] = iyf[s];
       if (s >= nslot) p.dep[1] = iyi[s - nslot];
     } else {
@@ -630,6 +630,7 @@ static sf_status validate(const sf_plan_desc &d) {
   if (d.tune_tile < 0 || d.tune_tile > 16 || (d.tune_tile & (d.tune_tile - 1)))
     return fail(SF_ERR_ARG, "tune_tile must be 0 or a power of two up to 16");
   if (d.tune_slab < 0) return fail(SF_ERR_ARG, "tune_slab must be >= 0");
+  if (d.tune_lag < 0 || d.tune_lag > 8) return fail(SF_ERR_ARG, "tune_lag must be in [0, 8]");
   return SF_OK;
 }
 
@@ -740,7 +741,7 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
       p.ax[1].L == p.ax[2].L && (p.ax[0].L == 512 || p.ax[0].L == 256)) {
     fastE = p.ax[0].L / 32;
     int S = d.tune_slab > 0 ? d.tune_slab : 4;
-    const int lag = 1;
+    const int lag = d.tune_lag > 0 ? d.tune_lag : 1;
     geo.S = fused() ? std::min(S, p.nsx) : p.nsx;
     geo.nslot = fused() ? lag + 1 : 1;
     geo.nfmax = nf;

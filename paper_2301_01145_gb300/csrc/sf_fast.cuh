@@ -59,6 +59,15 @@ template <int E> __device__ __forceinline__ int klayout(int lane, int j) {
   return k1 + E * (j + E * bitrev_lanes(q, G));
 }
 
+// row stride of the warp transpose buffer: 32 + G makes (k1 * stride + q) mod 16
+// a permutation over a half warp (8-byte elements), i.e. no bank conflicts
+template <int E> __host__ __device__ constexpr int wrow() { return 32 + 32 / E; }
+// Row of spectral index k in a 16-line transpose tile: stride 17, and the G
+// lane groups of the k layout (k / E^2) shifted by E/2 slots so that a half
+// warp writing one register of every lane hits 16 distinct bank pairs.
+template <int E> __device__ __forceinline__ int trow(int k) { return k * 17 + (k / (E * E)) * (E / 2); }
+template <int E> __host__ __device__ constexpr int trows_elems() { return 32 * E * 17 + 16; }
+
 // ---- pruned E-point DFTs ----------------------------------------------------
 // dft4 of (a0, a1, 0, 0)
 template <bool INV, typename V> __device__ __forceinline__ void dft4_2in(V a0, V a1, V &y0, V &y1, V &y2, V &y3) {
@@ -135,7 +144,7 @@ template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfo
 template <typename T, int E, bool HALFIN, int M>
 __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const cx<T> *__restrict__ tw) {
   typedef cx<T> V;
-  constexpr int L = 32 * E, G = 32 / E;
+  constexpr int L = 32 * E, G = 32 / E, P = wrow<E>();
   const int t = threadIdx.x & 31;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
@@ -151,13 +160,13 @@ __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
 #pragma unroll
   for (int m = 0; m < M; ++m)
 #pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) wsm[m * E * 33 + k1 * 33 + t] = v[m][k1];
+    for (int k1 = 0; k1 < E; ++k1) wsm[m * E * P + k1 * P + t] = v[m][k1];
   __syncwarp();
   const int k1 = t / G, q = t % G;
 #pragma unroll
   for (int m = 0; m < M; ++m)
 #pragma unroll
-    for (int s = 0; s < E; ++s) v[m][s] = wsm[m * E * 33 + k1 * 33 + G * s + q];
+    for (int s = 0; s < E; ++s) v[m][s] = wsm[m * E * P + k1 * P + G * s + q];
   __syncwarp();
 #pragma unroll
   for (int m = 0; m < M; ++m) dftR<E, false>(v[m]);
@@ -186,7 +195,7 @@ __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
 template <typename T, int E, bool HALFOUT, int M>
 __device__ __forceinline__ void wfft_inv_m(cx<T> (&v)[M][E], cx<T> *wsm, const cx<T> *__restrict__ tw) {
   typedef cx<T> V;
-  constexpr int L = 32 * E, G = 32 / E;
+  constexpr int L = 32 * E, G = 32 / E, P = wrow<E>();
   const int t = threadIdx.x & 31;
   const int k1 = t / G, q = t % G;
 #pragma unroll
@@ -217,12 +226,12 @@ __device__ __forceinline__ void wfft_inv_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
 #pragma unroll
   for (int m = 0; m < M; ++m)
 #pragma unroll
-    for (int s = 0; s < E; ++s) wsm[m * E * 33 + k1 * 33 + G * s + q] = v[m][s];
+    for (int s = 0; s < E; ++s) wsm[m * E * P + k1 * P + G * s + q] = v[m][s];
   __syncwarp();
 #pragma unroll
   for (int m = 0; m < M; ++m)
 #pragma unroll
-    for (int kk = 0; kk < E; ++kk) v[m][kk] = wsm[m * E * 33 + kk * 33 + t];
+    for (int kk = 0; kk < E; ++kk) v[m][kk] = wsm[m * E * P + kk * P + t];
   __syncwarp();
 #pragma unroll
   for (int kk = 1; kk < E; ++kk) {
@@ -257,8 +266,11 @@ struct FastGeo {
   int nfmax;  // fields per slot
 };
 
-#define SF_YZ_MAXM 3  // interleaved lines per warp in the YZ executor
-template <int E, int M> __host__ __device__ constexpr int fast_wsm_elems() { return 8 * M * E * 33; }
+#define SF_YZ_MAXM 3  // interleaved lines per warp in the YZ executor (z stage with 3 components)
+// warp-buffer depth of an executor variant: the split-curl variant (OPS = 2)
+// keeps one line per warp so that two CTAs fit on an SM
+__host__ __device__ constexpr int fast_yz_lines(int ops) { return ops == 2 ? 1 : SF_YZ_MAXM; }
+template <int E, int M> __host__ __device__ constexpr int fast_wsm_elems() { return 8 * M * E * wrow<E>(); }
 
 // tiles of the YZ passes (the device decoders below use the same geometry)
 #define SF_YF_ROWS 16  // z rows per YF tile
@@ -266,6 +278,11 @@ template <int E, int M> __host__ __device__ constexpr int fast_wsm_elems() { ret
 #define SF_YI_COLS 16  // z columns per YI tile
 template <typename T> __host__ __device__ inline int fast_tiles_yf(const Prob<T> &Q, int nkx) {
   return Q.nin * nkx * cdiv(Q.nuz, SF_YF_ROWS);
+}
+// forward 3D curl solved component by component (the z stage emits psi_c and
+// d/dz psi_c; the x / y derivatives are applied in y-spectral space by YI)
+template <typename T> __host__ __device__ inline bool fast_split_curl(const Prob<T> &Q) {
+  return Q.op == OPK_CURL && Q.ncomp == 3 && Q.dim == 3 && !Q.adjoint;
 }
 __host__ __device__ inline int fast_tiles_zs(int nkx, int L) { return nkx * (L / SF_ZS_ROWS); }
 template <typename T> __host__ __device__ inline int fast_tiles_yi(const Prob<T> &Q, int nkx) {
@@ -286,7 +303,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs
   V *wsm_all = reinterpret_cast<V *>(fsm);
   V *T = wsm_all + fast_wsm_elems<E, 1>();
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
-  V *wsm = wsm_all + warp * E * 33;
+  V *wsm = wsm_all + warp * E * wrow<E>();
   const Axis<float> &X = P.ax[0], &Y = P.ax[1];
   const int nuy = P.nuy, nuz = P.nuz, nux = X.nu, nsx = P.nsx;
   const int ty = cdiv(nuy, 16);
@@ -355,7 +372,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *prob
   V *wsm_all = reinterpret_cast<V *>(fsm);
   V *T = wsm_all + fast_wsm_elems<E, 1>();
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
-  V *wsm = wsm_all + warp * E * 33;
+  V *wsm = wsm_all + warp * E * wrow<E>();
   const Axis<float> &X = P.ax[0], &Y = P.ax[1];
   const int nuy = P.nuy, nuz = P.nuz, nux = X.nu, nsx = P.nsx;
   const int ty = cdiv(nuy, 16);
@@ -424,7 +441,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *prob
 // YZ tiles
 // ---------------------------------------------------------------------------
 // YF: 16 rows (consecutive z, fixed c and kx) of A along y -> I1 slot [c][kxl][ky][z]
-template <int E, bool PAD>
+template <int E, bool PAD, int M2>
 __device__ __forceinline__ void fast_yf(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
                                         cx<float> *wsm, cx<float> *T) {
   typedef cx<float> V;
@@ -440,29 +457,33 @@ __device__ __forceinline__ void fast_yf(const Prob<float> &P, const FastGeo &g, 
   const int z0 = iz * SF_YF_ROWS;
   if (c >= P.nin) return;  // tile outside the pass (uniform over the block)
   const V *A = reinterpret_cast<const V *>(P.A);
-  V v[2][E];
+  // two rows per warp, transformed together (M2 = 2) or one after the other (M2 = 1)
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int z = z0 + 2 * warp + h;
-    const V *src = A + (((size_t)c * nsx + kx) * nuz + z) * nuy;
+  for (int h0 = 0; h0 < 2; h0 += M2) {
+    V v[M2][E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int pos = t + 32 * r;
-      v[h][r] = ((!PAD || r < E / 2) && z < nuz && pos < nuy) ? __ldcs(&src[pos]) : czero<V>();
+    for (int h = 0; h < M2; ++h) {
+      const int z = z0 + 2 * warp + h0 + h;
+      const V *src = A + (((size_t)c * nsx + kx) * nuz + z) * nuy;
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        const int pos = t + 32 * r;
+        v[h][r] = ((!PAD || r < E / 2) && z < nuz && pos < nuy) ? __ldcs(&src[pos]) : czero<V>();
+      }
     }
+    wfft_fwd_m<float, E, PAD, M2>(v, wsm, P.ax[1].tw);
+#pragma unroll
+    for (int h = 0; h < M2; ++h)
+#pragma unroll
+      for (int j = 0; j < E; ++j) T[trow<E>(klayout<E>(t, j)) + 2 * warp + h0 + h] = v[h][j];
   }
-  wfft_fwd_m<float, E, PAD, 2>(v, wsm, P.ax[1].tw);
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int j = 0; j < E; ++j) T[klayout<E>(t, j) * 17 + 2 * warp + h] = v[h][j];
   __syncthreads();
   V *I1 = reinterpret_cast<V *>(P.I1) + (size_t)ps.slot * g.nfmax * g.S * L * nuz;
   const size_t base = (((size_t)c * g.S + kxl) * L) * nuz + z0;
   const int cnt = L * 16;
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const int l = e & 15, ky = e >> 4;
-    if (z0 + l < nuz) __stcg(&I1[base + (size_t)ky * nuz + l], T[ky * 17 + l]);
+    if (z0 + l < nuz) __stcg(&I1[base + (size_t)ky * nuz + l], T[trow<E>(ky) + l]);
   }
 }
 
@@ -493,18 +514,30 @@ __device__ __forceinline__ cx<float> op_coef(const Prob<float> &P, int o, int c,
 // spectra stay in registers; no block-wide synchronisation.
 // OPS = 1: 3D curl written out (u = i kappa x psi); OPS = 0: coefficient table (any operator or none)
 template <int E, int NC, bool PAD, int OPS>
+__device__ __forceinline__ void fast_zs_row(const Prob<float> &P, const FastGeo &g, const FPass &ps, int kxl, int ky,
+                                            cx<float> *wsm);
+
+template <int E, int NC, bool PAD, int OPS>
 __device__ __forceinline__ void fast_zs(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
                                         cx<float> *wsm) {
-  typedef cx<float> V;
   constexpr int L = 32 * E;
-  const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
-  const int nuz = P.nuz;
+  const int warp = threadIdx.x >> 5;
   const int nty = L / SF_ZS_ROWS;
   const int iy = tile % nty;
   const int kxl = tile / nty;
-  const int kx = ps.kx0 + kxl;
-  const int ky = iy * SF_ZS_ROWS + warp;
   if (kxl >= ps.nkx) return;
+#pragma unroll 1
+  for (int h = 0; h < SF_ZS_ROWS / 8; ++h) fast_zs_row<E, NC, PAD, OPS>(P, g, ps, kxl, iy * SF_ZS_ROWS + 8 * h + warp, wsm);
+}
+
+template <int E, int NC, bool PAD, int OPS>
+__device__ __forceinline__ void fast_zs_row(const Prob<float> &P, const FastGeo &g, const FPass &ps, int kxl, int ky,
+                                            cx<float> *wsm) {
+  typedef cx<float> V;
+  constexpr int L = 32 * E;
+  const int t = threadIdx.x & 31;
+  const int nuz = P.nuz;
+  const int kx = ps.kx0 + kxl;
   const int nop = P.nop;
   const size_t slot = (size_t)ps.slot * g.nfmax * g.S * L * nuz;
   const V *I1 = reinterpret_cast<const V *>(P.I1) + slot;
@@ -601,9 +634,63 @@ __device__ __forceinline__ void fast_zs(const Prob<float> &P, const FastGeo &g, 
   }
 }
 
+// ZS, split curl: 8 rows (consecutive ky) of one component c.  Emits
+// psi_c (I2 field c) and, for c = x, y, d/dz psi_c (I2 field 3 + c).
+template <int E, bool PAD>
+__device__ __forceinline__ void fast_zs_split(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
+                                              cx<float> *wsm) {
+  typedef cx<float> V;
+  constexpr int L = 32 * E;
+  const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
+  const int nuz = P.nuz;
+  const int nty = L / SF_ZS_ROWS;
+  const int iy = tile % nty;
+  const int rest = tile / nty;
+  const int kxl = rest % ps.nkx;
+  const int c = rest / ps.nkx;
+  if (c >= 3) return;
+  const int kx = ps.kx0 + kxl;
+  const int ky = iy * SF_ZS_ROWS + warp;
+  const size_t slot = (size_t)ps.slot * g.nfmax * g.S * L * nuz;
+  const V *I1 = reinterpret_cast<const V *>(P.I1) + slot;
+  V *I2 = reinterpret_cast<V *>(P.I2) + slot;
+  const V *tz = P.ax[2].tw;
+  V sp[1][E];
+  {
+    const V *src = I1 + (((size_t)c * g.S + kxl) * L + ky) * nuz;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int pos = t + 32 * r;
+      sp[0][r] = ((!PAD || r < E / 2) && pos < nuz) ? __ldcg(&src[pos]) : czero<V>();
+    }
+  }
+  wfft_fwd_m<float, E, PAD, 1>(sp, wsm, tz);
+#pragma unroll
+  for (int j = 0; j < E; ++j) sp[0][j] = cscale(sp[0][j], fast_mult(P, kx, ky, klayout<E>(t, j)));
+  if (c < 2) {
+    V dz[1][E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) dz[0][j] = mul_i(cscale(sp[0][j], __ldg(&P.ax[2].kap[klayout<E>(t, j)])));
+    wfft_inv_m<float, E, PAD, 1>(dz, wsm, tz);
+    V *dst = I2 + (((size_t)(3 + c) * g.S + kxl) * L + ky) * nuz;
+#pragma unroll
+    for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
+      const int z = t + 32 * r;
+      if (z < nuz) __stcg(&dst[z], dz[0][r]);
+    }
+  }
+  wfft_inv_m<float, E, PAD, 1>(sp, wsm, tz);
+  V *dst = I2 + (((size_t)c * g.S + kxl) * L + ky) * nuz;
+#pragma unroll
+  for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
+    const int z = t + 32 * r;
+    if (z < nuz) __stcg(&dst[z], sp[0][r]);
+  }
+}
+
 // YI: 16 z-columns (fixed f and kx) of I2 [f][kxl][ky][z], transposed through
 // shared memory, inverse y transform per column -> B rows along y
-template <int E, bool PAD>
+template <int E, bool PAD, bool SPLIT, int M2>
 __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
                                         cx<float> *wsm, cx<float> *T) {
   typedef cx<float> V;
@@ -619,39 +706,76 @@ __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, 
   const int z0 = iz * SF_YI_COLS;
   if (f >= P.nout) return;
   const size_t slot = (size_t)ps.slot * g.nfmax * g.S * L * nuz;
-  const V *src = reinterpret_cast<const V *>(P.I2) + slot + (((size_t)f * g.S + kxl) * L) * nuz + z0;
-  // L*16 elements, 2E per thread: all loads issued before any use
-  {
-    constexpr int PER = L * 16 / SF_FAST_THREADS;
-    V tmp[PER];
+  const V *I2 = reinterpret_cast<const V *>(P.I2) + slot;
+  auto field = [&](int ff) { return I2 + (((size_t)ff * g.S + kxl) * L) * nuz + z0; };
+  constexpr int PER = L * 16 / SF_FAST_THREADS;
+  constexpr int BATCH = SPLIT ? 16 : PER;  // loads in flight per thread before they are used
+  if (!SPLIT || f < 3) {
+    const V *src = field(f);
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
-      const int e = threadIdx.x + i * SF_FAST_THREADS;
-      const int l = e & 15, ky = e >> 4;
-      tmp[i] = (z0 + l < nuz) ? __ldcg(&src[(size_t)ky * nuz + l]) : czero<V>();
+    for (int b0 = 0; b0 < PER; b0 += BATCH) {
+      V tmp[BATCH];
+#pragma unroll
+      for (int i = 0; i < BATCH; ++i) {
+        const int e = threadIdx.x + (b0 + i) * SF_FAST_THREADS;
+        const int l = e & 15, ky = e >> 4;
+        tmp[i] = (z0 + l < nuz) ? __ldcg(&src[(size_t)ky * nuz + l]) : czero<V>();
+      }
+#pragma unroll
+      for (int i = 0; i < BATCH; ++i) {
+        const int e = threadIdx.x + (b0 + i) * SF_FAST_THREADS;
+        T[trow<E>(e >> 4) + (e & 15)] = tmp[i];
+      }
     }
+  } else {
+    // curl output in y-spectral space: u_x = i ky psi_z - dz psi_y, u_y = dz psi_x - i kx psi_z,
+    // u_z = i kx psi_y - i ky psi_x  (fields 0..2 psi, 3 dz psi_x, 4 dz psi_y)
+    const int fa = f == 3 ? 2 : (f == 4 ? 3 : 1);
+    const int fb = f == 3 ? 4 : (f == 4 ? 2 : 0);
+    const float kxv = __ldg(&P.ax[0].kap[kx]);
+    const V *sa = field(fa), *sb = field(fb);
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
-      const int e = threadIdx.x + i * SF_FAST_THREADS;
-      T[(e >> 4) * 17 + (e & 15)] = tmp[i];
+    for (int b0 = 0; b0 < PER; b0 += BATCH) {
+      V ta[BATCH], tb[BATCH];
+#pragma unroll
+      for (int i = 0; i < BATCH; ++i) {
+        const int e = threadIdx.x + (b0 + i) * SF_FAST_THREADS;
+        const int l = e & 15, ky = e >> 4;
+        const bool ok = z0 + l < nuz;
+        ta[i] = ok ? __ldcg(&sa[(size_t)ky * nuz + l]) : czero<V>();
+        tb[i] = ok ? __ldcg(&sb[(size_t)ky * nuz + l]) : czero<V>();
+      }
+#pragma unroll
+      for (int i = 0; i < BATCH; ++i) {
+        const int e = threadIdx.x + (b0 + i) * SF_FAST_THREADS;
+        const float kyv = __ldg(&P.ax[1].kap[e >> 4]);
+        V r;
+        if (f == 3) r = csub(mul_i(cscale(ta[i], kyv)), tb[i]);
+        else if (f == 4) r = csub(ta[i], mul_i(cscale(tb[i], kxv)));
+        else r = mul_i(csub(cscale(ta[i], kxv), cscale(tb[i], kyv)));
+        T[trow<E>(e >> 4) + (e & 15)] = r;
+      }
     }
   }
   __syncthreads();
-  V v[2][E];
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
+  for (int h0 = 0; h0 < 2; h0 += M2) {
+    V v[M2][E];
 #pragma unroll
-    for (int j = 0; j < E; ++j) v[h][j] = T[klayout<E>(t, j) * 17 + 2 * warp + h];
-  wfft_inv_m<float, E, PAD, 2>(v, wsm, P.ax[1].tw);
+    for (int h = 0; h < M2; ++h)
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int z = z0 + 2 * warp + h;
-    if (z < nuz) {
-      V *dst = reinterpret_cast<V *>(P.B) + (((size_t)f * nsx + kx) * nuz + z) * nuy;
+      for (int j = 0; j < E; ++j) v[h][j] = T[trow<E>(klayout<E>(t, j)) + 2 * warp + h0 + h];
+    wfft_inv_m<float, E, PAD, M2>(v, wsm, P.ax[1].tw);
 #pragma unroll
-      for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
-        const int y = t + 32 * r;
-        if (y < nuy) __stcs(&dst[y], v[h][r]);
+    for (int h = 0; h < M2; ++h) {
+      const int z = z0 + 2 * warp + h0 + h;
+      if (z < nuz) {
+        V *dst = reinterpret_cast<V *>(P.B) + (((size_t)f * nsx + kx) * nuz + z) * nuy;
+#pragma unroll
+        for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
+          const int y = t + 32 * r;
+          if (y < nuy) __stcs(&dst[y], v[h][r]);
+        }
       }
     }
   }
@@ -660,7 +784,7 @@ __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, 
 // persistent YZ executor over the slab work list (same queue / bounded-wait
 // protocol as k_exec)
 template <int E, int NC, bool PAD, int OPS>
-__global__ void __launch_bounds__(SF_FAST_THREADS)
+__global__ void __launch_bounds__(SF_FAST_THREADS, OPS == 2 ? 2 : 1)
     k_fyz(const Prob<float> *probs, FastGeo g, const FPass *passes, const int *pass_start, int npass, unsigned *done,
           ExecCtl *ctl, unsigned *sticky, unsigned long long timeout_ns, IOArgs<float> io) {
   typedef cx<float> V;
@@ -669,11 +793,12 @@ __global__ void __launch_bounds__(SF_FAST_THREADS)
   __shared__ FPass sPass;
   __shared__ int s_item, s_pass, s_ok;
   load_prob<float>(sP, probs, io);
+  constexpr int MM = fast_yz_lines(OPS);  // interleaved lines per warp (warp buffer depth)
   V *wsm_all = reinterpret_cast<V *>(fsm);
-  V *T = wsm_all + fast_wsm_elems<E, SF_YZ_MAXM>();
-  V *wsm = wsm_all + (threadIdx.x >> 5) * SF_YZ_MAXM * E * 33;
+  V *T = wsm_all + fast_wsm_elems<E, MM>();
+  V *wsm = wsm_all + (threadIdx.x >> 5) * MM * E * wrow<E>();
   // pass start table cached in shared memory (after the tile buffer)
-  int *s_start = reinterpret_cast<int *>(T + 32 * E * 17);
+  int *s_start = reinterpret_cast<int *>(T + trows_elems<E>());
   for (int i = threadIdx.x; i <= npass; i += blockDim.x) s_start[i] = pass_start[i];
   __syncthreads();
   const int total = s_start[npass];
@@ -722,9 +847,11 @@ __global__ void __launch_bounds__(SF_FAST_THREADS)
     if (s_ok) {
       const int tile = it - s_start[s_pass];
       const int kind = sPass.kind;
-      if (kind == FK_YF) fast_yf<E, PAD>(sP, g, sPass, tile, wsm, T);
-      else if (kind == FK_ZS) fast_zs<E, NC, PAD, OPS>(sP, g, sPass, tile, wsm);
-      else fast_yi<E, PAD>(sP, g, sPass, tile, wsm, T);
+      if (kind == FK_YF) fast_yf<E, PAD, MM == 1 ? 1 : 2>(sP, g, sPass, tile, wsm, T);
+      else if (kind == FK_ZS) {
+        if (OPS == 2) fast_zs_split<E, PAD>(sP, g, sPass, tile, wsm);
+        else fast_zs<E, NC, PAD, OPS>(sP, g, sPass, tile, wsm);
+      } else fast_yi<E, PAD, OPS == 2, MM == 1 ? 1 : 2>(sP, g, sPass, tile, wsm, T);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -759,14 +886,15 @@ int sf_fast_launch_e8(const FastLaunch &fl, const IOArgs<float> &io, int *launch
 int sf_fast_launch_e16(const FastLaunch &fl, const IOArgs<float> &io, int *launches);
 
 template <int E> size_t fast_x_smem() { return (size_t)(fast_wsm_elems<E, 1>() + (16 * E + 1) * 17) * sizeof(float2); }
-#define SF_FAST_MAXPASS 2048
-template <int E> size_t fast_yz_smem() {
-  return (size_t)(fast_wsm_elems<E, SF_YZ_MAXM>() + 32 * E * 17) * sizeof(float2) + (SF_FAST_MAXPASS + 1) * sizeof(int);
+#define SF_FAST_MAXPASS 1024
+template <int E, int OPS> size_t fast_yz_smem() {
+  return (size_t)(fast_wsm_elems<E, fast_yz_lines(OPS)>() + trows_elems<E>()) * sizeof(float2) +
+         (SF_FAST_MAXPASS + 1) * sizeof(int);
 }
 
 template <int E, int NC, bool PAD, int OPS> int fast_launch_yz(const FastLaunch &fl, const IOArgs<float> &io) {
   static bool attr = false;
-  const size_t smyz = fast_yz_smem<E>();
+  const size_t smyz = fast_yz_smem<E, OPS>();
   cudaError_t e;
   if (!attr) {
     e = cudaFuncSetAttribute(k_fyz<E, NC, PAD, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smyz);
@@ -810,7 +938,8 @@ template <int E, bool PAD> int fast_launch_all(const FastLaunch &fl, const IOArg
     if ((e = cudaMemsetAsync(fl.d_done, 0, fl.npass * sizeof(unsigned), fl.stream)) != cudaSuccess) return (int)e;
     if ((e = cudaMemsetAsync(fl.ctl, 0, sizeof(ExecCtl), fl.stream)) != cudaSuccess) return (int)e;
     int r;
-    if (Q.ncomp == 3 && Q.op == OPK_CURL) r = fast_launch_yz<E, 3, PAD, 1>(fl, io);
+    if (fast_split_curl(Q)) r = fast_launch_yz<E, 3, PAD, 2>(fl, io);
+    else if (Q.ncomp == 3 && Q.op == OPK_CURL) r = fast_launch_yz<E, 3, PAD, 1>(fl, io);
     else if (Q.ncomp == 3) r = fast_launch_yz<E, 3, PAD, 0>(fl, io);
     else if (Q.ncomp == 2) r = fast_launch_yz<E, 2, PAD, 0>(fl, io);
     else r = fast_launch_yz<E, 1, PAD, 0>(fl, io);

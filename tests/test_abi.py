@@ -87,6 +87,7 @@ def test_status_strings_and_version(lib):
     (dict(tune_radix=3), -1),
     (dict(tune_tile=3), -1),
     (dict(tune_slab=-1), -1),
+    (dict(tune_lag=9), -1),
 ])
 def test_descriptor_validation_without_gpu(lib, mutate, expect):
     from paper_2301_01145_gb300 import _lib
