@@ -53,14 +53,64 @@ def algorithmic_bytes(n: int, elem: int = 4):
     return b_io, b_method
 
 
+# FP32 lanes per SM and SM count of a GB300 (Blackwell Ultra); one FMA = 2 flops
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def transform_flops(n: int):
+    """Transform flops of the three kernels of one solve, standard FFT count.
+
+    Counted as 5 L log2 L per complex line of length L and 2.5 L log2 L per
+    real line (the usual FFT benchmark convention), over the line transforms
+    each kernel performs for the n^3 vector curl solve padded to L = 2n:
+      x forward (k_fx):   3 fields x n^2 real lines,
+      y/z executor (k_fyz, split curl): y forward 3 x (n+1) x n, z forward
+                          3 x (n+1) x L, z inverse 5 x (n+1) x L (psi and
+                          d/dz of two components), y inverse 6 x (n+1) x n,
+      x inverse (k_fxi):  6 fields x n^2 real lines.
+    Pruned transforms (half the input or output zero) are counted at full
+    length; spectral multiplies are not counted.
+    """
+    L = 2 * n
+    lg = math.log2(L)
+    cplx = 5 * L * lg
+    real = 2.5 * L * lg
+    nk = n + 1
+    return {"x_forward": 3 * n * n * real,
+            "yz_executor": (3 * n + 3 * L + 5 * L + 6 * n) * nk * cplx,
+            "x_inverse": 6 * n * n * real}
+
+
+def kernel_bytes(n: int, elem: int = 4):
+    """Algorithmic HBM bytes of each kernel of one solve (FP32).
+
+    x forward reads omega (3 n^3) and writes the x half-spectrum A
+    (3 x (n+1) x n x n complex); the y/z executor reads A and the Green's
+    octant ((n+1)^3 real) and writes B (6 x (n+1) x n x n complex); x inverse
+    reads B and writes psi and u (6 n^3).
+    """
+    half = (n + 1) * n * n * 2 * elem
+    field = n ** 3 * elem
+    return {"x_forward": 3 * field + 3 * half,
+            "yz_executor": 3 * half + (n + 1) ** 3 * elem + 6 * half,
+            "x_inverse": 6 * half + 6 * field}
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_fyz launch of this
+# workload (256^3 curl, split z stage), from the ncu capture summarised in
+# profiles/k_fyz_c3_256.md; None when the kernel has changed since.
+K_FYZ_TRAFFIC_256 = 596_018_688 + 1_704_366_000
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), "measured", float(d.get("sm_max_mhz", 2070.0))
     except Exception:
-        return HBM_FALLBACK, "fallback"
+        return HBM_FALLBACK, "fallback", 2070.0
 
 
 class ClockSampler:
@@ -337,6 +387,7 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.15)
+    plan.timing(True)  # CUDA events between this plan's kernels, on its launch stream
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -359,13 +410,40 @@ def main():
     value = points * world / (ms * 1e-3)
     launches = plan.launches() * args.steps
 
-    # roofline of the dominant (and, fused, only) kernel: the persistent executor
-    peak, peak_kind = read_peaks()
+    kms, ksolves = plan.kernel_ms()
+    plan.timing(False)
+
+    # roofline of the dominant kernel (the y/z executor, bound by FP32 issue),
+    # timed per launch by the events above; the other kernels and the whole
+    # step against HBM for context
+    hbm_peak, peak_kind, sm_mhz = read_peaks()
+    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
     b_io, b_method = algorithmic_bytes(n)
-    achieved = b_method / (ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "bytes_model": "B_method", "algorithmic_bytes": b_method,
-            "b_io_bytes": b_io, "b_io_frac": b_io / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_kind}
+    kb, kf = kernel_bytes(n), transform_flops(n)
+    names = ["x_forward", "yz_executor", "x_inverse"]
+    kernels = {}
+    if len(kms) == 3 and not args.unfused:
+        for k, name in enumerate(names):
+            t = kms[k] * 1e-3
+            kernels[name] = {"ms": kms[k], "share": kms[k] / sum(kms), "GB/s": kb[name] / t / 1e9,
+                             "hbm_frac": kb[name] / t / 1e9 / hbm_peak, "TFLOP/s": kf[name] / t / 1e12,
+                             "alu_frac": kf[name] / t / 1e12 / alu_peak, "bytes": kb[name], "flops": kf[name]}
+        dom = kernels["yz_executor"]
+        roof = {"bound": "alu", "kernel": "k_fyz (y/z executor)", "achieved": dom["TFLOP/s"], "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": dom["alu_frac"],
+                "traffic": K_FYZ_TRAFFIC_256 if n == 256 else None, "algorithmic_bytes": kb["yz_executor"],
+                "algorithmic_flops": kf["yz_executor"],
+                "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz",
+                "kernels": kernels, "solves_timed": ksolves,
+                "step_hbm": {"achieved": b_method / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": b_method / (ms * 1e-3) / 1e9 / hbm_peak, "bytes_model": "B_method",
+                             "algorithmic_bytes": b_method, "b_io_bytes": b_io,
+                             "b_io_frac": b_io / (ms * 1e-3) / 1e9 / hbm_peak, "peak_source": peak_kind}}
+    else:
+        achieved = b_method / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "whole step", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "bytes_model": "B_method", "algorithmic_bytes": b_method,
+                "b_io_bytes": b_io, "b_io_frac": b_io / (ms * 1e-3) / 1e9 / hbm_peak, "peak_source": peak_kind}
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     e2e = None

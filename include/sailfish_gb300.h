@@ -211,6 +211,24 @@ int sf_plan_launches(sf_plan p);
  * the per-pass breakdown of the GPU schedule. */
 sf_status sf_plan_stats(sf_plan p, double out[24]);
 
+/* Per-kernel CUDA-event timing of a plan (diagnostic, off by default).
+ * enable = 1 creates the events on first use and clears the record; from then
+ * on every full solve (sf_solve, sf_execute, sf_solve_host) records an event on
+ * the plan's stream before its first kernel, between consecutive kernels and
+ * after its last one.  enable = 0 stops recording.  Waits for the plan's
+ * stream.  Solves enqueued while the stream is being captured into a graph are
+ * not recorded.  SF_ERR_ARG for a null plan or a batch. */
+sf_status sf_plan_timing(sf_plan p, int enable);
+
+/* Mean device time in milliseconds of each kernel slot over the solves
+ * recorded since timing was enabled (the last 256 at most); waits for the
+ * plan's stream.  Register fast path: 3 slots (ms[0] x forward transform,
+ * ms[1] the y/z executor, ms[2] x inverse transform); general engine: 1 slot
+ * (the executor, all its launches).  ms must hold 4 doubles; unused slots are
+ * 0.  *nslot and *nsolve (either may be NULL) receive the slot count and the
+ * number of solves averaged (0 when nothing was recorded). */
+sf_status sf_plan_kernel_ms(sf_plan p, double ms[4], int *nslot, int *nsolve);
+
 /* A bounded solve that allocates nothing, for callers that cannot call
  * cudaMalloc (code inside host callbacks or driver hooks that must not
  * allocate, real-time loops that forbid allocation after start-up, processes

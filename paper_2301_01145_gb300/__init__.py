@@ -16,7 +16,8 @@ from typing import Optional, Sequence
 from . import _lib
 from ._lib import SolverError  # noqa: F401
 from ._lib import (sf_batch_create, sf_batch_solve, sf_execute, sf_get_output, sf_plan_create,  # noqa: F401
-                   sf_plan_destroy, sf_plan_launches, sf_plan_query, sf_plan_stats, sf_set_boundary, sf_set_source, sf_solve,
+                   sf_plan_destroy, sf_plan_kernel_ms, sf_plan_launches, sf_plan_query, sf_plan_stats,
+                   sf_plan_timing, sf_set_boundary, sf_set_source, sf_solve,
                    sf_solve_adjoint, sf_solve_host, sf_sync, sf_version)
 
 
@@ -99,6 +100,14 @@ class Plan:
 
     def stats(self):
         return sf_plan_stats(self.handle)
+
+    def timing(self, enable: bool = True):
+        """Start (and clear) or stop per-kernel CUDA-event timing of full solves."""
+        sf_plan_timing(self.handle, enable)
+
+    def kernel_ms(self):
+        """(mean device ms of each kernel slot, number of solves averaged)."""
+        return sf_plan_kernel_ms(self.handle)
 
     def _check_input(self, f):
         if tuple(f.shape) != tuple(self.in_shape) or f.dtype != self.dtype or not f.is_cuda or not f.is_contiguous():

@@ -79,6 +79,8 @@ SIGNATURES = {
     "sf_selftest_timeout": (c_int, [c_int, c_void_p]),
     "sf_solve_static": (c_int, [POINTER(sf_plan_desc), c_void_p, c_void_p, c_void_p]),
     "sf_plan_stats": (c_int, [c_void_p, POINTER(c_double)]),
+    "sf_plan_timing": (c_int, [c_void_p, c_int]),
+    "sf_plan_kernel_ms": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), POINTER(c_int)]),
     "sf_plan_destroy": (c_int, [c_void_p]),
     "sf_status_string": (c_char_p, [c_int]),
     "sf_last_error": (c_char_p, []),
@@ -228,6 +230,18 @@ def sf_plan_stats(plan):
     out = (c_double * 24)()
     _check(load().sf_plan_stats(plan, out), "sf_plan_stats")
     return [(out[3 * k], out[3 * k + 1], int(out[3 * k + 2])) for k in range(8)]
+
+
+def sf_plan_timing(plan, enable: bool):
+    _check(load().sf_plan_timing(plan, 1 if enable else 0), "sf_plan_timing")
+
+
+def sf_plan_kernel_ms(plan):
+    """(mean ms per kernel slot, solves averaged) since timing was enabled."""
+    ms = (c_double * 4)()
+    ns, nsol = c_int(0), c_int(0)
+    _check(load().sf_plan_kernel_ms(plan, ms, ctypes.byref(ns), ctypes.byref(nsol)), "sf_plan_kernel_ms")
+    return [ms[k] for k in range(ns.value)], nsol.value
 
 
 def sf_plan_destroy(plan):

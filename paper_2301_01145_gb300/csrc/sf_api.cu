@@ -406,12 +406,48 @@ template <typename T> sf_status upload_fast(FastList &fl, DevMem<T> &mem) {
 // ---------------------------------------------------------------------------
 // the plan object
 // ---------------------------------------------------------------------------
+// CUDA-event marks around the kernels of full solves: one event before the
+// first kernel, between consecutive kernels and after the last; a ring keeps
+// the marks of the last kRing solves.
+struct KernelTimer {
+  static const int kRing = 256, kMarks = 4;
+  bool on = false;
+  long long count = 0;
+  int nmark = 0;  // marks of the last recorded solve (slots = nmark - 1)
+  std::vector<cudaEvent_t> ev;
+  ~KernelTimer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  sf_status enable(bool en) {
+    if (en && ev.empty()) {
+      ev.resize(kRing * kMarks, nullptr);
+      for (auto &e : ev) SF_CK(cudaEventCreate(&e));
+    }
+    on = en;
+    count = 0;
+    nmark = 0;
+    return SF_OK;
+  }
+  // the marks of the next solve, or nullptr when timing is off or the stream is being captured
+  cudaEvent_t *next(cudaStream_t st) {
+    if (!on) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    return &ev[(size_t)(count % kRing) * kMarks];
+  }
+  void done(int marks) {
+    nmark = marks;
+    ++count;
+  }
+};
+
 struct sf_plan_s {
   virtual ~sf_plan_s() {}
   sf_plan_desc d{};
   cudaStream_t stream = nullptr;
   bool is_batch = false;
   int launches_per_exec = 0;
+  KernelTimer timer;
   virtual sf_status solve_part(bool front, bool back, const void *f, void *psi, void *op, int *launches) = 0;
   virtual sf_status adjoint(const void *gp, const void *go, void *gf) = 0;
   virtual sf_status sync() = 0;
@@ -461,12 +497,25 @@ template <typename T> struct PlanImpl : sf_plan_s {
   sf_status build_green();
 
   sf_status run_fast(const Prob<T> &Q, const Prob<T> *dq, FastList &fl, bool front, bool back, const IOArgs<T> &io,
-                     int *launches);
+                     int *launches, cudaEvent_t *marks = nullptr);
 
   sf_status solve_part(bool front, bool back, const void *f, void *psi, void *op, int *launches) override {
     IOArgs<T> io = io_forward(f, psi, op);
-    if (fastE) return run_fast(P, d_probs, fl_fwd, front, back, io, launches);
-    if (front && back) return launch_list<T>(ex_all, d_probs, fused(), stream, ctl, sticky, io, launches);
+    cudaEvent_t *mk = front && back ? timer.next(stream) : nullptr;
+    if (fastE) {
+      SF_TRY(run_fast(P, d_probs, fl_fwd, front, back, io, launches, mk));
+      if (mk) timer.done(4);
+      return SF_OK;
+    }
+    if (front && back) {
+      if (mk) SF_CK(cudaEventRecord(mk[0], stream));
+      SF_TRY(launch_list<T>(ex_all, d_probs, fused(), stream, ctl, sticky, io, launches));
+      if (mk) {
+        SF_CK(cudaEventRecord(mk[1], stream));
+        timer.done(2);
+      }
+      return SF_OK;
+    }
     if (front) return launch_list<T>(ex_front, d_probs, fused(), stream, ctl, sticky, io, launches);
     return launch_list<T>(ex_back, d_probs, fused(), stream, ctl, sticky, io, launches);
   }
@@ -541,13 +590,15 @@ template <typename T> struct PlanImpl : sf_plan_s {
 };
 
 template <typename T>
-sf_status PlanImpl<T>::run_fast(const Prob<T> &, const Prob<T> *, FastList &, bool, bool, const IOArgs<T> &, int *) {
+sf_status PlanImpl<T>::run_fast(const Prob<T> &, const Prob<T> *, FastList &, bool, bool, const IOArgs<T> &, int *,
+                                cudaEvent_t *) {
   return fail(SF_ERR_UNSUPPORTED, "fast path is FP32 only");
 }
 template <>
 sf_status PlanImpl<float>::run_fast(const Prob<float> &Q, const Prob<float> *dq, FastList &fl, bool front, bool back,
-                                    const IOArgs<float> &io, int *launches) {
+                                    const IOArgs<float> &io, int *launches, cudaEvent_t *marks) {
   FastLaunch L{};
+  L.marks = marks;
   L.d_prob = dq;
   L.h_prob = &Q;
   L.geo = geo;
@@ -1250,6 +1301,33 @@ sf_status sf_plan_stats(sf_plan p, double out[24]) {
     out[3 * k + 1] = (double)c.wait_ns[k];
     out[3 * k + 2] = (double)c.tiles[k];
   }
+  return SF_OK;
+}
+
+sf_status sf_plan_timing(sf_plan p, int enable) {
+  if (!p || p->is_batch) return fail(SF_ERR_ARG, "null plan or a batch");
+  if (p->stream) SF_CK(cudaStreamSynchronize(p->stream));
+  else SF_CK(cudaDeviceSynchronize());
+  return p->timer.enable(enable != 0);
+}
+
+sf_status sf_plan_kernel_ms(sf_plan p, double ms[4], int *nslot, int *nsolve) {
+  if (!p || !ms || p->is_batch) return fail(SF_ERR_ARG, "null argument or a batch");
+  KernelTimer &t = p->timer;
+  for (int k = 0; k < 4; ++k) ms[k] = 0.0;
+  const int nsol = (int)(t.count < KernelTimer::kRing ? t.count : KernelTimer::kRing);
+  const int ns = t.nmark > 1 ? t.nmark - 1 : 0;
+  if (nslot) *nslot = ns;
+  if (nsolve) *nsolve = nsol;
+  if (!t.on || nsol == 0) return SF_OK;
+  SF_CK(cudaStreamSynchronize(p->stream));
+  for (int i = 0; i < nsol; ++i)
+    for (int k = 0; k < ns; ++k) {
+      float e = 0.f;
+      SF_CK(cudaEventElapsedTime(&e, t.ev[(size_t)i * KernelTimer::kMarks + k], t.ev[(size_t)i * KernelTimer::kMarks + k + 1]));
+      ms[k] += e;
+    }
+  for (int k = 0; k < ns; ++k) ms[k] /= nsol;
   return SF_OK;
 }
 

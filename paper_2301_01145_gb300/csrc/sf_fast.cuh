@@ -879,6 +879,7 @@ struct FastLaunch {
   unsigned long long timeout_ns;
   bool front, back;
   cudaStream_t stream;
+  cudaEvent_t *marks;  // 4 events around k_fx, k_fyz, k_fxi of a full solve, or nullptr
 };
 
 // defined in sf_fast8.cu / sf_fast16.cu; return a cudaError_t value
@@ -932,11 +933,14 @@ template <int E, bool PAD> int fast_launch_all(const FastLaunch &fl, const IOArg
       return (int)e;
     attr = true;
   }
+  cudaEvent_t *mk = fl.front && fl.back ? fl.marks : nullptr;
+  if (mk && (e = cudaEventRecord(mk[0], fl.stream)) != cudaSuccess) return (int)e;
   if (fl.front) {
     k_fx<E, PAD><<<Q.nin * Q.nuz * cdiv(Q.nuy, 16), SF_FAST_THREADS, smx, fl.stream>>>(fl.d_prob, io);
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     if ((e = cudaMemsetAsync(fl.d_done, 0, fl.npass * sizeof(unsigned), fl.stream)) != cudaSuccess) return (int)e;
     if ((e = cudaMemsetAsync(fl.ctl, 0, sizeof(ExecCtl), fl.stream)) != cudaSuccess) return (int)e;
+    if (mk && (e = cudaEventRecord(mk[1], fl.stream)) != cudaSuccess) return (int)e;
     int r;
     if (fast_split_curl(Q)) r = fast_launch_yz<E, 3, PAD, 2>(fl, io);
     else if (Q.ncomp == 3 && Q.op == OPK_CURL) r = fast_launch_yz<E, 3, PAD, 1>(fl, io);
@@ -944,11 +948,13 @@ template <int E, bool PAD> int fast_launch_all(const FastLaunch &fl, const IOArg
     else if (Q.ncomp == 2) r = fast_launch_yz<E, 2, PAD, 0>(fl, io);
     else r = fast_launch_yz<E, 1, PAD, 0>(fl, io);
     if (r) return r;
+    if (mk && (e = cudaEventRecord(mk[2], fl.stream)) != cudaSuccess) return (int)e;
     if (launches) *launches += 2;
   }
   if (fl.back) {
     k_fxi<E, PAD><<<Q.nout * Q.nuz * cdiv(Q.nuy, 16), SF_FAST_THREADS, smx, fl.stream>>>(fl.d_prob, io);
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    if (mk && (e = cudaEventRecord(mk[3], fl.stream)) != cudaSuccess) return (int)e;
     if (launches) *launches += 1;
   }
   return 0;

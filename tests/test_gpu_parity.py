@@ -305,3 +305,25 @@ def test_small_batch_matches_single_solves_and_oracle():
     batch.close()
     for p in plans:
         p.close()
+
+
+def test_kernel_timing_slots():
+    # per-kernel CUDA-event timing: 3 slots on the register path, 1 on the general engine
+    import torch
+    import paper_2301_01145_gb300 as sf
+    for generic, nslot in ((False, 3), (True, 1)):
+        plan = sf.Plan(3, (128,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=2 / 128,
+                       rhs_scale=-1.0, generic=generic)
+        f = torch.randn(plan.in_shape, device="cuda")
+        psi, u = plan.empty_outputs()
+        ms, nsol = plan.kernel_ms()
+        assert nsol == 0
+        plan.timing(True)
+        for _ in range(3):
+            plan.execute(f, psi, u)
+        ms, nsol = plan.kernel_ms()
+        assert nsol == 3 and len(ms) == nslot and all(t > 0 for t in ms)
+        plan.timing(False)
+        plan.execute(f, psi, u)
+        plan.sync()
+        plan.close()
