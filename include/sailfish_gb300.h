@@ -109,7 +109,7 @@ typedef struct {
    *   tune_radix  largest radix of the general FFT engine (2, 4, 8 or 16)
    *   tune_tile   largest number of packed lines per tile of the general engine (1..16, power of 2)
    *   tune_slab   kx planes per slab of the register fast path's pipeline (>= 1)
-   *   tune_lag    slabs between the pipeline's stages (>= 1; ring depth = lag + 1) */
+   *   tune_lag    slabs between the pipeline's stages (>= 1; ring depth = lag + 2) */
   int32_t tune_radix;
   int32_t tune_tile;
   int32_t tune_slab;

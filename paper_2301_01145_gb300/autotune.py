@@ -56,7 +56,7 @@ def candidates(problem: Dict) -> List[Dict]:
     cands = [dict(tune_radix=0, tune_tile=0, tune_slab=0, fused=True)]
     for r, t in itertools.product((16, 8, 4), (16, 8, 4)):
         cands.append(dict(tune_radix=r, tune_tile=t, tune_slab=0, fused=True))
-    for sl, lag in itertools.product((2, 4, 8, 16), (1, 2)):
+    for sl, lag in itertools.product((1, 2, 3, 4, 8), (1, 2)):
         cands.append(dict(tune_radix=0, tune_tile=0, tune_slab=sl, tune_lag=lag, fused=True))
     cands.append(dict(tune_radix=0, tune_tile=0, tune_slab=0, fused=False))
     uniq, seen = [], set()

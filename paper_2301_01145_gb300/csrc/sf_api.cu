@@ -345,13 +345,15 @@ struct FastList {
 };
 
 // slab pipeline with stage lag D: step t issues YF(t), ZS(t-D), YI(t-2D).  The
-// I1 / I2 rings have nslot = D + 1 slabs, so a slot is rewritten only after the
-// pass that reads it was issued at least one step earlier (dependency edges
-// below); every dependency points to an earlier item of the list.
+// I1 / I2 rings have nslot = D + 2 slabs: a slot is rewritten only after the
+// pass that reads it (dependency edges below), and with one slot beyond the D + 1
+// in flight that pass was issued a full step (all three passes) earlier, so the
+// wait is normally already satisfied.  Every dependency points to an earlier
+// item of the list.  Unfused plans (nslot = 1) launch the passes one by one.
 template <typename T>
 void build_fast_list(const Prob<T> &Q, int S, int nslot, int L, FastList &fl) {
   const int nslab = cdiv(Q.nsx, S);
-  const int D = nslot > 1 ? nslot - 1 : 1;
+  const int D = nslot > 2 ? nslot - 2 : 1;
   std::vector<int> iyf(nslab, -1), izs(nslab, -1), iyi(nslab, -1);
   auto push = [&](int kind, int s) {
     FPass p{};
@@ -791,10 +793,10 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   if (sizeof(T) == 4 && d.dim == 3 && p.cpath && !(d.flags & SF_FLAG_GENERIC) && p.ax[0].L == p.ax[1].L &&
       p.ax[1].L == p.ax[2].L && (p.ax[0].L == 512 || p.ax[0].L == 256)) {
     fastE = p.ax[0].L / 32;
-    int S = d.tune_slab > 0 ? d.tune_slab : 4;
+    int S = d.tune_slab > 0 ? d.tune_slab : 2;
     const int lag = d.tune_lag > 0 ? d.tune_lag : 1;
     geo.S = fused() ? std::min(S, p.nsx) : p.nsx;
-    geo.nslot = fused() ? lag + 1 : 1;
+    geo.nslot = fused() ? lag + 2 : 1;
     geo.nfmax = nf;
     eI = (size_t)geo.nslot * nf * geo.S * p.ax[1].L * p.nuz;
   }
@@ -866,6 +868,9 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   if (fastE) {
     build_fast_list<T>(P, geo.S, geo.nslot, p.ax[1].L, fl_fwd);
     build_fast_list<T>(PA, geo.S, geo.nslot, p.ax[1].L, fl_adj);
+    // the executor packs the pass table into shared memory (see k_fyz)
+    if (fl_fwd.passes.size() > SF_FAST_MAXPASS || fl_adj.passes.size() > SF_FAST_MAXPASS)
+      return fail(SF_ERR_UNSUPPORTED, "too many slab passes for the register path; raise tune_slab");
     SF_TRY(upload_fast<T>(fl_fwd, mem));
     SF_TRY(upload_fast<T>(fl_adj, mem));
     launches_per_exec = 3;

@@ -488,6 +488,17 @@ __device__ __forceinline__ void fast_yf(const Prob<float> &P, const FastGeo &g, 
 }
 
 // multiplier of the fast path: Green's table in [kx][ky'][kz'] order (kz fastest) or eigenvalue sum
+// asynchronous global -> shared copies (4 bytes each), completed by cp_async_wait_all
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// per-warp staging row of the Green's table in the z stage (floats; >= L / 2 + 1)
+#define SF_ZS_GROW 264
+
 __device__ __forceinline__ float fast_mult(const Prob<float> &P, int kx, int ky, int kz) {
   if (P.green) {
     const int L = P.ax[2].L;
@@ -638,7 +649,7 @@ __device__ __forceinline__ void fast_zs_row(const Prob<float> &P, const FastGeo 
 // psi_c (I2 field c) and, for c = x, y, d/dz psi_c (I2 field 3 + c).
 template <int E, bool PAD>
 __device__ __forceinline__ void fast_zs_split(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
-                                              cx<float> *wsm) {
+                                              cx<float> *wsm, float *gstage) {
   typedef cx<float> V;
   constexpr int L = 32 * E;
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
@@ -655,6 +666,15 @@ __device__ __forceinline__ void fast_zs_split(const Prob<float> &P, const FastGe
   const V *I1 = reinterpret_cast<const V *>(P.I1) + slot;
   V *I2 = reinterpret_cast<V *>(P.I2) + slot;
   const V *tz = P.ax[2].tw;
+  // Green's row of (kx, |ky|) staged in shared memory by asynchronous copies
+  // that complete while the forward transform runs (unbounded axes only)
+  float *gs = gstage + warp * SF_ZS_GROW;
+  if (PAD && P.green) {
+    const int kyf = min(ky, L - ky);
+    const float *grow = P.ghat_t + ((size_t)kx * P.gny + kyf) * P.gnz;
+    for (int i = t; i < P.gnz; i += 32) cp_async4(gs + i, grow + i);
+    cp_async_commit();
+  }
   V sp[1][E];
   {
     const V *src = I1 + (((size_t)c * g.S + kxl) * L + ky) * nuz;
@@ -665,8 +685,18 @@ __device__ __forceinline__ void fast_zs_split(const Prob<float> &P, const FastGe
     }
   }
   wfft_fwd_m<float, E, PAD, 1>(sp, wsm, tz);
+  if (PAD && P.green) {
+    cp_async_wait_all();
+    __syncwarp();
 #pragma unroll
-  for (int j = 0; j < E; ++j) sp[0][j] = cscale(sp[0][j], fast_mult(P, kx, ky, klayout<E>(t, j)));
+    for (int j = 0; j < E; ++j) {
+      const int kz = klayout<E>(t, j);
+      sp[0][j] = cscale(sp[0][j], gs[min(kz, L - kz)]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < E; ++j) sp[0][j] = cscale(sp[0][j], fast_mult(P, kx, ky, klayout<E>(t, j)));
+  }
   if (c < 2) {
     V dz[1][E];
 #pragma unroll
@@ -782,7 +812,11 @@ __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, 
 }
 
 // persistent YZ executor over the slab work list (same queue / bounded-wait
-// protocol as k_exec)
+// protocol as k_exec).  The pass table is packed into shared memory at start;
+// thread 0 claims items and waits for their dependencies, thread 32 publishes
+// the completion of the previous tile, so the two round trips to L2 overlap.
+// The per-tile descriptor is double-buffered: thread 0 fills slot (k+1) & 1
+// while thread 32 still reads slot k & 1.
 template <int E, int NC, bool PAD, int OPS>
 __global__ void __launch_bounds__(SF_FAST_THREADS, OPS == 2 ? 2 : 1)
     k_fyz(const Prob<float> *probs, FastGeo g, const FPass *passes, const int *pass_start, int npass, unsigned *done,
@@ -790,75 +824,94 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS == 2 ? 2 : 1)
   typedef cx<float> V;
   extern __shared__ __align__(16) unsigned char fsm[];
   __shared__ __align__(16) Prob<float> sP;
-  __shared__ FPass sPass;
-  __shared__ int s_item, s_pass, s_ok;
+  __shared__ FPass sPass[2];
+  __shared__ int s_item[2], s_pass[2], s_ok[2];
+  __shared__ unsigned long long s_tbusy[2];
   load_prob<float>(sP, probs, io);
   constexpr int MM = fast_yz_lines(OPS);  // interleaved lines per warp (warp buffer depth)
   V *wsm_all = reinterpret_cast<V *>(fsm);
   V *T = wsm_all + fast_wsm_elems<E, MM>();
   V *wsm = wsm_all + (threadIdx.x >> 5) * MM * E * wrow<E>();
-  // pass start table cached in shared memory (after the tile buffer)
+  // packed pass table after the tile buffer: start[npass + 1], then per pass
+  // a = kind | slot << 2 | nkx << 6 | kx0 << 16 and b = (dep0 + 1) | (dep1 + 1) << 16
   int *s_start = reinterpret_cast<int *>(T + trows_elems<E>());
+  int *s_pa = s_start + npass + 1;
+  int *s_pb = s_pa + npass;
   for (int i = threadIdx.x; i <= npass; i += blockDim.x) s_start[i] = pass_start[i];
+  for (int i = threadIdx.x; i < npass; i += blockDim.x) {
+    const FPass &q = passes[i];
+    s_pa[i] = q.kind | (q.slot << 2) | (q.nkx << 6) | (q.kx0 << 16);
+    s_pb[i] = (q.dep[0] + 1) | ((q.dep[1] + 1) << 16);
+  }
   __syncthreads();
   const int total = s_start[npass];
   int next_it = 0;  // thread 0: item claimed one iteration ahead (queue round trip overlaps a tile)
   int cur = 0;      // thread 0: pass of the last item (items arrive in increasing order)
-  unsigned long long t_wait0 = 0, t_busy0 = 0;  // thread 0: tracing timestamps
   if (threadIdx.x == 0) next_it = (int)atomicAdd(&ctl->next, 1u);
-  for (;;) {
+  for (int k = 0;; k ^= 1) {
     if (threadIdx.x == 0) {
       const int it = next_it;
       if (it < total) next_it = (int)atomicAdd(&ctl->next, 1u);
-      s_item = it;
-      s_ok = 1;
+      s_item[k] = it;
+      s_ok[k] = 1;
       if (it < total) {
         while (s_start[cur + 1] <= it) ++cur;
         const int lo = cur;
-        s_pass = lo;
-        sPass = passes[lo];
-        t_wait0 = global_ns();
-        for (int d = 0; d < 2 && s_ok; ++d) {
-          const int dp = sPass.dep[d];
+        FPass &sp = sPass[k];
+        const int a = s_pa[lo], b = s_pb[lo];
+        sp.kind = a & 3;
+        sp.slot = (a >> 2) & 15;
+        sp.nkx = (a >> 6) & 1023;
+        sp.kx0 = a >> 16;
+        sp.ntiles = s_start[lo + 1] - s_start[lo];
+        s_pass[k] = lo;
+        const unsigned long long tw0 = global_ns();
+        for (int d = 0; d < 2; ++d) {
+          const int dp = ((d ? b >> 16 : b) & 0xffff) - 1;
           if (dp < 0) continue;
-          const unsigned need = (unsigned)sPass.depcnt[d];
-          const unsigned long long t0 = global_ns();
+          const unsigned need = (unsigned)(s_start[dp + 1] - s_start[dp]);
           unsigned iters = 0;
+          bool ok = true;
           while (ld_acquire(&done[dp]) < need) {
             __nanosleep(64);
-            if (((++iters) & 255u) == 0 && (global_ns() - t0 > timeout_ns || iters > (1u << 28))) {
+            if (((++iters) & 255u) == 0 && (global_ns() - tw0 > timeout_ns || iters > (1u << 28))) {
               atomicCAS(&ctl->error, 0u, 6u);
               atomicExch(&ctl->err_pass, (unsigned)lo);
               atomicOr(sticky, 1u);
-              s_ok = 0;
+              ok = false;
               break;
             }
           }
+          if (!ok) {
+            s_ok[k] = 0;
+            break;
+          }
         }
+        const unsigned long long tb = global_ns();
+        s_tbusy[k] = tb;
+        atomicAdd(&ctl->wait_ns[a & 3], tb - tw0);
       }
     }
-    if (threadIdx.x == 0 && s_item < total) {
-      t_busy0 = global_ns();
-      atomicAdd(&ctl->wait_ns[sPass.kind], t_busy0 - t_wait0);
-    }
     __syncthreads();
-    const int it = s_item;
+    const int it = s_item[k];
     if (it >= total) break;
-    if (s_ok) {
-      const int tile = it - s_start[s_pass];
-      const int kind = sPass.kind;
-      if (kind == FK_YF) fast_yf<E, PAD, MM == 1 ? 1 : 2>(sP, g, sPass, tile, wsm, T);
+    if (s_ok[k]) {
+      const FPass &ps = sPass[k];
+      const int tile = it - s_start[s_pass[k]];
+      const int kind = ps.kind;
+      if (kind == FK_YF) fast_yf<E, PAD, MM == 1 ? 1 : 2>(sP, g, ps, tile, wsm, T);
       else if (kind == FK_ZS) {
-        if (OPS == 2) fast_zs_split<E, PAD>(sP, g, sPass, tile, wsm);
-        else fast_zs<E, NC, PAD, OPS>(sP, g, sPass, tile, wsm);
-      } else fast_yi<E, PAD, OPS == 2, MM == 1 ? 1 : 2>(sP, g, sPass, tile, wsm, T);
+        if (OPS == 2) fast_zs_split<E, PAD>(sP, g, ps, tile, wsm, reinterpret_cast<float *>(T));
+        else fast_zs<E, NC, PAD, OPS>(sP, g, ps, tile, wsm);
+      } else fast_yi<E, PAD, OPS == 2, MM == 1 ? 1 : 2>(sP, g, ps, tile, wsm, T);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 32) {
       __threadfence();
-      atomicAdd(&done[s_pass], 1u);
-      atomicAdd(&ctl->busy_ns[sPass.kind], global_ns() - t_busy0);
-      atomicAdd(&ctl->tiles[sPass.kind], 1ull);
+      atomicAdd(&done[s_pass[k]], 1u);
+      const int kind = sPass[k].kind;
+      atomicAdd(&ctl->busy_ns[kind], global_ns() - s_tbusy[k]);
+      atomicAdd(&ctl->tiles[kind], 1ull);
     }
   }
 }
@@ -888,17 +941,20 @@ int sf_fast_launch_e16(const FastLaunch &fl, const IOArgs<float> &io, int *launc
 
 template <int E> size_t fast_x_smem() { return (size_t)(fast_wsm_elems<E, 1>() + (16 * E + 1) * 17) * sizeof(float2); }
 #define SF_FAST_MAXPASS 1024
-template <int E, int OPS> size_t fast_yz_smem() {
+// dynamic shared memory of k_fyz: warp buffers, tile buffer, packed pass table
+template <int E, int OPS> size_t fast_yz_smem(int npass) {
   return (size_t)(fast_wsm_elems<E, fast_yz_lines(OPS)>() + trows_elems<E>()) * sizeof(float2) +
-         (SF_FAST_MAXPASS + 1) * sizeof(int);
+         (size_t)(3 * npass + 1) * sizeof(int);
 }
 
 template <int E, int NC, bool PAD, int OPS> int fast_launch_yz(const FastLaunch &fl, const IOArgs<float> &io) {
   static bool attr = false;
-  const size_t smyz = fast_yz_smem<E, OPS>();
+  if (fl.npass > SF_FAST_MAXPASS) return (int)cudaErrorInvalidValue;
+  const size_t smyz = fast_yz_smem<E, OPS>(fl.npass);
   cudaError_t e;
   if (!attr) {
-    e = cudaFuncSetAttribute(k_fyz<E, NC, PAD, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smyz);
+    e = cudaFuncSetAttribute(k_fyz<E, NC, PAD, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fast_yz_smem<E, OPS>(SF_FAST_MAXPASS));
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_fyz<E, NC, PAD, OPS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return (int)e;
@@ -910,7 +966,6 @@ template <int E, int NC, bool PAD, int OPS> int fast_launch_yz(const FastLaunch 
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fyz<E, NC, PAD, OPS>, SF_FAST_THREADS, smyz)) != cudaSuccess)
     return (int)e;
   if (per < 1) return (int)cudaErrorLaunchOutOfResources;
-  if (fl.npass > SF_FAST_MAXPASS) return (int)cudaErrorInvalidValue;
   const int grid = fl.total < nsm * per ? fl.total : nsm * per;
   k_fyz<E, NC, PAD, OPS><<<grid, SF_FAST_THREADS, smyz, fl.stream>>>(fl.d_prob, fl.geo, fl.d_passes, fl.d_start, fl.npass,
                                                               fl.d_done, fl.ctl, fl.sticky, fl.timeout_ns, io);
