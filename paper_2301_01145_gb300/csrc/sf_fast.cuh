@@ -646,10 +646,17 @@ __device__ __forceinline__ void fast_zs_row(const Prob<float> &P, const FastGeo 
 }
 
 // ZS, split curl: 8 rows (consecutive ky) of one component c.  Emits
-// psi_c (I2 field c) and, for c = x, y, d/dz psi_c (I2 field 3 + c).
+// psi_c (I2 field c) and, for c = x, y, d/dz psi_c (I2 field 3 + c).  I2 of
+// the split path is stored transposed, [f][kxl][z][ky], so that the y inverse
+// reads whole ky rows: each warp leaves its z row in a shared staging block
+// [z][8 ky] (8-byte slots, ky index XOR-swizzled with (z >> 1) & 7 so that
+// neither the row writes nor the block reads conflict), and after one CTA
+// barrier the block leaves as 64-byte [z][ky0 .. ky0 + 7] segments.
+__device__ __forceinline__ int zs_stage_idx(int z, int kyl) { return z * SF_ZS_ROWS + (kyl ^ ((z >> 1) & 7)); }
+
 template <int E, bool PAD>
 __device__ __forceinline__ void fast_zs_split(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
-                                              cx<float> *wsm, float *gstage) {
+                                              cx<float> *wsm, cx<float> *T) {
   typedef cx<float> V;
   constexpr int L = 32 * E;
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
@@ -659,16 +666,25 @@ __device__ __forceinline__ void fast_zs_split(const Prob<float> &P, const FastGe
   const int rest = tile / nty;
   const int kxl = rest % ps.nkx;
   const int c = rest / ps.nkx;
-  if (c >= 3) return;
+  if (c >= 3) return;  // uniform over the CTA
   const int kx = ps.kx0 + kxl;
-  const int ky = iy * SF_ZS_ROWS + warp;
+  const int ky0 = iy * SF_ZS_ROWS;
+  const int ky = ky0 + warp;
   const size_t slot = (size_t)ps.slot * g.nfmax * g.S * L * nuz;
   const V *I1 = reinterpret_cast<const V *>(P.I1) + slot;
   V *I2 = reinterpret_cast<V *>(P.I2) + slot;
   const V *tz = P.ax[2].tw;
+  // T: Green's rows (8 x SF_ZS_GROW floats, unbounded axes), then the psi and
+  // d/dz staging blocks of nuz x 8 slots each (nuz = L / 2 padded, L periodic)
+  static_assert(SF_ZS_ROWS == 8, "staging block is [z][8 ky]");
+  static_assert(2 * SF_ZS_ROWS * 32 * E <= trows_elems<E>(), "staging blocks exceed the tile buffer");
+  static_assert(SF_ZS_ROWS * SF_ZS_GROW / 2 + 2 * SF_ZS_ROWS * 16 * E <= trows_elems<E>(),
+                "Green's rows and staging blocks exceed the tile buffer");
+  float *gs = reinterpret_cast<float *>(T) + warp * SF_ZS_GROW;
+  V *st_psi = T + (PAD ? SF_ZS_ROWS * SF_ZS_GROW / 2 : 0);
+  V *st_dz = st_psi + SF_ZS_ROWS * nuz;
   // Green's row of (kx, |ky|) staged in shared memory by asynchronous copies
   // that complete while the forward transform runs (unbounded axes only)
-  float *gs = gstage + warp * SF_ZS_GROW;
   if (PAD && P.green) {
     const int kyf = min(ky, L - ky);
     const float *grow = P.ghat_t + ((size_t)kx * P.gny + kyf) * P.gnz;
@@ -702,25 +718,94 @@ __device__ __forceinline__ void fast_zs_split(const Prob<float> &P, const FastGe
 #pragma unroll
     for (int j = 0; j < E; ++j) dz[0][j] = mul_i(cscale(sp[0][j], __ldg(&P.ax[2].kap[klayout<E>(t, j)])));
     wfft_inv_m<float, E, PAD, 1>(dz, wsm, tz);
-    V *dst = I2 + (((size_t)(3 + c) * g.S + kxl) * L + ky) * nuz;
 #pragma unroll
     for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
       const int z = t + 32 * r;
-      if (z < nuz) __stcg(&dst[z], dz[0][r]);
+      if (z < nuz) st_dz[zs_stage_idx(z, warp)] = dz[0][r];
     }
   }
   wfft_inv_m<float, E, PAD, 1>(sp, wsm, tz);
-  V *dst = I2 + (((size_t)c * g.S + kxl) * L + ky) * nuz;
 #pragma unroll
   for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
     const int z = t + 32 * r;
-    if (z < nuz) __stcg(&dst[z], sp[0][r]);
+    if (z < nuz) st_psi[zs_stage_idx(z, warp)] = sp[0][r];
+  }
+  __syncthreads();
+  const int nel = nuz * SF_ZS_ROWS;
+  V *dpsi = I2 + (((size_t)c * g.S + kxl) * nuz) * L + ky0;
+  V *ddz = I2 + (((size_t)(3 + c) * g.S + kxl) * nuz) * L + ky0;
+  for (int e = threadIdx.x; e < nel; e += SF_FAST_THREADS) {
+    const int z = e >> 3, kyl = e & 7;
+    const int si = zs_stage_idx(z, kyl);
+    __stcg(&dpsi[(size_t)z * L + kyl], st_psi[si]);
+    if (c < 2) __stcg(&ddz[(size_t)z * L + kyl], st_dz[si]);
+  }
+}
+
+// YI of the split path: whole ky rows of the transposed I2 [f][kxl][z][ky],
+// loaded directly in the k layout of the inverse transform (for every
+// register j the 32 lanes cover two runs of 16 consecutive ky), the curl
+// outputs combined in y-spectral space on the way in; two z rows per warp.
+template <int E, bool PAD>
+__device__ __forceinline__ void fast_yi_rows(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
+                                             cx<float> *wsm) {
+  typedef cx<float> V;
+  constexpr int L = 32 * E;
+  const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
+  const int nuy = P.nuy, nuz = P.nuz, nsx = P.nsx;
+  const int tz = cdiv(nuz, SF_YI_COLS);
+  const int iz = tile % tz;
+  const int rest = tile / tz;
+  const int kxl = rest % ps.nkx;
+  const int f = rest / ps.nkx;
+  const int kx = ps.kx0 + kxl;
+  if (f >= P.nout) return;
+  const size_t slot = (size_t)ps.slot * g.nfmax * g.S * L * nuz;
+  const V *I2 = reinterpret_cast<const V *>(P.I2) + slot;
+  // u_x = i ky psi_z - dz psi_y, u_y = dz psi_x - i kx psi_z, u_z = i kx psi_y - i ky psi_x
+  // (fields 0..2 psi, 3 dz psi_x, 4 dz psi_y)
+  const int fa = f < 3 ? f : (f == 3 ? 2 : (f == 4 ? 3 : 1));
+  const int fb = f == 3 ? 4 : (f == 4 ? 2 : 0);
+  const float kxv = __ldg(&P.ax[0].kap[kx]);
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int z = iz * SF_YI_COLS + 2 * warp + h;
+    if (z >= nuz) break;  // uniform over the warp
+    const V *ra = I2 + (((size_t)fa * g.S + kxl) * nuz + z) * L;
+    const V *rb = I2 + (((size_t)fb * g.S + kxl) * nuz + z) * L;
+    V v[1][E];
+    if (f < 3) {
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[0][j] = __ldcg(&ra[klayout<E>(t, j)]);
+    } else {
+      V tb[E];
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int k = klayout<E>(t, j);
+        v[0][j] = __ldcg(&ra[k]);
+        tb[j] = __ldcg(&rb[k]);
+      }
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const float kyv = __ldg(&P.ax[1].kap[klayout<E>(t, j)]);
+        if (f == 3) v[0][j] = csub(mul_i(cscale(v[0][j], kyv)), tb[j]);
+        else if (f == 4) v[0][j] = csub(v[0][j], mul_i(cscale(tb[j], kxv)));
+        else v[0][j] = mul_i(csub(cscale(v[0][j], kxv), cscale(tb[j], kyv)));
+      }
+    }
+    wfft_inv_m<float, E, PAD, 1>(v, wsm, P.ax[1].tw);
+    V *dst = reinterpret_cast<V *>(P.B) + (((size_t)f * nsx + kx) * nuz + z) * nuy;
+#pragma unroll
+    for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
+      const int y = t + 32 * r;
+      if (y < nuy) __stcs(&dst[y], v[0][r]);
+    }
   }
 }
 
 // YI: 16 z-columns (fixed f and kx) of I2 [f][kxl][ky][z], transposed through
 // shared memory, inverse y transform per column -> B rows along y
-template <int E, bool PAD, bool SPLIT, int M2>
+template <int E, bool PAD>
 __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
                                         cx<float> *wsm, cx<float> *T) {
   typedef cx<float> V;
@@ -739,66 +824,31 @@ __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, 
   const V *I2 = reinterpret_cast<const V *>(P.I2) + slot;
   auto field = [&](int ff) { return I2 + (((size_t)ff * g.S + kxl) * L) * nuz + z0; };
   constexpr int PER = L * 16 / SF_FAST_THREADS;
-  constexpr int BATCH = SPLIT ? 16 : PER;  // loads in flight per thread before they are used
-  if (!SPLIT || f < 3) {
-    const V *src = field(f);
+  const V *src = field(f);
+  // all loads of the tile in flight before the first shared store
+  V tmp[PER];
 #pragma unroll
-    for (int b0 = 0; b0 < PER; b0 += BATCH) {
-      V tmp[BATCH];
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * SF_FAST_THREADS;
+    const int l = e & 15, ky = e >> 4;
+    tmp[i] = (z0 + l < nuz) ? __ldcg(&src[(size_t)ky * nuz + l]) : czero<V>();
+  }
 #pragma unroll
-      for (int i = 0; i < BATCH; ++i) {
-        const int e = threadIdx.x + (b0 + i) * SF_FAST_THREADS;
-        const int l = e & 15, ky = e >> 4;
-        tmp[i] = (z0 + l < nuz) ? __ldcg(&src[(size_t)ky * nuz + l]) : czero<V>();
-      }
-#pragma unroll
-      for (int i = 0; i < BATCH; ++i) {
-        const int e = threadIdx.x + (b0 + i) * SF_FAST_THREADS;
-        T[trow<E>(e >> 4) + (e & 15)] = tmp[i];
-      }
-    }
-  } else {
-    // curl output in y-spectral space: u_x = i ky psi_z - dz psi_y, u_y = dz psi_x - i kx psi_z,
-    // u_z = i kx psi_y - i ky psi_x  (fields 0..2 psi, 3 dz psi_x, 4 dz psi_y)
-    const int fa = f == 3 ? 2 : (f == 4 ? 3 : 1);
-    const int fb = f == 3 ? 4 : (f == 4 ? 2 : 0);
-    const float kxv = __ldg(&P.ax[0].kap[kx]);
-    const V *sa = field(fa), *sb = field(fb);
-#pragma unroll
-    for (int b0 = 0; b0 < PER; b0 += BATCH) {
-      V ta[BATCH], tb[BATCH];
-#pragma unroll
-      for (int i = 0; i < BATCH; ++i) {
-        const int e = threadIdx.x + (b0 + i) * SF_FAST_THREADS;
-        const int l = e & 15, ky = e >> 4;
-        const bool ok = z0 + l < nuz;
-        ta[i] = ok ? __ldcg(&sa[(size_t)ky * nuz + l]) : czero<V>();
-        tb[i] = ok ? __ldcg(&sb[(size_t)ky * nuz + l]) : czero<V>();
-      }
-#pragma unroll
-      for (int i = 0; i < BATCH; ++i) {
-        const int e = threadIdx.x + (b0 + i) * SF_FAST_THREADS;
-        const float kyv = __ldg(&P.ax[1].kap[e >> 4]);
-        V r;
-        if (f == 3) r = csub(mul_i(cscale(ta[i], kyv)), tb[i]);
-        else if (f == 4) r = csub(ta[i], mul_i(cscale(tb[i], kxv)));
-        else r = mul_i(csub(cscale(ta[i], kxv), cscale(tb[i], kyv)));
-        T[trow<E>(e >> 4) + (e & 15)] = r;
-      }
-    }
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * SF_FAST_THREADS;
+    T[trow<E>(e >> 4) + (e & 15)] = tmp[i];
   }
   __syncthreads();
+  {
+    V v[2][E];
 #pragma unroll
-  for (int h0 = 0; h0 < 2; h0 += M2) {
-    V v[M2][E];
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
-    for (int h = 0; h < M2; ++h)
+      for (int j = 0; j < E; ++j) v[h][j] = T[trow<E>(klayout<E>(t, j)) + 2 * warp + h];
+    wfft_inv_m<float, E, PAD, 2>(v, wsm, P.ax[1].tw);
 #pragma unroll
-      for (int j = 0; j < E; ++j) v[h][j] = T[trow<E>(klayout<E>(t, j)) + 2 * warp + h0 + h];
-    wfft_inv_m<float, E, PAD, M2>(v, wsm, P.ax[1].tw);
-#pragma unroll
-    for (int h = 0; h < M2; ++h) {
-      const int z = z0 + 2 * warp + h0 + h;
+    for (int h = 0; h < 2; ++h) {
+      const int z = z0 + 2 * warp + h;
       if (z < nuz) {
         V *dst = reinterpret_cast<V *>(P.B) + (((size_t)f * nsx + kx) * nuz + z) * nuy;
 #pragma unroll
@@ -901,9 +951,10 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS == 2 ? 2 : 1)
       const int kind = ps.kind;
       if (kind == FK_YF) fast_yf<E, PAD, MM == 1 ? 1 : 2>(sP, g, ps, tile, wsm, T);
       else if (kind == FK_ZS) {
-        if (OPS == 2) fast_zs_split<E, PAD>(sP, g, ps, tile, wsm, reinterpret_cast<float *>(T));
+        if (OPS == 2) fast_zs_split<E, PAD>(sP, g, ps, tile, wsm, T);
         else fast_zs<E, NC, PAD, OPS>(sP, g, ps, tile, wsm);
-      } else fast_yi<E, PAD, OPS == 2, MM == 1 ? 1 : 2>(sP, g, ps, tile, wsm, T);
+      } else if (OPS == 2) fast_yi_rows<E, PAD>(sP, g, ps, tile, wsm);
+      else fast_yi<E, PAD>(sP, g, ps, tile, wsm, T);
     }
     __syncthreads();
     if (threadIdx.x == 32) {
