@@ -74,7 +74,7 @@ int radix_plan(int L, int *rad, int maxr) {
 struct AxisHost {
   int kind, n, nodes, u0, nu, L, ns, k0, nst, radix[5];
   double Ldom, h;
-  std::vector<double> tw, phase, lam, kap, kap2;  // complex tables interleaved re,im
+  std::vector<double> tw, twf, phase, lam, kap, kap2;  // complex tables interleaved re,im
 };
 
 // per-axis transform geometry and tables (Table 1; Sec. 2.4.3 wavenumbers)
@@ -101,6 +101,24 @@ AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, b
     const double ang = -2.0 * kPi * (double)j / (double)L;
     a.tw[2 * j] = std::cos(ang);
     a.tw[2 * j + 1] = std::sin(ang);
+  }
+  // warp-FFT twiddles (L = 32 E): [k1][t] = W_L^{t k1} (k1 < E, t < 32), then
+  // [j][q] = W_L^{q j E} (j < E, q < G = 32 / E), then [mm - 1 + r] = W_{2 mm}^r
+  // for the lane stages mm = 2, 4, .. < G (r < mm)
+  if (L == 256 || L == 512) {
+    const int E = L / 32, G = 32 / E;
+    std::vector<double> ang;
+    for (int k1 = 0; k1 < E; ++k1)
+      for (int t = 0; t < 32; ++t) ang.push_back(-2.0 * kPi * (double)(t * k1) / L);
+    for (int j = 0; j < E; ++j)
+      for (int q = 0; q < G; ++q) ang.push_back(-2.0 * kPi * (double)(q * j * E) / L);
+    for (int mm = 1; mm < G; mm <<= 1)
+      for (int r = 0; r < mm; ++r) ang.push_back(-2.0 * kPi * (double)r / (2.0 * mm));
+    a.twf.resize(2 * ang.size());
+    for (size_t i = 0; i < ang.size(); ++i) {
+      a.twf[2 * i] = std::cos(ang[i]);
+      a.twf[2 * i + 1] = std::sin(ang[i]);
+    }
   }
   a.phase.assign(2 * (size_t)(n + 1), 0.0);
   for (int k = 0; k <= n; ++k) {
@@ -184,13 +202,15 @@ template <typename T> sf_status fill_axis(Axis<T> &d, const AxisHost &h, DevMem<
   d.k0 = h.k0;
   d.nst = h.nst;
   for (int i = 0; i < 5; ++i) d.radix[i] = h.radix[i];
-  T *tw, *ph, *lam, *kap, *kap2;
+  T *tw, *twf, *ph, *lam, *kap, *kap2;
   SF_TRY(mem.template upload<T>(&tw, h.tw, true));
+  SF_TRY(mem.template upload<T>(&twf, h.twf, true));
   SF_TRY(mem.template upload<T>(&ph, h.phase, true));
   SF_TRY(mem.template upload<T>(&lam, h.lam, false));
   SF_TRY(mem.template upload<T>(&kap, h.kap, false));
   SF_TRY(mem.template upload<T>(&kap2, h.kap2, false));
   d.tw = reinterpret_cast<const cx<T> *>(tw);
+  d.twf = reinterpret_cast<const cx<T> *>(twf);
   d.phase = reinterpret_cast<const cx<T> *>(ph);
   d.lam = lam;
   d.kap = kap;

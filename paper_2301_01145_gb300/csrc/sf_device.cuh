@@ -187,6 +187,7 @@ template <typename T> struct Axis {
   int nst;    // number of radix stages
   int radix[5];
   const cx<T> *tw;     // exp(-2 pi i j / L), j < L
+  const cx<T> *twf;    // warp-FFT twiddles, lane-contiguous (L = 256, 512; see sf_fast.cuh), else null
   const cx<T> *phase;  // real kinds: phase_k, k in [0, n]
   const T *lam;        // eigenvalue per coefficient index (bounded)
   const T *kap;        // derivative wavenumber per coefficient index, Nyquist zeroed

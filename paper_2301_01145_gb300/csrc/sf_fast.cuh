@@ -141,6 +141,10 @@ template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfo
 // ---- warp FFTs -------------------------------------------------------------
 // M independent lines per warp, interleaved step by step so that their
 // dependency chains overlap (wsm: M consecutive buffers of E*33 elements).
+// Twiddles come from the lane-contiguous table twf of the axis:
+//   twf[k1 * 32 + t]          = W_L^{t k1}       (step 1, one 256-byte row per k1)
+//   twf[L + j * G + q]        = W_L^{q j E}      (step 3, E-point stage)
+//   twf[L + 32 + mm - 1 + r]  = W_{2 mm}^r       (step 3, lane stage mm)
 template <typename T, int E, bool HALFIN, int M>
 __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const cx<T> *__restrict__ tw) {
   typedef cx<T> V;
@@ -153,7 +157,7 @@ __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
   }
 #pragma unroll
   for (int k1 = 1; k1 < E; ++k1) {
-    const V w = __ldg(&tw[t * k1]);
+    const V w = __ldg(&tw[k1 * 32 + t]);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[m][k1] = cmul(v[m][k1], w);
   }
@@ -172,14 +176,14 @@ __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
   for (int m = 0; m < M; ++m) dftR<E, false>(v[m]);
 #pragma unroll
   for (int j = 1; j < E; ++j) {
-    const V w = __ldg(&tw[q * j * E]);
+    const V w = __ldg(&tw[L + j * G + q]);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[m][j] = cmul(v[m][j], w);
   }
 #pragma unroll
   for (int mm = G / 2; mm >= 1; mm >>= 1) {
     const float sg = (q & mm) ? -1.f : 1.f;  // hi lane: partner - mine, lo lane: mine + partner
-    const V w = __ldg(&tw[(q & (mm - 1)) * (L / (2 * mm))]);
+    const V w = __ldg(&tw[L + 32 + mm - 1 + (q & (mm - 1))]);
 #pragma unroll
     for (int m = 0; m < M; ++m)
 #pragma unroll
@@ -202,7 +206,7 @@ __device__ __forceinline__ void wfft_inv_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
   for (int mm = 1; mm < G; mm <<= 1) {
     const bool hi = (q & mm) != 0;
     const float sg = hi ? -1.f : 1.f;
-    const V w = __ldg(&tw[(q & (mm - 1)) * (L / (2 * mm))]);
+    const V w = __ldg(&tw[L + 32 + mm - 1 + (q & (mm - 1))]);
 #pragma unroll
     for (int m = 0; m < M; ++m)
 #pragma unroll
@@ -217,7 +221,7 @@ __device__ __forceinline__ void wfft_inv_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
   }
 #pragma unroll
   for (int j = 1; j < E; ++j) {
-    const V w = __ldg(&tw[q * j * E]);
+    const V w = __ldg(&tw[L + j * G + q]);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[m][j] = cmulc(v[m][j], w);
   }
@@ -235,7 +239,7 @@ __device__ __forceinline__ void wfft_inv_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
   __syncwarp();
 #pragma unroll
   for (int kk = 1; kk < E; ++kk) {
-    const V w = __ldg(&tw[t * kk]);
+    const V w = __ldg(&tw[kk * 32 + t]);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[m][kk] = cmulc(v[m][kk], w);
   }
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs
       v[r] = mk<V>(a, b);
     }
   }
-  wfft_fwd_m<float, E, PAD, 1>(vv, wsm, X.tw);
+  wfft_fwd_m<float, E, PAD, 1>(vv, wsm, X.twf);
   // natural order in the warp buffer (one pad slot per 32) for the Hermitian split
 #pragma unroll
   for (int j = 0; j < E; ++j) {
@@ -422,7 +426,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *prob
       v[j] = mk<V>(A.x + B.y, B.x - A.y);
     }
   }
-  wfft_inv_m<float, E, PAD, 1>(vv, wsm, X.tw);
+  wfft_inv_m<float, E, PAD, 1>(vv, wsm, X.twf);
   const int la = y0 + 2 * warp, lb = la + 1;
   float *dst = P.out_ptr[f];
   const size_t rowa = ((size_t)qz * Y.nodes + la) * X.nodes;
@@ -471,7 +475,7 @@ __device__ __forceinline__ void fast_yf(const Prob<float> &P, const FastGeo &g, 
         v[h][r] = ((!PAD || r < E / 2) && z < nuz && pos < nuy) ? __ldcs(&src[pos]) : czero<V>();
       }
     }
-    wfft_fwd_m<float, E, PAD, M2>(v, wsm, P.ax[1].tw);
+    wfft_fwd_m<float, E, PAD, M2>(v, wsm, P.ax[1].twf);
 #pragma unroll
     for (int h = 0; h < M2; ++h)
 #pragma unroll
@@ -553,7 +557,7 @@ __device__ __forceinline__ void fast_zs_row(const Prob<float> &P, const FastGeo 
   const size_t slot = (size_t)ps.slot * g.nfmax * g.S * L * nuz;
   const V *I1 = reinterpret_cast<const V *>(P.I1) + slot;
   V *I2 = reinterpret_cast<V *>(P.I2) + slot;
-  const V *tz = P.ax[2].tw;
+  const V *tz = P.ax[2].twf;
   V sp[NC][E];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -673,7 +677,7 @@ __device__ __forceinline__ void fast_zs_split(const Prob<float> &P, const FastGe
   const size_t slot = (size_t)ps.slot * g.nfmax * g.S * L * nuz;
   const V *I1 = reinterpret_cast<const V *>(P.I1) + slot;
   V *I2 = reinterpret_cast<V *>(P.I2) + slot;
-  const V *tz = P.ax[2].tw;
+  const V *tz = P.ax[2].twf;
   // T: Green's rows (8 x SF_ZS_GROW floats, unbounded axes), then the psi and
   // d/dz staging blocks of nuz x 8 slots each (nuz = L / 2 padded, L periodic)
   static_assert(SF_ZS_ROWS == 8, "staging block is [z][8 ky]");
@@ -793,7 +797,7 @@ __device__ __forceinline__ void fast_yi_rows(const Prob<float> &P, const FastGeo
         else v[0][j] = mul_i(csub(cscale(v[0][j], kxv), cscale(tb[j], kyv)));
       }
     }
-    wfft_inv_m<float, E, PAD, 1>(v, wsm, P.ax[1].tw);
+    wfft_inv_m<float, E, PAD, 1>(v, wsm, P.ax[1].twf);
     V *dst = reinterpret_cast<V *>(P.B) + (((size_t)f * nsx + kx) * nuz + z) * nuy;
 #pragma unroll
     for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
@@ -845,7 +849,7 @@ __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, 
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int j = 0; j < E; ++j) v[h][j] = T[trow<E>(klayout<E>(t, j)) + 2 * warp + h];
-    wfft_inv_m<float, E, PAD, 2>(v, wsm, P.ax[1].tw);
+    wfft_inv_m<float, E, PAD, 2>(v, wsm, P.ax[1].twf);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int z = z0 + 2 * warp + h;
