@@ -461,6 +461,30 @@ __device__ __forceinline__ void fast_yf(const Prob<float> &P, const FastGeo &g, 
   const int z0 = iz * SF_YF_ROWS;
   if (c >= P.nin) return;  // tile outside the pass (uniform over the block)
   const V *A = reinterpret_cast<const V *>(P.A);
+  if (M2 == 1 && PAD) {
+    // one row after the other; the (half, nonzero) input of the second row is
+    // loaded with the first so that both loads share one memory latency
+    const int za = z0 + 2 * warp, zb = za + 1;
+    const V *sa = A + (((size_t)c * nsx + kx) * nuz + za) * nuy;
+    const V *sb = A + (((size_t)c * nsx + kx) * nuz + zb) * nuy;
+    V v[1][E], nb[E / 2];
+#pragma unroll
+    for (int r = 0; r < E / 2; ++r) {
+      const int pos = t + 32 * r;
+      v[0][r] = (za < nuz && pos < nuy) ? __ldcs(&sa[pos]) : czero<V>();
+      nb[r] = (zb < nuz && pos < nuy) ? __ldcs(&sb[pos]) : czero<V>();
+    }
+#pragma unroll
+    for (int r = E / 2; r < E; ++r) v[0][r] = czero<V>();
+    wfft_fwd_m<float, E, true, 1>(v, wsm, P.ax[1].twf);
+#pragma unroll
+    for (int j = 0; j < E; ++j) T[trow<E>(klayout<E>(t, j)) + 2 * warp] = v[0][j];
+#pragma unroll
+    for (int r = 0; r < E; ++r) v[0][r] = r < E / 2 ? nb[r] : czero<V>();
+    wfft_fwd_m<float, E, true, 1>(v, wsm, P.ax[1].twf);
+#pragma unroll
+    for (int j = 0; j < E; ++j) T[trow<E>(klayout<E>(t, j)) + 2 * warp + 1] = v[0][j];
+  } else
   // two rows per warp, transformed together (M2 = 2) or one after the other (M2 = 1)
 #pragma unroll
   for (int h0 = 0; h0 < 2; h0 += M2) {
