@@ -22,12 +22,17 @@
 //   k_fx   source rows along x  -> A  [c][kx][z][y]     (transposed store, 16 y per chunk)
 //   YF     rows of A along y    -> I1 [c][kx][ky][z]    (transposed store, 16 z per chunk)
 //   ZS     rows of I1 along z: forward, multiply, operator, inverse
-//                               -> I2 [f][kx][ky][z]    (direct row store)
-//   YI     columns of I2 along ky (transposed load) -> B [f][kx][z][y] (direct row store)
+//                               -> I2 [f][kx][ky][z]    (direct row store), or, for the
+//                                  split curl, I2 [f][kx][z][ky] (64-byte chunks)
+//   YI     columns of I2 along ky (transposed load), or whole ky rows of the
+//          split layout         -> B  [f][kx][z][y]     (direct row store)
 //   k_fxi  B transposed back    -> result rows along x
 // YF/ZS/YI run in one persistent kernel over slabs of S kx-planes; I1 and I2
-// are rings of two slabs so that they stay resident in L2 while the slab
-// pipeline (YF of slab s, ZS of s-1, YI of s-2) advances.
+// are rings of D + 2 slabs (D = stage lag) so that they stay resident in L2
+// while the slab pipeline (YF of slab s, ZS of s-D, YI of s-2D) advances.
+// The 3-component curl is split by component in the z stage: it emits psi_c
+// and, for c = x, y, d/dz psi_c (5 z inverses per (kx, ky) instead of 6), and
+// the y inverse forms u = curl psi from them in y-spectral space.
 #pragma once
 
 #include "sf_kernels.cuh"
