@@ -57,6 +57,35 @@ template <typename V> __device__ __forceinline__ V shfl_xor_c(V v, int m) {
   return r;
 }
 
+// W_32^m = exp(-2 pi i m / 32) for a compile-time m (folded to immediates
+// after unrolling): cos(2 pi r / 32), r = 0..8, and quadrant symmetry
+__host__ __device__ constexpr float cos32(int r) {
+  return r == 0 ? 1.0f
+       : r == 1 ? 0.980785280403230449126f
+       : r == 2 ? 0.923879532511286756128f
+       : r == 3 ? 0.831469612302545237078f
+       : r == 4 ? 0.707106781186547524401f
+       : r == 5 ? 0.555570233019602224742f
+       : r == 6 ? 0.382683432365089771728f
+       : r == 7 ? 0.195090322016128267848f
+                : 0.0f;
+}
+template <typename V> __device__ __forceinline__ V w32c(int m) {
+  m &= 31;
+  float c, sn;  // cos and sin of 2 pi m / 32
+  if (m <= 8) { c = cos32(m); sn = cos32(8 - m); }
+  else if (m <= 16) { c = -cos32(16 - m); sn = cos32(m - 8); }
+  else if (m <= 24) { c = -cos32(m - 16); sn = -cos32(24 - m); }
+  else { c = cos32(32 - m); sn = -cos32(m - 24); }
+  return mk<V>(c, -sn);
+}
+// twiddle W_L^{q j E} = W_32^{q j} of the E-point stage (L = 32 E, lane group index q < G)
+template <int G, typename V> __device__ __forceinline__ V w_stage2(int q, int j) {
+  if (G == 1) return w32c<V>(0);
+  if (G == 2) return q ? w32c<V>(j) : w32c<V>(0);
+  return q == 0 ? w32c<V>(0) : (q == 1 ? w32c<V>(j) : (q == 2 ? w32c<V>(2 * j) : w32c<V>(3 * j)));
+}
+
 // k index held in register j by this lane after a forward warp FFT
 template <int E> __device__ __forceinline__ int klayout(int lane, int j) {
   constexpr int G = 32 / E;
@@ -148,7 +177,8 @@ template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfo
 // dependency chains overlap (wsm: M consecutive buffers of E*33 elements).
 // Twiddles come from the lane-contiguous table twf of the axis:
 //   twf[k1 * 32 + t]          = W_L^{t k1}       (step 1, one 256-byte row per k1)
-//   twf[L + j * G + q]        = W_L^{q j E}      (step 3, E-point stage)
+//   twf[L + j * G + q]        = W_L^{q j E}      (step 3, E-point stage; the kernels use the
+//                                                 equal constants W_32^{q j} of w_stage2)
 //   twf[L + 32 + mm - 1 + r]  = W_{2 mm}^r       (step 3, lane stage mm)
 template <typename T, int E, bool HALFIN, int M>
 __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const cx<T> *__restrict__ tw) {
@@ -160,11 +190,22 @@ __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
     if (HALFIN) dft_halfin<E, false>(v[m]);
     else dftR<E, false>(v[m]);
   }
+  {
+    // W_L^{t k1}: rows k1 < 4 and k1 = 0 mod 4 are loaded, the others are one
+    // product W_L^{t (k1 & ~3)} W_L^{t (k1 & 3)} (one rounding more)
+    const V w1 = __ldg(&tw[1 * 32 + t]), w2 = __ldg(&tw[2 * 32 + t]), w3 = __ldg(&tw[3 * 32 + t]);
 #pragma unroll
-  for (int k1 = 1; k1 < E; ++k1) {
-    const V w = __ldg(&tw[k1 * 32 + t]);
+    for (int k1 = 1; k1 < E; ++k1) {
+      V w;
+      if ((k1 & 3) == 0 || k1 < 4) w = __ldg(&tw[k1 * 32 + t]);
+      else {
+        const V a = __ldg(&tw[(k1 & ~3) * 32 + t]);
+        const int b = k1 & 3;
+        w = cmul(a, b == 1 ? w1 : (b == 2 ? w2 : w3));
+      }
 #pragma unroll
-    for (int m = 0; m < M; ++m) v[m][k1] = cmul(v[m][k1], w);
+      for (int m = 0; m < M; ++m) v[m][k1] = cmul(v[m][k1], w);
+    }
   }
 #pragma unroll
   for (int m = 0; m < M; ++m)
@@ -181,7 +222,7 @@ __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
   for (int m = 0; m < M; ++m) dftR<E, false>(v[m]);
 #pragma unroll
   for (int j = 1; j < E; ++j) {
-    const V w = __ldg(&tw[L + j * G + q]);
+    const V w = w_stage2<G, V>(q, j);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[m][j] = cmul(v[m][j], w);
   }
@@ -226,7 +267,7 @@ __device__ __forceinline__ void wfft_inv_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
   }
 #pragma unroll
   for (int j = 1; j < E; ++j) {
-    const V w = __ldg(&tw[L + j * G + q]);
+    const V w = w_stage2<G, V>(q, j);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[m][j] = cmulc(v[m][j], w);
   }
@@ -242,11 +283,21 @@ __device__ __forceinline__ void wfft_inv_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
 #pragma unroll
     for (int kk = 0; kk < E; ++kk) v[m][kk] = wsm[m * E * P + kk * P + t];
   __syncwarp();
+  {
+    // conjugate of W_L^{t kk}, built as in the forward transform
+    const V w1 = __ldg(&tw[1 * 32 + t]), w2 = __ldg(&tw[2 * 32 + t]), w3 = __ldg(&tw[3 * 32 + t]);
 #pragma unroll
-  for (int kk = 1; kk < E; ++kk) {
-    const V w = __ldg(&tw[kk * 32 + t]);
+    for (int kk = 1; kk < E; ++kk) {
+      V w;
+      if ((kk & 3) == 0 || kk < 4) w = __ldg(&tw[kk * 32 + t]);
+      else {
+        const V a = __ldg(&tw[(kk & ~3) * 32 + t]);
+        const int b = kk & 3;
+        w = cmul(a, b == 1 ? w1 : (b == 2 ? w2 : w3));
+      }
 #pragma unroll
-    for (int m = 0; m < M; ++m) v[m][kk] = cmulc(v[m][kk], w);
+      for (int m = 0; m < M; ++m) v[m][kk] = cmulc(v[m][kk], w);
+    }
   }
 #pragma unroll
   for (int m = 0; m < M; ++m) {
