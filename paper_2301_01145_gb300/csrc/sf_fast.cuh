@@ -360,10 +360,10 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs
   __shared__ __align__(16) Prob<float> sP;
   load_prob<float>(sP, probs, io);
   const Prob<float> &P = sP;
-  V *wsm_all = reinterpret_cast<V *>(fsm);
-  V *T = wsm_all + fast_wsm_elems<E, 1>();
+  // one region: the warp buffers during the transform, then the output tile
+  V *T = reinterpret_cast<V *>(fsm);
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
-  V *wsm = wsm_all + warp * E * wrow<E>();
+  V *wsm = T + warp * E * wrow<E>();
   const Axis<float> &X = P.ax[0], &Y = P.ax[1];
   const int nuy = P.nuy, nuz = P.nuz, nux = X.nu, nsx = P.nsx;
   const int ty = cdiv(nuy, 16);
@@ -401,12 +401,29 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs
   }
   __syncwarp();
   const int half = L / 2;
-  for (int k = t; k <= half; k += 32) {
-    const int km = (L - k) & (L - 1);
-    const V zk = wsm[k + (k >> 5)];
-    const V zm = wsm[km + (km >> 5)];
-    T[k * 17 + 2 * warp] = mk<V>((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
-    T[k * 17 + 2 * warp + 1] = mk<V>((zk.y + zm.y) * 0.5f, -(zk.x - zm.x) * 0.5f);
+  // Hermitian split into registers (k = t + 32 i <= L/2), then the tile
+  // overwrites the warp buffers of all warps
+  constexpr int NK = (16 * E) / 32 + 1;
+  V sa[NK], sb[NK];
+#pragma unroll
+  for (int i = 0; i < NK; ++i) {
+    const int k = t + 32 * i;
+    if (k <= half) {
+      const int km = (L - k) & (L - 1);
+      const V zk = wsm[k + (k >> 5)];
+      const V zm = wsm[km + (km >> 5)];
+      sa[i] = mk<V>((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
+      sb[i] = mk<V>((zk.y + zm.y) * 0.5f, -(zk.x - zm.x) * 0.5f);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NK; ++i) {
+    const int k = t + 32 * i;
+    if (k <= half) {
+      T[k * 17 + 2 * warp] = sa[i];
+      T[k * 17 + 2 * warp + 1] = sb[i];
+    }
   }
   __syncthreads();
   V *out = reinterpret_cast<V *>(P.A);
@@ -421,6 +438,12 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs
 // ---------------------------------------------------------------------------
 // XINV: B[f][kx][z][y0..y0+16) -> 16 result lines along x
 // ---------------------------------------------------------------------------
+// shared memory of k_fx / k_fxi: one region that serves as the 16-line
+// transpose tile and, at another time, as the warp buffers
+template <int E> __host__ __device__ constexpr int fast_xi_elems() {
+  return (16 * E + 1) * 17 > fast_wsm_elems<E, 1>() ? (16 * E + 1) * 17 : fast_wsm_elems<E, 1>();
+}
+
 template <int E, bool PAD>
 __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *probs, IOArgs<float> io) {
   typedef cx<float> V;
@@ -429,10 +452,9 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *prob
   __shared__ __align__(16) Prob<float> sP;
   load_prob<float>(sP, probs, io);
   const Prob<float> &P = sP;
-  V *wsm_all = reinterpret_cast<V *>(fsm);
-  V *T = wsm_all + fast_wsm_elems<E, 1>();
+  V *T = reinterpret_cast<V *>(fsm);
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
-  V *wsm = wsm_all + warp * E * wrow<E>();
+  V *wsm = T + warp * E * wrow<E>();
   const Axis<float> &X = P.ax[0], &Y = P.ax[1];
   const int nuy = P.nuy, nuz = P.nuz, nux = X.nu, nsx = P.nsx;
   const int ty = cdiv(nuy, 16);
@@ -482,6 +504,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *prob
       v[j] = mk<V>(A.x + B.y, B.x - A.y);
     }
   }
+  __syncthreads();  // the tile is free: it becomes the warp buffers
   wfft_inv_m<float, E, PAD, 1>(vv, wsm, X.twf);
   const int la = y0 + 2 * warp, lb = la + 1;
   float *dst = P.out_ptr[f];
@@ -1074,7 +1097,7 @@ struct FastLaunch {
 int sf_fast_launch_e8(const FastLaunch &fl, const IOArgs<float> &io, int *launches);
 int sf_fast_launch_e16(const FastLaunch &fl, const IOArgs<float> &io, int *launches);
 
-template <int E> size_t fast_x_smem() { return (size_t)(fast_wsm_elems<E, 1>() + (16 * E + 1) * 17) * sizeof(float2); }
+template <int E> size_t fast_x_smem() { return (size_t)fast_xi_elems<E>() * sizeof(float2); }
 #define SF_FAST_MAXPASS 1024
 // dynamic shared memory of k_fyz: warp buffers, tile buffer, packed pass table
 template <int E, int OPS> size_t fast_yz_smem(int npass) {
@@ -1109,13 +1132,13 @@ template <int E, int NC, bool PAD, int OPS> int fast_launch_yz(const FastLaunch 
 
 template <int E, bool PAD> int fast_launch_all(const FastLaunch &fl, const IOArgs<float> &io, int *launches) {
   const Prob<float> &Q = *fl.h_prob;
-  const size_t smx = fast_x_smem<E>();
+  const size_t smx = fast_x_smem<E>(), smxi = smx;
   static bool attr = false;
   cudaError_t e;
   if (!attr) {
     if ((e = cudaFuncSetAttribute(k_fx<E, PAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess)
       return (int)e;
-    if ((e = cudaFuncSetAttribute(k_fxi<E, PAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_fxi<E, PAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smxi)) != cudaSuccess)
       return (int)e;
     if ((e = cudaFuncSetAttribute(k_fx<E, PAD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
       return (int)e;
@@ -1142,7 +1165,7 @@ template <int E, bool PAD> int fast_launch_all(const FastLaunch &fl, const IOArg
     if (launches) *launches += 2;
   }
   if (fl.back) {
-    k_fxi<E, PAD><<<Q.nout * Q.nuz * cdiv(Q.nuy, 16), SF_FAST_THREADS, smx, fl.stream>>>(fl.d_prob, io);
+    k_fxi<E, PAD><<<Q.nout * Q.nuz * cdiv(Q.nuy, 16), SF_FAST_THREADS, smxi, fl.stream>>>(fl.d_prob, io);
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     if (mk && (e = cudaEventRecord(mk[3], fl.stream)) != cudaSuccess) return (int)e;
     if (launches) *launches += 1;
