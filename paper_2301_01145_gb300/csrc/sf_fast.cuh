@@ -86,6 +86,14 @@ template <int G, typename V> __device__ __forceinline__ V w_stage2(int q, int j)
   return q == 0 ? w32c<V>(0) : (q == 1 ? w32c<V>(j) : (q == 2 ? w32c<V>(2 * j) : w32c<V>(3 * j)));
 }
 
+// derivative wavenumber of FFT index k on a periodic or doubled axis of
+// length L: ks * kappa_1 with ks = k (k < L/2), k - L (k > L/2), 0 (Nyquist),
+// where kappa_1 = kap[1] of the axis; equals the kap table to one rounding
+template <int L> __device__ __forceinline__ float kap_of(int k, float kap1) {
+  const int ks = k < L / 2 ? k : (k > L / 2 ? k - L : 0);
+  return (float)ks * kap1;
+}
+
 // k index held in register j by this lane after a forward warp FFT
 template <int E> __device__ __forceinline__ int klayout(int lane, int j) {
   constexpr int G = 32 / E;
@@ -353,7 +361,7 @@ template <typename T> __host__ __device__ inline int fast_tiles_yi(const Prob<T>
 // XFWD: 16 source lines (8 packed pairs, one per warp) -> A[c][kx][z][y]
 // ---------------------------------------------------------------------------
 template <int E, bool PAD>
-__global__ void __launch_bounds__(SF_FAST_THREADS) k_fx(const Prob<float> *probs, IOArgs<float> io) {
+__global__ void __launch_bounds__(SF_FAST_THREADS, 5) k_fx(const Prob<float> *probs, IOArgs<float> io) {
   typedef cx<float> V;
   constexpr int L = 32 * E;
   extern __shared__ __align__(16) unsigned char fsm[];
@@ -445,7 +453,7 @@ template <int E> __host__ __device__ constexpr int fast_xi_elems() {
 }
 
 template <int E, bool PAD>
-__global__ void __launch_bounds__(SF_FAST_THREADS) k_fxi(const Prob<float> *probs, IOArgs<float> io) {
+__global__ void __launch_bounds__(SF_FAST_THREADS, 5) k_fxi(const Prob<float> *probs, IOArgs<float> io) {
   typedef cx<float> V;
   constexpr int L = 32 * E;
   extern __shared__ __align__(16) unsigned char fsm[];
@@ -821,9 +829,10 @@ __device__ __forceinline__ void fast_zs_split(const Prob<float> &P, const FastGe
     for (int j = 0; j < E; ++j) sp[0][j] = cscale(sp[0][j], fast_mult(P, kx, ky, klayout<E>(t, j)));
   }
   if (c < 2) {
+    const float kz1 = __ldg(&P.ax[2].kap[1]);
     V dz[1][E];
 #pragma unroll
-    for (int j = 0; j < E; ++j) dz[0][j] = mul_i(cscale(sp[0][j], __ldg(&P.ax[2].kap[klayout<E>(t, j)])));
+    for (int j = 0; j < E; ++j) dz[0][j] = mul_i(cscale(sp[0][j], kap_of<L>(klayout<E>(t, j), kz1)));
     wfft_inv_m<float, E, PAD, 1>(dz, wsm, tz);
 #pragma unroll
     for (int r = 0; r < (PAD ? E / 2 : E); ++r) {
@@ -874,6 +883,7 @@ __device__ __forceinline__ void fast_yi_rows(const Prob<float> &P, const FastGeo
   const int fa = f < 3 ? f : (f == 3 ? 2 : (f == 4 ? 3 : 1));
   const int fb = f == 3 ? 4 : (f == 4 ? 2 : 0);
   const float kxv = __ldg(&P.ax[0].kap[kx]);
+  const float ky1 = __ldg(&P.ax[1].kap[1]);
 #pragma unroll 1
   for (int h = 0; h < 2; ++h) {
     const int z = iz * SF_YI_COLS + 2 * warp + h;
@@ -894,7 +904,7 @@ __device__ __forceinline__ void fast_yi_rows(const Prob<float> &P, const FastGeo
       }
 #pragma unroll
       for (int j = 0; j < E; ++j) {
-        const float kyv = __ldg(&P.ax[1].kap[klayout<E>(t, j)]);
+        const float kyv = kap_of<L>(klayout<E>(t, j), ky1);
         if (f == 3) v[0][j] = csub(mul_i(cscale(v[0][j], kyv)), tb[j]);
         else if (f == 4) v[0][j] = csub(v[0][j], mul_i(cscale(tb[j], kxv)));
         else v[0][j] = mul_i(csub(cscale(v[0][j], kxv), cscale(tb[j], kyv)));
