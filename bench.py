@@ -59,27 +59,27 @@ N_SM = 152
 
 
 def transform_flops(n: int):
-    """Transform flops of the three kernels of one solve, standard FFT count.
+    """Algorithmic transform flops of the three kernels of one solve.
 
-    Counted as 5 L log2 L per complex line of length L and 2.5 L log2 L per
-    real line (the usual FFT benchmark convention), over the line transforms
-    each kernel performs for the n^3 vector curl solve padded to L = 2n:
-      x forward (k_fx):   3 fields x n^2 real lines,
-      y/z executor (k_fyz, split curl): y forward 3 x (n+1) x n, z forward
-                          3 x (n+1) x L, z inverse 5 x (n+1) x L (psi and
-                          d/dz of two components), y inverse 6 x (n+1) x n,
-      x inverse (k_fxi):  6 fields x n^2 real lines.
-    Pruned transforms (half the input or output zero) are counted at full
-    length; spectral multiplies are not counted.
+    Split-radix count S(L) = 4 L log2 L - 6 L + 8 per complex line of length L;
+    every line of the doubled axes is pruned (half of its input zero, or half
+    of its output discarded), counted as one radix-2 stage of L/2 twiddle
+    products plus two half-length transforms, P(L) = 2 S(L/2) + 3 L; a real
+    line counts half.  One field-direction (one 3D transform of one field)
+    is n^2 real x lines + (n+1) n y lines + (n+1) L z lines, 3.42 GFLOP at
+    n = 256, and a solve is 9 field-directions (3 forward, 6 inverse: psi and
+    u = curl psi), whatever the kernels do to save work.  x forward: 3 x parts;
+    y/z executor: 9 y and z parts; x inverse: 6 x parts.
     """
     L = 2 * n
-    lg = math.log2(L)
-    cplx = 5 * L * lg
-    real = 2.5 * L * lg
-    nk = n + 1
-    return {"x_forward": 3 * n * n * real,
-            "yz_executor": (3 * n + 3 * L + 5 * L + 6 * n) * nk * cplx,
-            "x_inverse": 6 * n * n * real}
+
+    def S(m):
+        return 4 * m * math.log2(m) - 6 * m + 8
+
+    P = 2 * S(L // 2) + 3 * L
+    x_part = n * n * P / 2
+    yz_part = ((n + 1) * n + (n + 1) * L) * P
+    return {"x_forward": 3 * x_part, "yz_executor": 9 * yz_part, "x_inverse": 6 * x_part}
 
 
 def kernel_bytes(n: int, elem: int = 4):
