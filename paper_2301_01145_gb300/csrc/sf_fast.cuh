@@ -595,10 +595,24 @@ __device__ __forceinline__ void fast_yf(const Prob<float> &P, const FastGeo &g, 
   __syncthreads();
   V *I1 = reinterpret_cast<V *>(P.I1) + (size_t)ps.slot * g.nfmax * g.S * L * nuz;
   const size_t base = (((size_t)c * g.S + kxl) * L) * nuz + z0;
-  const int cnt = L * 16;
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const int l = e & 15, ky = e >> 4;
-    if (z0 + l < nuz) __stcg(&I1[base + (size_t)ky * nuz + l], T[trow<E>(ky) + l]);
+  if ((nuz & 1) == 0) {
+    // pairs of z: 16-byte stores (z0 and nuz even keep every pair aligned and inside the row)
+    float4 *I1q = reinterpret_cast<float4 *>(I1 + base);
+    const int cnt = L * 8;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int l2 = e & 7, ky = e >> 3;
+      if (z0 + 2 * l2 < nuz) {
+        const V a = T[trow<E>(ky) + 2 * l2], b = T[trow<E>(ky) + 2 * l2 + 1];
+        __stcg(&I1q[((size_t)ky * nuz >> 1) + l2], make_float4(a.x, a.y, b.x, b.y));
+      }
+    }
+  } else {
+    const int cnt = L * 16;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int l = e & 15, ky = e >> 4;
+      if (z0 + l < nuz) __stcg(&I1[base + (size_t)ky * nuz + l], T[trow<E>(ky) + l]);
+    }
   }
 }
 
