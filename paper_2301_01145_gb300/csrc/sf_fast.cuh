@@ -436,10 +436,23 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, 5) k_fx(const Prob<float> *pr
   __syncthreads();
   V *out = reinterpret_cast<V *>(P.A);
   const size_t plane = (size_t)nuz * nuy;
-  const int cnt = (half + 1) * 16;
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const int l = e & 15, kx = e >> 4;
-    if (y0 + l < nuy) out[((size_t)c * nsx + kx) * plane + (size_t)qz * nuy + y0 + l] = T[kx * 17 + l];
+  if ((nuy & 1) == 0) {
+    // pairs of y as 16-byte stores (y0 and nuy even keep every pair aligned and inside the row)
+    const int cnt = (half + 1) * 8;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int l2 = e & 7, kx = e >> 3;
+      if (y0 + 2 * l2 < nuy) {
+        const V a = T[kx * 17 + 2 * l2], b = T[kx * 17 + 2 * l2 + 1];
+        float4 *dst = reinterpret_cast<float4 *>(out + ((size_t)c * nsx + kx) * plane + (size_t)qz * nuy + y0 + 2 * l2);
+        *dst = make_float4(a.x, a.y, b.x, b.y);
+      }
+    }
+  } else {
+    const int cnt = (half + 1) * 16;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int l = e & 15, kx = e >> 4;
+      if (y0 + l < nuy) out[((size_t)c * nsx + kx) * plane + (size_t)qz * nuy + y0 + l] = T[kx * 17 + l];
+    }
   }
 }
 
