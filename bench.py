@@ -100,7 +100,7 @@ def kernel_bytes(n: int, elem: int = 4):
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fyz launch of this
 # workload (256^3 curl, split z stage), from the ncu capture summarised in
 # profiles/k_fyz_c3_256.md; None when the kernel has changed since.
-K_FYZ_TRAFFIC_256 = None
+K_FYZ_TRAFFIC_256 = 472_535_040 + 910_688_768
 
 
 def read_peaks():
@@ -247,6 +247,64 @@ def cpu_baseline(n: int):
     return {"value": n ** 3 * reps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{reps} oracle solve(s) of the same workload at {n}^3 (padded {2 * n}^3), psi + curl, "
                       f"FP64, single-threaded numpy, {dt:.1f} s"}
+
+
+def cpu_fast_baseline(n: int, gpu_psi=None, gpu_u=None):
+    """The same unbounded curl solve with scipy.fft on all host cores (FP32 and FP64).
+
+    A fast CPU comparison beside the oracle: zero-padded real FFTs of length
+    2n on every axis (the Green's table and its transform are set-up, outside
+    the timed region), psi_hat = g_hat * omega_hat (g_hat = h^3 FFT of
+    G(r) = erf(r / (sigma sqrt 2)) / (4 pi r), the wrap offset n taken as +n),
+    u_hat = i k x psi_hat on the doubled grid's wavenumbers (Nyquist zero),
+    inverse FFTs, crop to [0, n).  Its relative L2 difference from the GPU
+    result is reported as a cross-check.
+    """
+    import numpy as np
+    import scipy.fft as sfft
+    import scipy.special as ssp
+
+    import workloads
+
+    cores = os.cpu_count() or 1
+    h = 1.0 / n
+    L = 2 * n
+    sigma = 2.0 * h
+    omega64 = workloads.vortex_ring(n)["omega"]
+    d = np.arange(L, dtype=np.float64)
+    d = np.where(d <= n, d, d - L) * h
+    r = np.sqrt(d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        G = ssp.erf(r / (sigma * math.sqrt(2.0))) / (4.0 * math.pi * r)
+    G[0, 0, 0] = math.sqrt(2.0) / (4.0 * math.pi ** 1.5 * sigma)
+    ghat64 = sfft.rfftn(G * h ** 3, workers=cores).real
+    del G, r
+    k = np.fft.fftfreq(L, d=2.0 / L) * 2.0 * math.pi  # period 2 (doubled unit domain)
+    k[L // 2] = 0.0
+    kr = np.fft.rfftfreq(L, d=2.0 / L) * 2.0 * math.pi
+    kr[-1] = 0.0
+    out = {"kind": "scipy.fft", "cores": cores, "sample": f"one full {n}^3 solve (padded {L}^3), psi + curl"}
+    for prec, rdt in (("f32", np.float32), ("f64", np.float64)):
+        om = omega64.astype(rdt)
+        ghat = ghat64.astype(rdt)
+        kz = k.astype(rdt)[:, None, None]
+        ky = k.astype(rdt)[None, :, None]
+        kx = kr.astype(rdt)[None, None, :]
+        t0 = time.perf_counter()
+        ph = [sfft.rfftn(om[c], s=(L, L, L), workers=cores) * ghat for c in range(3)]
+        uh = [1j * (ky * ph[2] - kz * ph[1]), 1j * (kz * ph[0] - kx * ph[2]), 1j * (kx * ph[1] - ky * ph[0])]
+        psi = [sfft.irfftn(a, s=(L, L, L), workers=cores)[:n, :n, :n] for a in ph]
+        u = [sfft.irfftn(a, s=(L, L, L), workers=cores)[:n, :n, :n] for a in uh]
+        dt = time.perf_counter() - t0
+        out[prec] = {"value": n ** 3 / dt, "unit": UNIT, "ms_per_solve": dt * 1e3}
+        if gpu_psi is not None and prec == "f32":
+            num = sum(float(np.sum((psi[c] - gpu_psi[c]) ** 2)) for c in range(3))
+            den = sum(float(np.sum(gpu_psi[c].astype(np.float64) ** 2)) for c in range(3))
+            numu = sum(float(np.sum((u[c] - gpu_u[c]) ** 2)) for c in range(3))
+            denu = sum(float(np.sum(gpu_u[c].astype(np.float64) ** 2)) for c in range(3))
+            out["rel_l2_vs_gpu"] = {"psi": math.sqrt(num / den), "u": math.sqrt(numu / denu)}
+        del ph, uh, psi, u
+    return out
 
 
 def _events_time(fn, steps, stream):
@@ -424,6 +482,7 @@ def main():
 
     kms, ksolves = plan.kernel_ms()
     plan.timing(False)
+    fma_tflops = sf._lib.sf_probe_fp32_fma()  # measured FP32 FMA stream, after the timed region
 
     # roofline of the dominant kernel (the y/z executor, bound by FP32 issue),
     # timed per launch by the events above; the other kernels and the whole
@@ -446,6 +505,7 @@ def main():
                 "traffic": K_FYZ_TRAFFIC_256 if n == 256 else None, "algorithmic_bytes": kb["yz_executor"],
                 "algorithmic_flops": kf["yz_executor"],
                 "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz",
+                "peak_fma_measured": fma_tflops, "frac_of_fma_measured": dom["TFLOP/s"] / fma_tflops,
                 "kernels": kernels, "solves_timed": ksolves,
                 "step_hbm": {"achieved": b_method / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                              "frac": b_method / (ms * 1e-3) / 1e9 / hbm_peak, "bytes_model": "B_method",
@@ -500,9 +560,13 @@ def main():
                 "f32_rel_l2_vs_f64": {"psi": rel, "u": relu}}
         p64.close()
 
-    cpu = None
+    cpu = cpu_fast = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.cpu_n)
+        try:
+            cpu_fast = cpu_fast_baseline(n, psi.cpu().numpy(), u.cpu().numpy())
+        except ImportError as exc:  # scipy missing on the host
+            cpu_fast = {"unavailable": str(exc)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -510,7 +574,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": c3_config(n, world, args.unfused),
                 "gpu_launches": launches, "roofline": roof, "clocks": clocks, "e2e": e2e, "fp64": fp64,
-                "cpu_baseline": cpu}
+                "cpu_baseline": cpu, "cpu_fast": cpu_fast}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

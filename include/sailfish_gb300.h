@@ -259,6 +259,15 @@ sf_status sf_solve_static(const sf_plan_desc *d, const void *dev_f, void *dev_ps
  * the wait did not give up).  No work is done on user data. */
 sf_status sf_selftest_timeout(int timeout_ms, void *cuda_stream);
 
+/* Measured FP32 FMA throughput of the current device in TFLOP/s (one FMA =
+ * 2 flop): 8 independent FMA chains per thread on 8 CTAs x 256 threads per
+ * SM, one launch of about 30 ms timed with CUDA events on cuda_stream (NULL:
+ * the legacy default stream), after one shorter warm-up launch.  It is the
+ * measured counterpart of the unit-count FP32 peak against which the
+ * register fast path (bound by FP32 issue) is quoted; the paper has no such
+ * step.  SF_ERR_ARG for a null result pointer, SF_ERR_CUDA on a CUDA error. */
+sf_status sf_probe_fp32_fma(double *tflops, void *cuda_stream);
+
 /* Release a plan or batch and its device memory (waits for its stream). */
 sf_status sf_plan_destroy(sf_plan p);
 

@@ -80,6 +80,7 @@ SIGNATURES = {
     "sf_solve_static": (c_int, [POINTER(sf_plan_desc), c_void_p, c_void_p, c_void_p]),
     "sf_plan_stats": (c_int, [c_void_p, POINTER(c_double)]),
     "sf_plan_timing": (c_int, [c_void_p, c_int]),
+    "sf_probe_fp32_fma": (c_int, [POINTER(c_double), c_void_p]),
     "sf_plan_kernel_ms": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), POINTER(c_int)]),
     "sf_plan_destroy": (c_int, [c_void_p]),
     "sf_status_string": (c_char_p, [c_int]),
@@ -242,6 +243,13 @@ def sf_plan_kernel_ms(plan):
     ns, nsol = c_int(0), c_int(0)
     _check(load().sf_plan_kernel_ms(plan, ms, ctypes.byref(ns), ctypes.byref(nsol)), "sf_plan_kernel_ms")
     return [ms[k] for k in range(ns.value)], nsol.value
+
+
+def sf_probe_fp32_fma(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device (TFLOP/s)."""
+    out = c_double(0.0)
+    _check(load().sf_probe_fp32_fma(ctypes.byref(out), _stream(stream)), "sf_probe_fp32_fma")
+    return out.value
 
 
 def sf_plan_destroy(plan):

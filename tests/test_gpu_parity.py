@@ -327,3 +327,10 @@ def test_kernel_timing_slots():
         plan.execute(f, psi, u)
         plan.sync()
         plan.close()
+
+
+def test_fp32_fma_probe():
+    # measured FMA stream vs the unit-count peak (152 SMs x 128 lanes x 2 x up to 2.07 GHz)
+    import paper_2301_01145_gb300 as sf
+    tf = sf._lib.sf_probe_fp32_fma()
+    assert 10.0 < tf < 90.0
