@@ -344,6 +344,9 @@ template <int E, int M> __host__ __device__ constexpr int fast_wsm_elems() { ret
 #define SF_YF_ROWS 16  // z rows per YF tile
 #define SF_ZS_ROWS 8   // ky rows per ZS tile (one per warp)
 #define SF_YI_COLS 16  // z columns per YI tile
+#ifndef SF_YI_SPLIT_ROWS
+#define SF_YI_SPLIT_ROWS 32  // z rows per YI tile of the split curl (4 per warp)
+#endif
 template <typename T> __host__ __device__ inline int fast_tiles_yf(const Prob<T> &Q, int nkx) {
   return Q.nin * nkx * cdiv(Q.nuz, SF_YF_ROWS);
 }
@@ -354,7 +357,7 @@ template <typename T> __host__ __device__ inline bool fast_split_curl(const Prob
 }
 __host__ __device__ inline int fast_tiles_zs(int nkx, int L) { return nkx * (L / SF_ZS_ROWS); }
 template <typename T> __host__ __device__ inline int fast_tiles_yi(const Prob<T> &Q, int nkx) {
-  return Q.nout * nkx * cdiv(Q.nuz, SF_YI_COLS);
+  return Q.nout * nkx * cdiv(Q.nuz, fast_split_curl(Q) ? SF_YI_SPLIT_ROWS : SF_YI_COLS);
 }
 
 // ---------------------------------------------------------------------------
@@ -888,7 +891,7 @@ __device__ __forceinline__ void fast_zs_split(const Prob<float> &P, const FastGe
 // YI of the split path: whole ky rows of the transposed I2 [f][kxl][z][ky],
 // loaded directly in the k layout of the inverse transform (for every
 // register j the 32 lanes cover two runs of 16 consecutive ky), the curl
-// outputs combined in y-spectral space on the way in; two z rows per warp.
+// outputs combined in y-spectral space on the way in; SF_YI_SPLIT_ROWS / 8 z rows per warp.
 template <int E, bool PAD>
 __device__ __forceinline__ void fast_yi_rows(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
                                              cx<float> *wsm) {
@@ -896,7 +899,9 @@ __device__ __forceinline__ void fast_yi_rows(const Prob<float> &P, const FastGeo
   constexpr int L = 32 * E;
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   const int nuy = P.nuy, nuz = P.nuz, nsx = P.nsx;
-  const int tz = cdiv(nuz, SF_YI_COLS);
+  constexpr int RPW = SF_YI_SPLIT_ROWS / (SF_FAST_THREADS / 32);  // rows per warp
+  static_assert(RPW >= 1 && RPW * (SF_FAST_THREADS / 32) == SF_YI_SPLIT_ROWS, "rows per YI tile");
+  const int tz = cdiv(nuz, SF_YI_SPLIT_ROWS);
   const int iz = tile % tz;
   const int rest = tile / tz;
   const int kxl = rest % ps.nkx;
@@ -912,8 +917,8 @@ __device__ __forceinline__ void fast_yi_rows(const Prob<float> &P, const FastGeo
   const float kxv = __ldg(&P.ax[0].kap[kx]);
   const float ky1 = __ldg(&P.ax[1].kap[1]);
 #pragma unroll 1
-  for (int h = 0; h < 2; ++h) {
-    const int z = iz * SF_YI_COLS + 2 * warp + h;
+  for (int h = 0; h < RPW; ++h) {
+    const int z = iz * SF_YI_SPLIT_ROWS + RPW * warp + h;
     if (z >= nuz) break;  // uniform over the warp
     const V *ra = I2 + (((size_t)fa * g.S + kxl) * nuz + z) * L;
     const V *rb = I2 + (((size_t)fb * g.S + kxl) * nuz + z) * L;
