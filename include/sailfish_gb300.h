@@ -175,6 +175,21 @@ sf_status sf_execute(sf_plan p, const void *dev_f, void *dev_psi, void *dev_op_o
  * staging buffers owned by the plan. */
 sf_status sf_solve_host(sf_plan p, const void *host_f, void *host_psi, void *host_op_out);
 
+/* n independent end-to-end solves on HOST buffers, pipelined: host_f[i] is
+ * copied host->device on a side stream while solve i-1 runs on the plan
+ * stream, and the results of solve i are copied device->host on a second
+ * side stream while solve i+1 runs.  Two device staging sets owned by the
+ * plan alternate (allocated on first use: 2 x (ncomp + nop) fields).  Returns
+ * after every copy has landed.  host_f, host_psi (and host_op_out when
+ * op != NONE) are tables of n host pointers laid out as for sf_solve_host;
+ * pinned memory gives full copy bandwidth and lets the copies overlap the
+ * solves.  An input buffer may appear more than once; an output buffer
+ * written twice holds the later solve.  SF_ERR_ARG for a null table or
+ * entry, n < 0; SF_ERR_STATE on a batch.  The paper has no counterpart (its
+ * solver works on host memory one call at a time). */
+sf_status sf_solve_host_many(sf_plan p, int n, const void *const *host_f, void *const *host_psi,
+                             void *const *host_op_out);
+
 /* Transposed solve for gradients: given dL/dpsi (g_psi, may be NULL) and
  * dL/d(op output) (g_op, may be NULL), write dL/df into g_f.  The solve is
  * affine in f; boundary data only shifts it, so it does not enter here.

@@ -85,6 +85,10 @@ class Plan:
     def solve_host(self, f_host, psi_host, op_host=None):
         sf_solve_host(self.handle, f_host, psi_host, op_host)
 
+    def solve_host_many(self, f_hosts, psi_hosts, op_hosts=None):
+        """Pipelined host solves: uploads and downloads overlap the neighbouring solves."""
+        _lib.sf_solve_host_many(self.handle, f_hosts, psi_hosts, op_hosts)
+
     def adjoint(self, g_psi=None, g_op=None, g_f=None):
         torch = _torch()
         if g_f is None:

@@ -80,6 +80,7 @@ SIGNATURES = {
     "sf_solve_static": (c_int, [POINTER(sf_plan_desc), c_void_p, c_void_p, c_void_p]),
     "sf_plan_stats": (c_int, [c_void_p, POINTER(c_double)]),
     "sf_plan_timing": (c_int, [c_void_p, c_int]),
+    "sf_solve_host_many": (c_int, [c_void_p, c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p)]),
     "sf_probe_fp32_fma": (c_int, [POINTER(c_double), c_void_p]),
     "sf_plan_kernel_ms": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), POINTER(c_int)]),
     "sf_plan_destroy": (c_int, [c_void_p]),
@@ -193,6 +194,16 @@ def sf_execute(plan, f, psi, op=None):
 
 def sf_solve_host(plan, f_host, psi_host, op_host=None):
     _check(load().sf_solve_host(plan, _ptr(f_host), _ptr(psi_host), _ptr(op_host)), "sf_solve_host")
+
+
+def sf_solve_host_many(plan, f_hosts, psi_hosts, op_hosts=None):
+    n = len(f_hosts)
+    if len(psi_hosts) != n or (op_hosts is not None and len(op_hosts) != n):
+        raise ValueError("buffer tables differ in length")
+    tf = (c_void_p * n)(*[x.data_ptr() for x in f_hosts])
+    tp = (c_void_p * n)(*[x.data_ptr() for x in psi_hosts])
+    to = (c_void_p * n)(*[x.data_ptr() for x in op_hosts]) if op_hosts is not None else None
+    _check(load().sf_solve_host_many(plan, n, tf, tp, to), "sf_solve_host_many")
 
 
 def sf_solve_adjoint(plan, g_psi, g_op, g_f):

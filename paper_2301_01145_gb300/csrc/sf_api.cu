@@ -476,6 +476,7 @@ struct sf_plan_s {
   virtual sf_status query(size_t in_shape[4], size_t out_shape[4], size_t op_shape[4], size_t *ws) = 0;
   virtual sf_status set_face(int axis, int side, const void *p) = 0;
   virtual sf_status host_solve(const void *hf, void *hpsi, void *hop) = 0;
+  virtual sf_status host_solve_many(int n, const void *const *hf, void *const *hpsi, void *const *hop) = 0;
   virtual ExecCtl *exec_ctl() = 0;
   const void *src = nullptr;
   bool solved = false;
@@ -607,6 +608,58 @@ template <typename T> struct PlanImpl : sf_plan_s {
     SF_TRY(solve_part(true, true, st_in, st_psi, st_op, nullptr));
     SF_CK(cudaMemcpyAsync(hpsi, st_psi, fb * P.ncomp, cudaMemcpyDeviceToHost, stream));
     if (P.nop && hop) SF_CK(cudaMemcpyAsync(hop, st_op, fb * P.nop, cudaMemcpyDeviceToHost, stream));
+    return sync();
+  }
+
+  // n host solves in a pipeline: the upload of solve i+1 and the download of
+  // solve i-1 run on two side streams while solve i runs on the plan stream;
+  // two device staging sets alternate, ordered by events
+  void *pin[2] = {nullptr, nullptr}, *ppsi[2] = {nullptr, nullptr}, *pop[2] = {nullptr, nullptr};
+  cudaStream_t s_up = nullptr, s_down = nullptr;
+  cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_down[2] = {nullptr, nullptr};
+
+  ~PlanImpl() override {
+    if (s_up) cudaStreamSynchronize(s_up);
+    if (s_down) cudaStreamSynchronize(s_down);
+    for (int b = 0; b < 2; ++b) {
+      if (ev_up[b]) cudaEventDestroy(ev_up[b]);
+      if (ev_comp[b]) cudaEventDestroy(ev_comp[b]);
+      if (ev_down[b]) cudaEventDestroy(ev_down[b]);
+    }
+    if (s_up) cudaStreamDestroy(s_up);
+    if (s_down) cudaStreamDestroy(s_down);
+  }
+
+  sf_status host_solve_many(int n, const void *const *hf, void *const *hpsi, void *const *hop) override {
+    const size_t fb = field_elems * sizeof(T);
+    if (!s_up) {
+      for (int b = 0; b < 2; ++b) {
+        SF_TRY(mem.alloc(&pin[b], fb * P.ncomp));
+        SF_TRY(mem.alloc(&ppsi[b], fb * P.ncomp));
+        if (P.nop) SF_TRY(mem.alloc(&pop[b], fb * P.nop));
+        SF_CK(cudaEventCreateWithFlags(&ev_up[b], cudaEventDisableTiming));
+        SF_CK(cudaEventCreateWithFlags(&ev_comp[b], cudaEventDisableTiming));
+        SF_CK(cudaEventCreateWithFlags(&ev_down[b], cudaEventDisableTiming));
+      }
+      SF_CK(cudaStreamCreateWithFlags(&s_up, cudaStreamNonBlocking));
+      SF_CK(cudaStreamCreateWithFlags(&s_down, cudaStreamNonBlocking));
+    }
+    for (int i = 0; i < n; ++i) {
+      const int b = i & 1;
+      if (i >= 2) SF_CK(cudaStreamWaitEvent(s_up, ev_comp[b], 0));  // solve i-2 has read pin[b]
+      SF_CK(cudaMemcpyAsync(pin[b], hf[i], fb * P.ncomp, cudaMemcpyHostToDevice, s_up));
+      SF_CK(cudaEventRecord(ev_up[b], s_up));
+      SF_CK(cudaStreamWaitEvent(stream, ev_up[b], 0));
+      if (i >= 2) SF_CK(cudaStreamWaitEvent(stream, ev_down[b], 0));  // outputs of solve i-2 are home
+      SF_TRY(solve_part(true, true, pin[b], ppsi[b], pop[b], nullptr));
+      SF_CK(cudaEventRecord(ev_comp[b], stream));
+      SF_CK(cudaStreamWaitEvent(s_down, ev_comp[b], 0));
+      SF_CK(cudaMemcpyAsync(hpsi[i], ppsi[b], fb * P.ncomp, cudaMemcpyDeviceToHost, s_down));
+      if (P.nop && hop && hop[i]) SF_CK(cudaMemcpyAsync(hop[i], pop[b], fb * P.nop, cudaMemcpyDeviceToHost, s_down));
+      SF_CK(cudaEventRecord(ev_down[b], s_down));
+    }
+    SF_CK(cudaStreamSynchronize(s_up));
+    SF_CK(cudaStreamSynchronize(s_down));
     return sync();
   }
 };
@@ -1107,6 +1160,9 @@ template <typename T> struct BatchImpl : sf_plan_s {
   sf_status set_face(int, int, const void *) override { return fail(SF_ERR_STATE, "not available on a batch"); }
   ExecCtl *exec_ctl() override { return ctl; }
   sf_status host_solve(const void *, void *, void *) override { return fail(SF_ERR_STATE, "not available on a batch"); }
+  sf_status host_solve_many(int, const void *const *, void *const *, void *const *) override {
+    return fail(SF_ERR_STATE, "not available on a batch");
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -1216,6 +1272,21 @@ sf_status sf_solve_host(sf_plan p, const void *host_f, void *host_psi, void *hos
   if (!host_f || !host_psi) return fail(SF_ERR_ARG, "null buffer");
   if (p->d.op != SF_OP_NONE && !host_op_out) return fail(SF_ERR_ARG, "plan has an operator: op output needed");
   return p->host_solve(host_f, host_psi, host_op_out);
+}
+
+sf_status sf_solve_host_many(sf_plan p, int n, const void *const *host_f, void *const *host_psi,
+                             void *const *host_op_out) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  if (n < 0) return fail(SF_ERR_ARG, "n must be >= 0");
+  if (n == 0) return SF_OK;
+  if (!host_f || !host_psi) return fail(SF_ERR_ARG, "null buffer table");
+  const bool need_op = p->d.op != SF_OP_NONE;
+  if (need_op && !host_op_out) return fail(SF_ERR_ARG, "plan has an operator: op output table needed");
+  for (int i = 0; i < n; ++i) {
+    if (!host_f[i] || !host_psi[i]) return fail(SF_ERR_ARG, "null buffer in table");
+    if (need_op && !host_op_out[i]) return fail(SF_ERR_ARG, "null op output in table");
+  }
+  return p->host_solve_many(n, host_f, host_psi, host_op_out);
 }
 
 sf_status sf_solve_adjoint(sf_plan p, const void *g_psi, const void *g_op, void *g_f) {

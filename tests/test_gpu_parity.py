@@ -334,3 +334,25 @@ def test_fp32_fma_probe():
     import paper_2301_01145_gb300 as sf
     tf = sf._lib.sf_probe_fp32_fma()
     assert 10.0 < tf < 90.0
+
+
+def test_solve_host_many_matches_device_solves():
+    # pipelined host solves (uploads / downloads overlapping the solves) equal device solves
+    import torch
+    import paper_2301_01145_gb300 as sf
+    n = 64
+    plan = sf.Plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=2 / n, rhs_scale=-1.0)
+    fs = [torch.randn(plan.in_shape).pin_memory() for _ in range(5)]
+    ps = [torch.empty(plan.out_shape).pin_memory() for _ in range(5)]
+    us = [torch.empty(plan.op_shape).pin_memory() for _ in range(5)]
+    plan.solve_host_many(fs, ps, us)
+    for i in range(5):
+        psi, u = plan(fs[i].cuda())
+        plan.sync()
+        assert torch.equal(psi.cpu(), ps[i]) and torch.equal(u.cpu(), us[i])
+    # repeated input buffer, two alternating outputs
+    plan.solve_host_many([fs[0]] * 4, [ps[0], ps[1]] * 2, [us[0], us[1]] * 2)
+    psi, u = plan(fs[0].cuda())
+    plan.sync()
+    assert torch.equal(psi.cpu(), ps[0]) and torch.equal(psi.cpu(), ps[1])
+    plan.close()
