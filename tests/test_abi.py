@@ -88,6 +88,13 @@ def test_status_strings_and_version(lib):
     (dict(tune_tile=3), -1),
     (dict(tune_slab=-1), -1),
     (dict(tune_lag=9), -1),
+    (dict(n=(0, 16, 16)), -1),         # empty axis
+    (dict(n=(16, -4, 16)), -1),        # negative size
+    (dict(n=(1, 16, 16)), -1),         # one cell
+    (dict(n=(2, 16, 16), bc="DDD", grid="regular"), -1),  # regular Dirichlet needs >= 3 cells
+    (dict(n=(4096, 16, 16)), -2),      # FFT length above 2048
+    (dict(n=(2, 16, 16)), -2),         # periodic FFT length 2 is below 4
+    (dict(n=(17, 16, 16)), -2),        # odd periodic x length
 ])
 def test_descriptor_validation_without_gpu(lib, mutate, expect):
     from paper_2301_01145_gb300 import _lib
