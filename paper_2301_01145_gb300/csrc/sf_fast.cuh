@@ -1107,8 +1107,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS == 2 ? 2 : 1)
     }
     __syncthreads();
     if (threadIdx.x == 32) {
-      __threadfence();
-      atomicAdd(&done[s_pass[k]], 1u);
+      red_release_add(&done[s_pass[k]], 1u);  // publishes the tile (cumulative over the barrier above)
       const int kind = sPass[k].kind;
       atomicAdd(&ctl->busy_ns[kind], global_ns() - s_tbusy[k]);
       atomicAdd(&ctl->tiles[kind], 1ull);

@@ -55,6 +55,11 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+// release reduction: orders every write this thread has observed (through a
+// preceding CTA barrier, the writes of its CTA) before the counter update
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -127,8 +132,7 @@ __global__ void __launch_bounds__(SF_THREADS)
     if (s_ok) run_tile<T>(sP, sPass, it - pass_start[s_pass], reinterpret_cast<cx<T> *>(sf_smem), (size_t)sPass.bufsz);
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(&done[s_pass], 1u);
+      red_release_add(&done[s_pass], 1u);  // publishes the tile (cumulative over the barrier above)
       atomicAdd(&ctl->busy_ns[sPass.kind & 7], global_ns() - t_busy0);
       atomicAdd(&ctl->tiles[sPass.kind & 7], 1ull);
     }
