@@ -179,6 +179,50 @@ def dist_info():
     return world, rank, local
 
 
+def max_over_ranks(x: float) -> float:
+    """Maximum of a per-rank number over the job (the slowest rank's time); x when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float) -> float:
+    """Sum of a per-rank number over the job (units processed by all ranks); x when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def lpt_partition(costs, nranks: int):
+    """Longest-processing-time-first: each item, largest estimated cost first, goes to the least loaded rank."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    loads = [0.0] * nranks
+    parts = [[] for _ in range(nranks)]
+    for i in order:
+        r = min(range(nranks), key=lambda k: (loads[k], k))
+        parts[r].append(i)
+        loads[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def problem_cost(bp) -> float:
+    """Estimated cost of one batch problem: its transform points times log2 of the FFT size."""
+    pts = 1
+    for n in bp.n_cells:
+        pts *= 2 * n if bp.bc in ("U", "D", "N") else n
+    return pts * math.log2(max(pts, 2))
+
+
 def c3_config(n: int, world: int, unfused: bool = False):
     return {"workload": "3D unbounded vector Poisson lap(psi) = -omega, 256^3 cell-centred on "
                         "[-0.5,0.5]^3 padded to 512^3, G2 kernel sigma=2h, outputs psi and "
@@ -328,11 +372,16 @@ def run_other(args):
     import paper_2301_01145_gb300 as sf
     import workloads
 
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
     ge.build()
     stream = torch.cuda.current_stream()
     dev = lambda a, dt=torch.float32: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
-    line = {"unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+    line = {"unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    parallelism = f"replicas x{world}"
     if args.workload == "c1":
         pm = workloads.periodic_modes(64)
         plan = sf.Plan(3, (64,) * 3, (0,) * 3, (2 * math.pi,) * 3, "PPP", eig="PS", prec="f64")
@@ -376,6 +425,13 @@ def run_other(args):
                            "forward + adjoint backward per step", "grid": n}
     else:  # c4
         probs = workloads.batch_problems(512)
+        total_points = sum(bp.out_points() for bp in probs)
+        if world > 1:
+            # independent problems: each rank solves its longest-processing-time share, no collective
+            mine = lpt_partition([problem_cost(bp) for bp in probs], world)[rank]
+            probs = [probs[i] for i in mine]
+            parallelism = f"problem shards x{world} (LPT by estimated cost)"
+            line["scaling"] = "strong"
         plans, fs, ps = [], [], []
         for bp in probs:
             dim = bp.dim
@@ -390,14 +446,21 @@ def run_other(args):
         points, dtype = sum(bp.out_points() for bp in probs), "f32"
         cfg = {"workload": "512 uneven problems in one persistent launch (CUDA graph): 2D 64^2..1024^2, 3D "
                            "32^3..128^3, periodic/Dirichlet/Neumann/unbounded, regular/staggered, low-pass "
-                           "N(0,1) sources", "problems": 512, "points_per_step": points}
+                           "N(0,1) sources", "problems": 512, "points_per_step": total_points}
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    ms = _events_time(step, args.steps, stream)
-    line.update({"metric": f"grid points/s ({args.workload})", "value": points / (ms * 1e-3), "ms_per_step": ms,
+    if world > 1:
+        torch.distributed.barrier()
+    ms = max_over_ranks(_events_time(step, args.steps, stream))
+    points_all = sum_over_ranks(float(points))  # units every rank processed in one step
+    cfg["parallelism"] = parallelism
+    line.update({"metric": f"grid points/s ({args.workload})", "value": points_all / (ms * 1e-3), "ms_per_step": ms,
                  "dtype": dtype, "config": cfg})
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -471,13 +534,9 @@ def main():
     barrier()
     clocks = sampler.stop(t_wall0, t_wall1)
     plan.sync()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
     points = n ** 3
-    value = points * world / (ms * 1e-3)
+    value = sum_over_ranks(float(points)) / (ms * 1e-3)  # every rank solves its own replica
     launches = plan.launches() * args.steps
 
     kms, ksolves = plan.kernel_ms()
@@ -528,12 +587,7 @@ def main():
         def host_many(k):
             plan.solve_host_many([hf] * k, [hpsi[i & 1] for i in range(k)], [hu[i & 1] for i in range(k)])
 
-        def reduce_max(dt):
-            if world > 1:
-                t = torch.tensor([dt], device="cuda")
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                dt = float(t.item())
-            return dt
+        reduce_max = max_over_ranks
 
         # serial: one call per step (upload, solve, download, wait)
         plan.solve_host(hf, hpsi[0], hu[0])
@@ -548,11 +602,11 @@ def main():
         t0 = time.perf_counter()
         host_many(ksteps)
         dt = reduce_max(time.perf_counter() - t0)
-        e2e = {"value": points * world * ksteps / dt, "unit": UNIT, "h2d_bytes_per_step": hf.numel() * 4,
+        e2e = {"value": sum_over_ranks(float(points)) * ksteps / dt, "unit": UNIT, "h2d_bytes_per_step": hf.numel() * 4,
                "d2h_bytes_per_step": (hpsi[0].numel() + hu[0].numel()) * 4, "steps": ksteps,
                "mode": "sf_solve_host_many: pinned host buffers, every step uploads its source and downloads "
                        "psi and u; copies of neighbouring steps overlap the solve",
-               "serial": {"value": points * world * ksteps / dt_serial, "unit": UNIT,
+               "serial": {"value": sum_over_ranks(float(points)) * ksteps / dt_serial, "unit": UNIT,
                           "mode": "sf_solve_host per step (upload, solve, download, wait)"}}
 
     # FP64 plain GPU solve of the same workload (comparison the metric names)
