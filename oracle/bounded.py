@@ -14,6 +14,9 @@ Steps, in the paper's order (Sec. 2.4, the four-step solve):
   7. write the unknowns back and fill regular Dirichlet boundary nodes with the
      face values (x faces first, then y, then z; later faces overwrite shared
      edge nodes).
+An axis may carry a Dirichlet and a Neumann face ('DN' / 'ND'); it is then
+transformed in the quarter-wave sine / cosine basis (r2r.py) and each face
+follows its own lifting rule below.
 
 Boundary lifting (our reading; the paper gives no formulas).  With g the face
 value (Dirichlet: psi; Neumann: d psi / d x_axis) and h the spacing, the
@@ -68,7 +71,7 @@ def lift(desc: Desc, rhs: np.ndarray, faces: Optional[Dict[Tuple[int, int], np.n
     if not faces:
         return out
     for (ax, side), face in faces.items():
-        bc = desc.bc[ax]
+        bc = desc.face(ax, side)
         h = desc.h(ax)
         g = _face_on_unknowns(desc, ax, np.asarray(face, dtype=np.float64))
         if bc == "D":
@@ -153,9 +156,11 @@ def fill_dirichlet(desc: Desc, psi: np.ndarray, faces) -> None:
     if not faces:
         return
     for ax in range(desc.dim):
-        if desc.bc[ax] != "D" or desc.staggered:
+        if desc.staggered:
             continue
         for side in (0, 1):
+            if desc.face(ax, side) != "D":
+                continue
             face = faces.get((ax, side))
             if face is None:
                 continue

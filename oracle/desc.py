@@ -19,7 +19,7 @@ class Desc:
     n: Tuple[int, ...]  # cells per axis (x, y[, z])
     lo: Tuple[float, ...]
     hi: Tuple[float, ...]
-    bc: Tuple[str, ...]  # per axis: 'P', 'D', 'N', 'U'
+    bc: Tuple[str, ...]  # per axis: 'P', 'D', 'N', 'U', or 'DN' / 'ND' (lower face, upper face)
     staggered: bool = True
     eig: str = "PS"  # 'PS' or 'FD2'
     op: str = "NONE"  # 'NONE', 'GRAD', 'DIV', 'CURL', 'NABLA'
@@ -33,21 +33,29 @@ class Desc:
     def length(self, ax: int) -> float:
         return self.hi[ax] - self.lo[ax]
 
+    def face(self, ax: int, side: int) -> str:
+        """Boundary type of one face of an axis ('P', 'D', 'N', 'U')."""
+        b = self.bc[ax]
+        return b[side] if len(b) == 2 else b
+
     def nodes(self, ax: int) -> int:
         """Node count of the input/output array along an axis (Sec. 2.4.2)."""
-        if self.bc[ax] in ("D", "N") and not self.staggered:
+        if self.bc[ax] in ("D", "N", "DN", "ND") and not self.staggered:
             return self.n[ax] + 1
         return self.n[ax]
 
     def unknown_range(self, ax: int) -> Tuple[int, int]:
         """[start, stop) of the unknowns inside the node array.
 
-        Regular Dirichlet axes keep their two boundary nodes as given data; all
-        other axis types solve for every node.
+        On regular grids a Dirichlet face node is given data (filled from the
+        face), a Neumann face node is an unknown; staggered and periodic axes
+        solve for every node.
         """
-        if self.bc[ax] == "D" and not self.staggered:
-            return 1, self.n[ax]
-        return 0, self.nodes(ax)
+        if self.staggered or self.bc[ax] in ("P", "U"):
+            return 0, self.nodes(ax)
+        lo = 1 if self.face(ax, 0) == "D" else 0
+        hi = self.n[ax] if self.face(ax, 1) == "D" else self.n[ax] + 1
+        return lo, hi
 
     def shape(self) -> Tuple[int, ...]:
         """Array shape of one field component in [z][y][x] order."""

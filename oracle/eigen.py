@@ -9,6 +9,8 @@ indexed by the transform's own output index k (FFTW ordering):
   Neumann regular      -(pi k/L)^2                 -(4/h^2) sin^2(pi k / (2(n-1)))
   Neumann staggered    -(pi k/L)^2                 -(4/h^2) sin^2(pi k / (2n))
   Periodic             -(2 pi k'/L)^2, k'=min(k, n-k)   -(4/h^2) sin^2(pi k / n)
+  Dirichlet-Neumann,   -(pi (k+1/2)/L)^2           -(4/h^2) sin^2(pi (k+1/2) / (2n))
+  Neumann-Dirichlet    (either grid; n = N_c unknowns)
 
 Pinned in tests/test_oracle_eigen.py: the FD2 column must equal the spectrum
 of the explicit 3-point finite-difference matrix with the ghost-node rules,
@@ -32,6 +34,9 @@ def eigenvalues(bc: str, staggered: bool, eig: str, n: int, L: float, h: float) 
     elif bc == "N":
         m = k
         denom = 2.0 * (n - 1) if not staggered else 2.0 * n
+    elif bc in ("DN", "ND"):
+        m = k + 0.5
+        denom = 2.0 * n
     else:
         raise ValueError(bc)
     if eig == "PS":

@@ -91,6 +91,7 @@ def stencil_residual(desc, psi, faces, f):
             near2 = [slice(None)] * dim
             near2[nax] = slice(2, 3) if side == 0 else slice(n - 1, n)
             sgn = -1.0 if side == 0 else 1.0
+            bc = desc.face(ax, side)
             if bc == "D" and not desc.staggered:
                 w[tuple(ghost)] = g  # boundary node value
             elif bc == "D":
@@ -103,7 +104,7 @@ def stencil_residual(desc, psi, faces, f):
         lo_s[nax] = slice(0, n)
         hi_s = [slice(None)] * dim
         hi_s[nax] = slice(2, n + 2)
-        if bc == "P":
+        if desc.bc[ax] == "P":
             lap += (np.roll(u, 1, nax) - 2 * u + np.roll(u, -1, nax)) / h ** 2
         else:
             lap += (w[tuple(lo_s)] - 2 * u + w[tuple(hi_s)]) / h ** 2
@@ -238,3 +239,57 @@ def test_2d_periodic_grad_of_modes():
     np.testing.assert_allclose(psi[0], psi_a, atol=1e-12)
     np.testing.assert_allclose(g[0], 3 * np.cos(3 * X) * np.cos(2 * Y), atol=1e-11)
     np.testing.assert_allclose(g[1], -2 * np.sin(3 * X) * np.sin(2 * Y), atol=1e-11)
+
+
+MIXED = [("DN", "D", "N"), ("ND", "N", "D"), ("DN", "ND", "D"), ("N", "DN", "ND")]
+
+
+@pytest.mark.parametrize("bcs", MIXED)
+@pytest.mark.parametrize("stag", [False, True])
+def test_fd2_residual_mixed_faces(bcs, stag):
+    # one Dirichlet and one Neumann face on an axis (the quarter-wave bases):
+    # the explicit stencil with each face's own ghost rule reproduces the rhs
+    man = workloads.manufactured(seed_index=12)
+    n = (10, 12, 8)
+    case = workloads.bounded_case(man, n, bcs, stag)
+    d = Desc(3, n, (0,) * 3, (1.0,) * 3, bcs, stag, "FD2", rhs_scale=1.3)
+    f = case["f"] / 1.3
+    psi, _ = oracle.solve(d, f, case["faces"])
+    res = stencil_residual(d, psi[0], case["faces"], f)
+    assert np.max(np.abs(res)) < 1e-9 * np.max(np.abs(f))
+
+
+@pytest.mark.parametrize("bcs,stag", [(("DN", "D", "N"), False), (("ND", "DN", "N"), True),
+                                      (("D", "ND", "DN"), False), (("DN", "DN", "ND"), True)])
+def test_fd2_dense_lu_mixed_faces(bcs, stag):
+    n = (5, 6, 4)
+    d = Desc(3, n, (0,) * 3, (1.0, 0.8, 1.3), bcs, stag, "FD2")
+    rng = np.random.default_rng(4)
+    f = rng.normal(size=d.shape())
+    psi, _ = oracle.solve(d, f)
+    A = assemble_fd(d)
+    usl = tuple(slice(*d.unknown_range(ax)) for ax in reversed(range(3)))
+    ref = np.linalg.solve(A, f[usl].ravel()).reshape(f[usl].shape)
+    np.testing.assert_allclose(psi[0][usl], ref, atol=1e-11)
+
+
+@pytest.mark.parametrize("bc", ["DN", "ND"])
+@pytest.mark.parametrize("stag", [False, True])
+def test_ps_quarter_wave_modes_exact(bc, stag):
+    # psi = product of quarter-wave modes sin/cos((m + 1/2) pi x / L) is exact for PS
+    n = (12, 10, 8)
+    L = (1.0, 1.5, 0.75)
+    m = (2, 0, 1)
+    d = Desc(3, n, (0.0,) * 3, L, (bc,) * 3, stag, "PS")
+    coords = []
+    for ax in range(3):
+        h = L[ax] / n[ax]
+        cnt = d.nodes(ax)
+        x = h * (np.arange(cnt) + (0.5 if stag else 0.0))
+        fn = np.sin if bc == "DN" else np.cos
+        coords.append(fn((m[ax] + 0.5) * math.pi * x / L[ax]))
+    psi_a = coords[2][:, None, None] * coords[1][None, :, None] * coords[0][None, None, :]
+    lam = -sum(((m[ax] + 0.5) * math.pi / L[ax]) ** 2 for ax in range(3))
+    psi, _ = oracle.solve(d, lam * psi_a)
+    usl = tuple(slice(*d.unknown_range(ax)) for ax in reversed(range(3)))
+    np.testing.assert_allclose(psi[0][usl], psi_a[usl], atol=1e-12)

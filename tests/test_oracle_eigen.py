@@ -47,10 +47,28 @@ def fd_matrix(bc, staggered, nc, h):
         A[0, 0] = -1
         A[-1, -1] = -1
         return A / h ** 2
+    if bc in ("DN", "ND"):
+        # one Dirichlet and one Neumann face: unknowns are the N_c nodes off the
+        # Dirichlet face (regular) or the N_c cells (staggered)
+        n = nc
+        A = np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)
+        d_end, n_end = (0, n - 1) if bc == "DN" else (n - 1, 0)
+        if staggered:
+            A[d_end, d_end] = -3  # ghost = -psi at a Dirichlet face
+            A[n_end, n_end] = -1  # ghost = psi at a Neumann face
+        else:
+            # Dirichlet face node is data (zero here); Neumann face node is an
+            # unknown with ghost psi_{n+1} = psi_{n-1}
+            if n > 1:
+                A[n_end, n_end - 1 if n_end > 0 else 1] = 2
+            else:
+                A[0, 0] = -2
+        return A / h ** 2
     raise ValueError
 
 
-CASES = [("P", True), ("D", False), ("D", True), ("N", False), ("N", True)]
+CASES = [("P", True), ("D", False), ("D", True), ("N", False), ("N", True),
+         ("DN", False), ("DN", True), ("ND", False), ("ND", True)]
 
 
 @pytest.mark.parametrize("bc,stag", CASES)
@@ -89,16 +107,22 @@ def test_ps_basis_is_continuous_eigenfunction(bc, stag):
         x = lo + h * np.arange(1, nc)
     elif bc == "N" and not stag:
         x = lo + h * np.arange(nc + 1)
+    elif bc == "DN" and not stag:
+        x = lo + h * np.arange(1, nc + 1)
+    elif bc == "ND" and not stag:
+        x = lo + h * np.arange(nc)
     else:
         x = lo + h * (np.arange(nc) + 0.5)
     n = len(x)
     basis = r2r.backward(bc, stag, np.eye(n), 0)
     lam = eigen.eigenvalues(bc, stag, "PS", n, L, h)
+    half = bc in ("DN", "ND")  # quarter-wave modes: m = k + 1/2
     for k in range(n):
         m = math.sqrt(-lam[k]) * L / math.pi
-        assert abs(m - round(m)) < 1e-9
-        fn = np.sin if bc == "D" else np.cos
-        ref = fn(math.pi * round(m) * (x - lo) / L)
+        mm = round(m - 0.5) + 0.5 if half else round(m)
+        assert abs(m - mm) < 1e-9
+        fn = np.sin if bc in ("D", "DN") else np.cos
+        ref = fn(math.pi * mm * (x - lo) / L)
         v = basis[:, k]
         scale = np.dot(v, ref) / np.dot(ref, ref)
         np.testing.assert_allclose(v, scale * ref, atol=1e-12)

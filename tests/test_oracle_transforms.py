@@ -49,8 +49,8 @@ def test_fft_multi_axis():
     np.testing.assert_allclose(fft.idftn(fft.dftn(x, [2, 1]), [2, 1]).real, x, atol=1e-13)
 
 
-KINDS = {"DST1": (1, "dst"), "DST2": (2, "dst"), "DST3": (3, "dst"),
-         "DCT1": (1, "dct"), "DCT2": (2, "dct"), "DCT3": (3, "dct")}
+KINDS = {"DST1": (1, "dst"), "DST2": (2, "dst"), "DST3": (3, "dst"), "DST4": (4, "dst"),
+         "DCT1": (1, "dct"), "DCT2": (2, "dct"), "DCT3": (3, "dct"), "DCT4": (4, "dct")}
 
 
 @pytest.mark.parametrize("kind", sorted(KINDS))
@@ -74,6 +74,16 @@ def test_r2r_inverse_pairs(n):
                 continue
             fwd = r2r.forward(bc, stag, eye, 0)
             back = r2r.backward(bc, stag, fwd, 0)
+            np.testing.assert_allclose(back, eye, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 16, 48])
+def test_r2r_inverse_pairs_mixed_faces(n):
+    # Dirichlet-Neumann / Neumann-Dirichlet axes: forward then backward with its scale is the identity
+    eye = np.eye(n)
+    for bc in ("DN", "ND"):
+        for stag in (False, True):
+            back = r2r.backward(bc, stag, r2r.forward(bc, stag, eye, 0), 0)
             np.testing.assert_allclose(back, eye, atol=1e-12)
 
 

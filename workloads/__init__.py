@@ -127,15 +127,16 @@ def bounded_case(man: Manufactured, n_cells: Tuple[int, int, int], bc: Tuple[str
                  staggered: bool) -> Dict[str, object]:
     """Source, faces and exact potential on the solver's node arrays.
 
-    bc[axis] in {'D', 'N', 'P'}.  Regular D/N axes carry n+1 nodes, staggered
-    and periodic axes n nodes.  Faces are evaluated on the node arrays of the
-    two other axes: D faces hold psi, N faces hold d psi / d x_axis, both at the
+    bc[axis] in {'D', 'N', 'P', 'DN', 'ND'} ('DN': Dirichlet lower face,
+    Neumann upper face).  Regular D/N axes carry n+1 nodes, staggered and
+    periodic axes n nodes.  Faces are evaluated on the node arrays of the two
+    other axes: D faces hold psi, N faces hold d psi / d x_axis, both at the
     boundary plane itself (x = X_l or X_u).
     """
     coords = []
     for ax in range(3):
         nc = n_cells[ax]
-        reg_nodes = (bc[ax] in ("D", "N")) and not staggered
+        reg_nodes = (bc[ax] in ("D", "N", "DN", "ND")) and not staggered
         cnt = nc + 1 if reg_nodes else nc
         coords.append(node_positions(man.lo[ax], man.hi[ax], nc, staggered, cnt))
     xs, ys, zs = coords
@@ -143,13 +144,14 @@ def bounded_case(man: Manufactured, n_cells: Tuple[int, int, int], bc: Tuple[str
     psi = man.field(xs, ys, zs)
     faces = {}
     for ax in range(3):
-        if bc[ax] not in ("D", "N"):
+        if bc[ax] not in ("D", "N", "DN", "ND"):
             continue
         for side, xb in ((0, man.lo[ax]), (1, man.hi[ax])):
+            kind = bc[ax][side] if len(bc[ax]) == 2 else bc[ax]
             pts = [xs, ys, zs]
             pts[ax] = np.array([xb])
             deriv = [0, 0, 0]
-            if bc[ax] == "N":
+            if kind == "N":
                 deriv[ax] = 1
             val = man.field(pts[0], pts[1], pts[2], tuple(deriv))
             faces[(ax, side)] = np.squeeze(val, axis=2 - ax)
