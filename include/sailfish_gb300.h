@@ -70,13 +70,20 @@ typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
  * Problem description (Sec. 2.4 solver options, Sec. 2.5.1 Table 1).
  *   dim        2 or 3.
  *   n[a]       cell count N_c per axis a = x, y, z (n[2] ignored in 2D).  Every
- *              FFT length used (N_c for periodic, 2 N_c otherwise) must be of the
+ *              FFT length used (N_c for periodic, 4 N_c for an axis with a
+ *              Dirichlet and a Neumann face, 2 N_c otherwise) must be of the
  *              form 2^p or 3*2^p and lie in [4, 2048]; N_c >= 2 (>= 3 for
- *              regular Dirichlet).
+ *              regular Dirichlet on both faces).
  *   lo, hi     domain bounds X_l, X_u per axis.
  *   bc[a][s]   boundary type of axis a on its lower (s = 0) and upper (s = 1)
- *              face.  Both faces of an axis must agree (the paper's solvers
- *              use uniform boundaries, Sec. 2.4.1).  Either every axis is
+ *              face.  The faces of an axis agree, or one is Dirichlet and the
+ *              other Neumann: that axis is then transformed in the quarter-wave
+ *              sine (Dirichlet lower) or cosine (Neumann lower) basis, modes
+ *              k + 1/2 (FFTW's RODFT01 / RODFT11 and REDFT01 / REDFT11 on the
+ *              regular / staggered grid), the paper's stated next step beyond
+ *              its uniform boundaries (Sec. 2.4.1).  On a regular grid a
+ *              Dirichlet face node is filled from the face data and a Neumann
+ *              face node is solved for.  Either every axis is
  *              periodic/unbounded, or every axis is Dirichlet/Neumann.
  *   grid       REGULAR or STAGGERED.  Unbounded axes need STAGGERED.
  *   eig        PS or FD2 (bounded axes; ignored when unbounded).

@@ -121,7 +121,8 @@ def make_desc(dim, n, lo, hi, bc, grid="staggered", eig="PS", op="NONE", sigma=0
         d.lo[a] = float(lo[a]) if a < len(lo) else 0.0
         d.hi[a] = float(hi[a]) if a < len(hi) else 1.0
         b = bc[a] if a < len(bc) else "P"
-        pair = (b, b) if isinstance(b, str) else tuple(b)
+        # one letter: both faces; two letters ("DN", "ND") or a pair: (lower face, upper face)
+        pair = ((b, b) if len(b) == 1 else (b[0], b[1])) if isinstance(b, str) else tuple(b)
         d.bc[a][0] = BC[pair[0]]
         d.bc[a][1] = BC[pair[1]]
     d.grid = GRID[grid]

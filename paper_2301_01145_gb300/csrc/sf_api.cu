@@ -91,6 +91,11 @@ AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, b
     case AK_NR: a.nodes = n + 1; a.u0 = 0; a.nu = n + 1; a.L = 2 * n; a.k0 = 0; break;
     case AK_DS: a.nodes = n; a.u0 = 0; a.nu = n; a.L = 2 * n; a.k0 = 1; break;
     case AK_NS: a.nodes = n; a.u0 = 0; a.nu = n; a.L = 2 * n; a.k0 = 0; break;
+    // one Dirichlet and one Neumann face: the Dirichlet axis of 2n cells, mirrored
+    case AK_DNR: a.nodes = n + 1; a.u0 = 1; a.nu = n; a.L = 4 * n; a.k0 = 1; break;
+    case AK_NDR: a.nodes = n + 1; a.u0 = 0; a.nu = n; a.L = 4 * n; a.k0 = 1; break;
+    case AK_DNS: a.nodes = n; a.u0 = 0; a.nu = n; a.L = 4 * n; a.k0 = 1; break;
+    case AK_NDS: a.nodes = n; a.u0 = 0; a.nu = n; a.L = 4 * n; a.k0 = 1; break;
   }
   if (cpath) a.ns = is_x ? a.L / 2 + 1 : a.L;
   else a.ns = a.nu;
@@ -120,11 +125,14 @@ AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, b
       a.twf[2 * i + 1] = std::sin(ang[i]);
     }
   }
-  a.phase.assign(2 * (size_t)(n + 1), 0.0);
-  for (int k = 0; k <= n; ++k) {
+  // phases over k in [0, L/2]; a mixed axis takes those of its doubled Dirichlet axis
+  const int half = L / 2;
+  const int pkind = (kind == AK_DNR || kind == AK_NDR) ? AK_DR : ((kind == AK_DNS || kind == AK_NDS) ? AK_DS : kind);
+  a.phase.assign(2 * (size_t)(half + 1), 0.0);
+  for (int k = 0; k <= half; ++k) {
     double re = 1, im = 0;
-    const double c = std::cos(kPi * k / (2.0 * n)), s = std::sin(kPi * k / (2.0 * n));
-    switch (kind) {
+    const double c = std::cos(kPi * k / (2.0 * half)), s = std::sin(kPi * k / (2.0 * half));
+    switch (pkind) {
       case AK_DR: re = 0; im = -1; break;
       case AK_NS: re = c; im = s; break;
       case AK_DS: re = s; im = -c; break;  // -i e^{i pi k/2n}
@@ -142,6 +150,10 @@ AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, b
       const int kk = std::min(k, n - k);
       if (eig == SF_EIG_PS) a.lam[i] = -std::pow(2.0 * kPi * kk / a.Ldom, 2);
       else a.lam[i] = -(4.0 / (a.h * a.h)) * std::pow(std::sin(kPi * k / n), 2);
+    } else if (ak_mixed(kind)) {
+      const double m = i + 0.5;  // quarter-wave mode k + 1/2 (odd mode 2k+1 of the doubled axis)
+      if (eig == SF_EIG_PS) a.lam[i] = -std::pow(kPi * m / a.Ldom, 2);
+      else a.lam[i] = -(4.0 / (a.h * a.h)) * std::pow(std::sin(kPi * m / (2.0 * n)), 2);
     } else if (kind != AK_U) {
       const int m = i + a.k0;  // mode number of Table 1
       if (eig == SF_EIG_PS) a.lam[i] = -std::pow(kPi * m / a.Ldom, 2);
@@ -587,7 +599,7 @@ template <typename T> struct PlanImpl : sf_plan_s {
   sf_status set_face(int axis, int side, const void *p) override {
     if (axis < 0 || axis >= d.dim || side < 0 || side > 1) return fail(SF_ERR_ARG, "axis/side out of range");
     const int k = P.ax[axis].kind;
-    if (p && !(k == AK_DR || k == AK_DS || k == AK_NR || k == AK_NS))
+    if (p && (k == AK_P || k == AK_U))
       return fail(SF_ERR_ARG, "boundary data needs a Dirichlet or Neumann axis");
     if (p && d.eig != SF_EIG_FD2) return fail(SF_ERR_UNSUPPORTED, "inhomogeneous boundaries need FD2 eigenvalues (Sec. 2.5.2)");
     if (p && P.ncomp != 1) return fail(SF_ERR_UNSUPPORTED, "boundary data only for scalar solves");
@@ -693,8 +705,13 @@ sf_status PlanImpl<float>::run_fast(const Prob<float> &Q, const Prob<float> *dq,
   return SF_OK;
 }
 
-static int axis_kind(int bc, int grid) {
+static int axis_kind(int bc, int grid, int bc_hi = -1) {
   const bool stag = grid == SF_GRID_STAGGERED;
+  if (bc_hi >= 0 && bc_hi != bc) {  // one Dirichlet and one Neumann face
+    if (bc == SF_BC_DIRICHLET && bc_hi == SF_BC_NEUMANN) return stag ? AK_DNS : AK_DNR;
+    if (bc == SF_BC_NEUMANN && bc_hi == SF_BC_DIRICHLET) return stag ? AK_NDS : AK_NDR;
+    return -1;
+  }
   switch (bc) {
     case SF_BC_PERIODIC: return AK_P;
     case SF_BC_UNBOUNDED: return AK_U;
@@ -725,14 +742,17 @@ static sf_status validate(const sf_plan_desc &d) {
     return fail(SF_ERR_ARG, "rhs_scale must be finite and non-zero");
   int ncp = 0, nreal = 0, nunb = 0;
   for (int a = 0; a < d.dim; ++a) {
-    if (d.bc[a][0] != d.bc[a][1]) return fail(SF_ERR_UNSUPPORTED, "different boundary types on the two faces of an axis");
     const int bc = d.bc[a][0];
     if (bc < SF_BC_PERIODIC || bc > SF_BC_UNBOUNDED) return fail(SF_ERR_ARG, "bad boundary type");
+    if (d.bc[a][1] < SF_BC_PERIODIC || d.bc[a][1] > SF_BC_UNBOUNDED) return fail(SF_ERR_ARG, "bad boundary type");
+    const bool mixed = d.bc[a][0] != d.bc[a][1];
+    if (mixed && axis_kind(bc, d.grid, d.bc[a][1]) < 0)
+      return fail(SF_ERR_UNSUPPORTED, "unequal faces on one axis: only a Dirichlet / Neumann pair is supported");
     if (!(d.hi[a] > d.lo[a])) return fail(SF_ERR_ARG, "domain bounds need hi > lo");
     const int n = d.n[a];
-    const int minn = (bc == SF_BC_DIRICHLET && d.grid == SF_GRID_REGULAR) ? 3 : 2;
+    const int minn = (bc == SF_BC_DIRICHLET && d.grid == SF_GRID_REGULAR && !mixed) ? 3 : 2;
     if (n < minn) return fail(SF_ERR_ARG, "too few cells on an axis");
-    const int L = bc == SF_BC_PERIODIC ? n : 2 * n;
+    const int L = bc == SF_BC_PERIODIC ? n : (mixed ? 4 * n : 2 * n);
     if (!valid_len(L)) return fail(SF_ERR_UNSUPPORTED, "FFT length " + std::to_string(L) + " is not 2^p or 3*2^p in [4, 2048]");
     if (bc == SF_BC_PERIODIC || bc == SF_BC_UNBOUNDED) ++ncp;
     else ++nreal;
@@ -768,8 +788,9 @@ template <typename T> static void derive_extents(Prob<T> &P) {
   P.nsz = P.dim == 3 ? P.ax[2].ns : 1;
   const int ndx = P.ax[0].nodes, ndy = P.ax[1].nodes, ndz = P.dim == 3 ? P.ax[2].nodes : 1;
   int fill = 0;
-  if (P.ax[1].kind == AK_DR) fill += 2 * ndz * ndx;
-  if (P.dim == 3 && P.ax[2].kind == AK_DR) fill += 2 * ndy * ndx;
+  const int ym = dnode_mask(P.ax[1].kind), zm = P.dim == 3 ? dnode_mask(P.ax[2].kind) : 0;
+  fill += ((ym & 1) + (ym >> 1)) * ndz * ndx;
+  fill += ((zm & 1) + (zm >> 1)) * ndy * ndx;
   P.fill_count = fill;
 }
 
@@ -790,7 +811,8 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   AxisHost ah[3];
   for (int a = 0; a < 3; ++a) {
     if (a < d.dim) {
-      ah[a] = build_axis(axis_kind(d.bc[a][0], d.grid), d.n[a], d.lo[a], d.hi[a], d.eig, a == 0, p.cpath, d.tune_radix);
+      ah[a] = build_axis(axis_kind(d.bc[a][0], d.grid, d.bc[a][1]), d.n[a], d.lo[a], d.hi[a], d.eig, a == 0, p.cpath,
+                         d.tune_radix);
       prodL *= ah[a].L;
       hd *= ah[a].h;
     } else {  // unused z axis of a 2D problem: a trivial periodic axis of one point
@@ -848,11 +870,10 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   for (int a = 0; a < d.dim; ++a) {
     const double h = ah[a].h;
     double w0 = 0, w1 = 0;
-    switch (ah[a].kind) {
-      case AK_DR: w0 = w1 = -1.0 / (h * h); break;
-      case AK_DS: w0 = w1 = -2.0 / (h * h); break;
-      case AK_NR: w0 = 2.0 / h; w1 = -2.0 / h; break;
-      case AK_NS: w0 = 1.0 / h; w1 = -1.0 / h; break;
+    if (ah[a].kind != AK_P && ah[a].kind != AK_U) {  // each face by its own type
+      const bool reg = d.grid == SF_GRID_REGULAR;
+      w0 = d.bc[a][0] == SF_BC_DIRICHLET ? (reg ? -1.0 : -2.0) / (h * h) : (reg ? 2.0 : 1.0) / h;
+      w1 = d.bc[a][1] == SF_BC_DIRICHLET ? (reg ? -1.0 : -2.0) / (h * h) : -(reg ? 2.0 : 1.0) / h;
     }
     p.facew[a][0] = (T)(w0 / d.rhs_scale);
     p.facew[a][1] = (T)(w1 / d.rhs_scale);
@@ -902,7 +923,7 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   PA.nout = p.ncomp;
   PA.adjoint = 1;
   for (int a = 0; a < d.dim; ++a)
-    if (p.ax[a].kind == AK_NR) PA.nrw = 1;
+    if (p.ax[a].kind == AK_NR || p.ax[a].kind == AK_DNR || p.ax[a].kind == AK_NDR) PA.nrw = 1;
   SF_TRY(mem.alloc(&tmp, 2 * sizeof(Prob<T>)));
   d_probs = (Prob<T> *)tmp;
   SF_CK(cudaMemcpy(d_probs, &P, sizeof(Prob<T>), cudaMemcpyHostToDevice));

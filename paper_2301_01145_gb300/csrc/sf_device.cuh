@@ -162,7 +162,38 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V *x
 // ---------------------------------------------------------------------------
 // problem description (device copy)
 // ---------------------------------------------------------------------------
-enum AxisKind : int { AK_P = 0, AK_U = 1, AK_DR = 2, AK_NR = 3, AK_DS = 4, AK_NS = 5 };
+enum AxisKind : int {
+  AK_P = 0, AK_U = 1, AK_DR = 2, AK_NR = 3, AK_DS = 4, AK_NS = 5,
+  // one Dirichlet and one Neumann face (lower, upper), regular / staggered grid
+  AK_DNR = 6, AK_DNS = 7, AK_NDR = 8, AK_NDS = 9
+};
+
+// An axis with a Dirichlet and a Neumann face is solved as the Dirichlet axis
+// of twice the length whose data are mirrored about the Neumann face (the
+// discrete problem with homogeneous Neumann data at the face is exactly the
+// symmetric half of it).  Its FFT has length L = 4n; only the odd modes of the
+// doubled axis (the quarter-wave modes k + 1/2) carry coefficients.
+__host__ __device__ inline bool ak_mixed(int kind) { return kind >= AK_DNR; }
+__host__ __device__ inline bool ak_mixed_regular(int kind) { return kind == AK_DNR || kind == AK_NDR; }
+// unknown indices (qa, qb) of the doubled Dirichlet axis that hold data index q
+// (qa is the one inside the original half; qb its mirror image, = qa on the Neumann node)
+__host__ __device__ inline void mixed_pair(int kind, int n, int q, int &qa, int &qb) {
+  switch (kind) {
+    case AK_DNR: qa = q; qb = 2 * n - 2 - q; break;
+    case AK_DNS: qa = q; qb = 2 * n - 1 - q; break;
+    case AK_NDR: qa = n - 1 + q; qb = n - 1 - q; break;
+    default: qa = n + q; qb = n - 1 - q; break;  // AK_NDS
+  }
+}
+// regular-grid Dirichlet face nodes of an axis: bit 0 lower face, bit 1 upper face
+__host__ __device__ inline int dnode_mask(int kind) {
+  return kind == AK_DR ? 3 : (kind == AK_DNR ? 1 : (kind == AK_NDR ? 2 : 0));
+}
+// data index q is a regular-grid Neumann face node (weight 1/2 in the discrete
+// orthogonality of its transform; used by the adjoint's end-point weights)
+__host__ __device__ inline bool nr_node(int kind, int q, int nu) {
+  return (kind == AK_NR && (q == 0 || q == nu - 1)) || (kind == AK_DNR && q == nu - 1) || (kind == AK_NDR && q == 0);
+}
 enum OpKind : int { OPK_NONE = 0, OPK_GRAD = 1, OPK_DIV = 2, OPK_CURL = 3, OPK_NABLA = 4 };
 enum PassKind : int {
   PK_XFWD = 0,     // x transform of the source lines, transposed store to A

@@ -38,6 +38,18 @@ template <typename T> __device__ __forceinline__ void put_ext_c(cx<T> *a, const 
 template <typename T> __device__ __forceinline__ void put_ext_r(cx<T> *a, const Axis<T> &ax, int Wp, int j, int q, T v) {
   T *af = reinterpret_cast<T *>(a);
   const int l = j >> 1, part = j & 1;
+  if (ak_mixed(ax.kind)) {  // both mirrored unknowns of the doubled Dirichlet axis, each with its odd image
+    int qa, qb;
+    mixed_pair(ax.kind, ax.n, q, qa, qb);
+    const int off = ak_mixed_regular(ax.kind) ? 1 : 0, L = ax.L;
+    af[2 * ((qa + off) * Wp + l) + part] = v;
+    af[2 * ((L - 1 - qa) * Wp + l) + part] = -v;
+    if (qb != qa) {
+      af[2 * ((qb + off) * Wp + l) + part] = v;
+      af[2 * ((L - 1 - qb) * Wp + l) + part] = -v;
+    }
+    return;
+  }
   const int m = ext_pos(ax.kind, ax.n, q);
   af[2 * (m * Wp + l) + part] = v;
   int sg;
@@ -46,15 +58,27 @@ template <typename T> __device__ __forceinline__ void put_ext_r(cx<T> *a, const 
 }
 // value of data point q of line j after an inverse transform
 template <typename T> __device__ __forceinline__ T get_ext_r(const cx<T> *a, const Axis<T> &ax, int Wp, int j, int q) {
-  const cx<T> v = a[ext_pos(ax.kind, ax.n, q) * Wp + (j >> 1)];
+  int m;
+  if (ak_mixed(ax.kind)) {
+    int qa, qb;
+    mixed_pair(ax.kind, ax.n, q, qa, qb);
+    m = qa + (ak_mixed_regular(ax.kind) ? 1 : 0);
+  } else {
+    m = ext_pos(ax.kind, ax.n, q);
+  }
+  const cx<T> v = a[m * Wp + (j >> 1)];
   return (j & 1) ? v.y : v.x;
+}
+// FFT index of real coefficient ci (mixed axes: the odd modes of the doubled axis)
+template <typename T> __device__ __forceinline__ int coef_index(const Axis<T> &ax, int ci) {
+  return ak_mixed(ax.kind) ? 2 * ci + 1 : ci + ax.k0;
 }
 
 // Real coefficient ci of real line j (packed in line j/2) from the forward FFT
 // output: Hermitian split, then division by the kind's phase.
 template <typename T> __device__ __forceinline__ T coef_r(const cx<T> *a, const Axis<T> &ax, int Wp, int j, int ci) {
   typedef cx<T> V;
-  const int k = ci + ax.k0;
+  const int k = coef_index(ax, ci);
   const int L = ax.L;
   const int l = j >> 1;
   const V zk = a[k * Wp + l];
@@ -75,12 +99,13 @@ template <typename T> __device__ __forceinline__ T coef_r(const cx<T> *a, const 
 template <typename T, typename CGet>
 __device__ __forceinline__ void build_spec_r(cx<T> *a, const Axis<T> &ax, int Wp, int W, CGet cget) {
   typedef cx<T> V;
-  const int n = ax.n, L = ax.L;
-  const int cnt = W * (n + 1);
+  const int L = ax.L, half = L / 2;
+  const bool mixed = ak_mixed(ax.kind);
+  const int cnt = W * (half + 1);
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const int l = e % W;
     const int k = e / W;
-    const int ci = k - ax.k0;
+    const int ci = mixed ? ((k & 1) ? (k >> 1) : -1) : k - ax.k0;
     V ea = czero<V>(), eb = czero<V>();
     if (ci >= 0 && ci < ax.ns) {
       const V ph = ax.phase[k];
@@ -89,7 +114,7 @@ __device__ __forceinline__ void build_spec_r(cx<T> *a, const Axis<T> &ax, int Wp
       eb = cscale(ph, cb);
     }
     a[k * Wp + l] = mk<V>(ea.x - eb.y, ea.y + eb.x);
-    if (k >= 1 && k <= n - 1) a[(L - k) * Wp + l] = mk<V>(ea.x + eb.y, eb.x - ea.y);
+    if (k >= 1 && k <= half - 1) a[(L - k) * Wp + l] = mk<V>(ea.x + eb.y, eb.x - ea.y);
   }
 }
 
@@ -224,10 +249,10 @@ template <typename T> __device__ void tile_xfwd(const Prob<T> &P, const Pass<T> 
           if (qz == nuz - 1 && P.face[2][1]) v += P.facew[2][1] * P.face[2][1][(size_t)yn * ndx + xn];
         }
       }
-      if (P.nrw) {  // adjoint end-point weights of regular-Neumann axes
-        if (X.kind == AK_NR && (q == 0 || q == nux - 1)) v *= (T)2;
-        if (Y.kind == AK_NR && (qy == 0 || qy == nuy - 1)) v *= (T)2;
-        if (P.dim == 3 && Z.kind == AK_NR && (qz == 0 || qz == nuz - 1)) v *= (T)2;
+      if (P.nrw) {  // adjoint end-point weights of regular-grid Neumann face nodes
+        if (nr_node(X.kind, q, nux)) v *= (T)2;
+        if (nr_node(Y.kind, qy, nuy)) v *= (T)2;
+        if (P.dim == 3 && nr_node(Z.kind, qz, nuz)) v *= (T)2;
       }
       put_ext_r<T>(a, X, Wp, r, q, v);
     }
@@ -484,11 +509,12 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
     for (int c = 0; c < ncomp; ++c) {
       fwd_field(c, c);
       V *a = bufs[c];
-      const int n = ax.n;
-      const int cnt = Wl * (n + 1);
+      const int half = L / 2;
+      const bool mixed = ak_mixed(ax.kind);
+      const int cnt = Wl * (half + 1);
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         const int l = e % Wl, k = e / Wl;
-        const int ci = k - ax.k0;
+        const int ci = mixed ? ((k & 1) ? (k >> 1) : -1) : k - ax.k0;
         const V zk = a[k * Wp + l];
         const V zm = a[((L - k) % L) * Wp + l];
         V ea = mk<V>((zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5);
@@ -510,7 +536,7 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
         ea = cscale(ph, ca);
         eb = cscale(ph, cb);
         a[k * Wp + l] = mk<V>(ea.x - eb.y, ea.y + eb.x);
-        if (k >= 1 && k <= n - 1) a[(L - k) * Wp + l] = mk<V>(ea.x + eb.y, eb.x - ea.y);
+        if (k >= 1 && k <= half - 1) a[(L - k) * Wp + l] = mk<V>(ea.x + eb.y, eb.x - ea.y);
       }
       __syncthreads();
       inv_field(c, c);
@@ -685,8 +711,9 @@ template <typename T> __device__ void tile_xinv(const Prob<T> &P, const Pass<T> 
   T *dst = P.out_ptr[f];
   const int zn = P.dim == 3 ? qz + Z.u0 : 0;
   const int ndx = X.nodes, ndy = Y.nodes;
-  const bool dr = X.kind == AK_DR;
-  const int nxw = dr ? nux + 2 : nux;  // regular Dirichlet: also write the two boundary nodes
+  const int dmask = dnode_mask(X.kind);  // regular-grid Dirichlet face nodes of x, also written here
+  const int nbd = (dmask & 1) + (dmask >> 1);
+  const int nxw = nux + nbd;
   const int cnt = nl * nxw;
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const int r = e / nxw;
@@ -695,8 +722,8 @@ template <typename T> __device__ void tile_xinv(const Prob<T> &P, const Pass<T> 
     const int yn = qy + Y.u0;
     int xn;
     T v;
-    if (dr && p >= nux) {  // boundary node x = 0 or x = n
-      const int side = p - nux;
+    if (p >= nux) {  // boundary node x = 0 or x = n
+      const int side = nbd == 2 ? p - nux : (dmask == 1 ? 0 : 1);
       xn = side == 0 ? 0 : X.n;
       v = 0;
       if (!P.adjoint && P.face[0][side]) v = P.face[0][side][(size_t)zn * ndy + yn];
@@ -704,9 +731,9 @@ template <typename T> __device__ void tile_xinv(const Prob<T> &P, const Pass<T> 
       xn = p + X.u0;
       v = get_ext_r<T>(a, X, Wp, r, p);
       if (P.nrw) {
-        if (X.kind == AK_NR && (p == 0 || p == nux - 1)) v *= (T)0.5;
-        if (Y.kind == AK_NR && (qy == 0 || qy == nuy - 1)) v *= (T)0.5;
-        if (P.dim == 3 && Z.kind == AK_NR && (qz == 0 || qz == nuz - 1)) v *= (T)0.5;
+        if (nr_node(X.kind, p, nux)) v *= (T)0.5;
+        if (nr_node(Y.kind, qy, nuy)) v *= (T)0.5;
+        if (P.dim == 3 && nr_node(Z.kind, qz, nuz)) v *= (T)0.5;
       }
     }
     dst[((size_t)zn * ndy + yn) * ndx + xn] = v;
@@ -719,9 +746,10 @@ template <typename T> __device__ void tile_xinv(const Prob<T> &P, const Pass<T> 
 template <typename T> __device__ void tile_fill(const Prob<T> &P, const Pass<T> &ps, int t) {
   const Axis<T> &X = P.ax[0], &Y = P.ax[1], &Z = P.ax[2];
   const int ndx = X.nodes, ndy = Y.nodes, ndz = P.dim == 3 ? Z.nodes : 1;
-  const bool ydr = Y.kind == AK_DR, zdr = P.dim == 3 && Z.kind == AK_DR;
-  const int ny_pl = ydr ? 2 * ndz * ndx : 0;
-  const int nz_pl = zdr ? 2 * ndy * ndx : 0;
+  const int ym = dnode_mask(Y.kind), zm = P.dim == 3 ? dnode_mask(Z.kind) : 0;
+  const int nys = (ym & 1) + (ym >> 1), nzs = (zm & 1) + (zm >> 1);  // Dirichlet face planes per axis
+  const int ny_pl = nys * ndz * ndx;
+  const int nz_pl = nzs * ndy * ndx;
   const int per_field = ny_pl + nz_pl;
   const int total = per_field * P.nout;
   const int chunk = 4096;
@@ -731,18 +759,20 @@ template <typename T> __device__ void tile_fill(const Prob<T> &P, const Pass<T> 
     int g = e - f * per_field;
     T *dst = P.out_ptr[f];
     if (g < ny_pl) {  // y planes
-      const int side = g / (ndz * ndx);
-      g -= side * ndz * ndx;
+      const int si = g / (ndz * ndx);
+      g -= si * ndz * ndx;
+      const int side = nys == 2 ? si : (ym == 1 ? 0 : 1);
       const int zn = g / ndx, xn = g - zn * ndx;
-      if (zdr && (zn == 0 || zn == Z.n)) continue;  // owned by the z planes
+      if (((zm & 1) && zn == 0) || ((zm & 2) && zn == Z.n)) continue;  // owned by the z planes
       const int yn = side == 0 ? 0 : Y.n;
       T v = 0;
       if (!P.adjoint && P.face[1][side]) v = P.face[1][side][(size_t)zn * ndx + xn];
       dst[((size_t)zn * ndy + yn) * ndx + xn] = v;
     } else {
       g -= ny_pl;
-      const int side = g / (ndy * ndx);
-      g -= side * ndy * ndx;
+      const int si = g / (ndy * ndx);
+      g -= si * ndy * ndx;
+      const int side = nzs == 2 ? si : (zm == 1 ? 0 : 1);
       const int yn = g / ndx, xn = g - yn * ndx;
       const int zn = side == 0 ? 0 : Z.n;
       T v = 0;

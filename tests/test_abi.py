@@ -78,7 +78,9 @@ def test_status_strings_and_version(lib):
     (dict(ncomp=0), -1),
     (dict(n=(10, 10, 10)), -2),        # FFT length 20 is not 2^p or 3*2^p
     (dict(bc=("P", "D", "P")), -2),    # periodic mixed with Dirichlet
-    (dict(bc=(("D", "N"), "D", "D")), -2),  # different faces on one axis
+    (dict(bc=(("D", "P"), "D", "D")), -2),  # unequal faces other than a Dirichlet / Neumann pair
+    (dict(bc=(("U", "N"), "D", "D")), -2),
+    (dict(bc=(("D", "N"), "P", "P")), -2),  # a Dirichlet / Neumann axis mixed with periodic axes
     (dict(rhs_scale=0.0), -1),
     (dict(bc="UUU", grid="regular"), -2),
     (dict(bc="UUU", sigma=0.0), -1),

@@ -29,10 +29,12 @@ CASES = [
     Desc(2, (6, 4), (0,) * 2, (1, 2), ("N", "N"), False, "FD2"),
     Desc(3, (4, 4, 6), (0,) * 3, (1,) * 3, ("P",) * 3, True, "PS", op="CURL", ncomp=3),
     Desc(2, (8, 6), (0,) * 2, (1,) * 2, ("P",) * 2, True, "FD2", op="DIV", ncomp=2),
+    Desc(3, (4, 3, 4), (0,) * 3, (1,) * 3, ("DN", "N", "ND"), False, "FD2", rhs_scale=0.5),
+    Desc(2, (5, 4), (0,) * 2, (1, 2), ("ND", "DN"), True, "PS"),
 ]
 
 
-@pytest.mark.parametrize("desc", CASES, ids=lambda d: f"{d.dim}D-{''.join(d.bc)}-{d.op}")
+@pytest.mark.parametrize("desc", CASES, ids=lambda d: f"{d.dim}D-{'-'.join(d.bc)}-{d.op}")
 def test_adjoint_is_dense_transpose(desc):
     A = forward_matrix(desc)
     rng = np.random.default_rng(0)
