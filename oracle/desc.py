@@ -26,6 +26,7 @@ class Desc:
     ncomp: int = 1
     rhs_scale: float = 1.0
     sigma: float = 0.0  # Gaussian core width of the regularised Green's function
+    kernel: str = "G2"  # unbounded kernel: Gaussian regularisation of order 2, 4, 6, 8 or 10
 
     def h(self, ax: int) -> float:
         return (self.hi[ax] - self.lo[ax]) / self.n[ax]

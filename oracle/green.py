@@ -1,4 +1,4 @@
-"""Gaussian-regularised Green's functions (Sec. 2.6.2, the order-2 kernel "G2").
+"""Gaussian-regularised Green's functions (Sec. 2.6.2, kernels "G2" to "G10").
 
 Convention: -lap G = zeta_sigma, the normalised Gaussian of width sigma, so
 that G > 0 and the solution of lap(psi) = s f is psi = -s (G * f).
@@ -10,6 +10,20 @@ that G > 0 and the solution of lap(psi) = s f is psi = -s (G * f).
 (The paper names the kernels but prints no formula; these are the standard
 Gaussian-smoothed kernels and their r -> 0 limits.)  erf and E1 come from
 scipy.special.
+
+Order P = 2m (Sec. 2.6.2: P-th order approximations to the inverse Gaussian
+regularisation).  Our reading: the smoothing zeta_P has the transform
+  zeta_P^(k) = exp(-(k sigma)^2 / 2) * sum_{j<m} (k sigma)^{2j} / (2^j j!),
+the Gaussian times the Taylor series of its inverse cut below order P, so
+that zeta_P^ = 1 + O(k^P).  In real space zeta_P = sum_{j<m} sigma^{2j} /
+(2^j j!) (-lap)^j zeta_sigma, and since -lap G2 = zeta_sigma,
+  G_P = G2 + sum_{j=1}^{m-1} sigma^{2j} / (2^j j!) (-lap)^{j-1} zeta_sigma.
+With u = r^2/sigma^2, (-lap)^j zeta_sigma = zeta_sigma p_j(u) / sigma^{2j}
+where the polynomials follow from the radial Laplacian in d dimensions:
+  p_0 = 1,  p_{j+1} = -[4u p_j'' + (2d - 4u) p_j' + (u - d) p_j].
+Pinned in tests/test_oracle_unbounded.py against the Fourier definition of
+zeta_P (radial quadrature), its vanishing moments, and the order of
+convergence on a Gaussian blob.
 
 Pinned in tests/test_oracle_unbounded.py: lap G = -zeta checked by finite
 differences of the closed form, the r -> 0 limit, and the Gaussian-blob
@@ -40,5 +54,31 @@ def g2_2d(r: np.ndarray, sigma: float) -> np.ndarray:
     return np.where(r > 0.0, val, g0)
 
 
-def green(dim: int, r: np.ndarray, sigma: float) -> np.ndarray:
-    return g2_3d(r, sigma) if dim == 3 else g2_2d(r, sigma)
+def smoothing_poly(dim: int, j: int) -> np.polynomial.Polynomial:
+    """p_j(u) with (-lap)^j zeta_sigma = zeta_sigma p_j(u) / sigma^{2j}, u = r^2 / sigma^2."""
+    P = np.polynomial.Polynomial
+    p = P([1.0])
+    u = P([0.0, 1.0])
+    for _ in range(j):
+        p = -(4.0 * u * p.deriv(2) + (2.0 * dim - 4.0 * u) * p.deriv(1) + (u - dim) * p)
+    return p
+
+
+def gaussian(dim: int, r: np.ndarray, sigma: float) -> np.ndarray:
+    """zeta_sigma: the normalised Gaussian of width sigma in dim dimensions."""
+    r = np.asarray(r, dtype=np.float64)
+    return np.exp(-r * r / (2.0 * sigma * sigma)) / (2.0 * math.pi * sigma * sigma) ** (dim / 2.0)
+
+
+def green(dim: int, r: np.ndarray, sigma: float, kernel: str = "G2") -> np.ndarray:
+    g = g2_3d(r, sigma) if dim == 3 else g2_2d(r, sigma)
+    order = int(kernel[1:])
+    if kernel[0] != "G" or order not in (2, 4, 6, 8, 10):
+        raise ValueError(f"unknown kernel {kernel}")
+    m = order // 2
+    r = np.asarray(r, dtype=np.float64)
+    u = r * r / (sigma * sigma)
+    corr = np.zeros_like(u)
+    for j in range(1, m):
+        corr = corr + smoothing_poly(dim, j - 1)(u) * sigma ** 2 / (2.0 ** j * math.factorial(j))
+    return g + gaussian(dim, r, sigma) * corr

@@ -36,7 +36,7 @@ def green_table(desc: Desc) -> np.ndarray:
         m = np.arange(M)
         d = np.minimum(m, M - m) * desc.h(ax)
         r2 = r2 + ops._bcast(d * d, desc.dim, ax)
-    return green(desc.dim, np.sqrt(r2), desc.sigma)
+    return green(desc.dim, np.sqrt(r2), desc.sigma, desc.kernel)
 
 
 def green_hat(desc: Desc) -> np.ndarray:
@@ -121,7 +121,7 @@ def derivative_tables(desc: Desc):
             else:
                 d = np.arange(desc.n[ax] + 1) * desc.h(ax)
             r2 = r2 + ops._bcast(d * d, dim, ax)
-        g = green(dim, np.sqrt(r2), desc.sigma)
+        g = green(dim, np.sqrt(r2), desc.sigma, desc.kernel)
         nax = dim - 1 - a
         M = 2 * desc.n[a]
         mult = ops.deriv_multiplier(M, M * desc.h(a))
@@ -172,7 +172,7 @@ def sample_points(desc: Desc, f: np.ndarray, points, tables=None):
             o = ops._bcast(o, dim, ax)
             offs.append(o)
             r2 = r2 + (o * desc.h(ax)) ** 2
-        g = green(dim, np.sqrt(r2), desc.sigma)
+        g = green(dim, np.sqrt(r2), desc.sigma, desc.kernel)
         psi_out.append([scale * np.sum(g * f[c]) for c in range(ncomp)])
         if desc.op in ("GRAD", "DIV", "CURL"):
             K = [_gather(tables[a], dim, offs, a) for a in range(dim)]

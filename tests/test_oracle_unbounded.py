@@ -178,3 +178,62 @@ def test_sampled_points_match_full_oracle(op, ncomp, dim):
         np.testing.assert_allclose(ps[i], psi[(slice(None),) + idx], rtol=1e-11, atol=1e-13)
         if opo is not None:
             np.testing.assert_allclose(os_[i], opo[(slice(None),) + idx], rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# higher-order Gaussian kernels G4..G10 (Sec. 2.6.2)
+# ---------------------------------------------------------------------------
+def _zeta_fourier(dim, P, sigma, r):
+    """zeta_P at radius r from its transform exp(-(k s)^2/2) sum_{j<P/2} (k s)^{2j}/(2^j j!) (radial quadrature)."""
+    from scipy import integrate, special
+    m = P // 2
+
+    def zhat(k):
+        return math.exp(-(k * sigma) ** 2 / 2) * sum((k * sigma) ** (2 * j) / (2 ** j * math.factorial(j)) for j in range(m))
+
+    if dim == 3:
+        return integrate.quad(lambda k: zhat(k) * k * math.sin(k * r), 0, 60 / sigma, limit=400)[0] / (2 * math.pi ** 2 * r)
+    return integrate.quad(lambda k: zhat(k) * k * special.j0(k * r), 0, 60 / sigma, limit=400)[0] / (2 * math.pi)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("P", [2, 4, 6, 8, 10])
+def test_higher_order_kernel_laplacian_is_fourier_smoothing(dim, P):
+    # -lap G_P (finite differences of the closed form) equals the smoothing of order P
+    # defined in Fourier space, computed independently by quadrature
+    sig = 0.7
+    scale = abs(_zeta_fourier(dim, P, sig, 1e-3))
+    for r in (0.2, 0.7, 1.3, 2.5):
+        d = 1e-3
+        g = lambda x: float(green.green(dim, np.array(x), sig, f"G{P}"))
+        g0, gp, gm = g(r), g(r + d), g(r - d)
+        lap = (gp - 2 * g0 + gm) / d ** 2 + (dim - 1) / r * (gp - gm) / (2 * d)
+        assert abs(-lap - _zeta_fourier(dim, P, sig, r)) < 1e-4 * scale
+
+
+def test_higher_order_kernels_converge_faster_on_a_blob():
+    # Gaussian blob of width s: the unregularised potential is erf(r/(s sqrt 2))/(4 pi r);
+    # at sigma = 2h the solve's error falls with every step of the kernel order
+    from scipy import special
+    n = 32
+    h = 1.0 / n
+    x = -0.5 + h * (np.arange(n) + 0.5)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    R = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+    s = 0.08
+    om = np.exp(-R ** 2 / (2 * s * s)) / (2 * math.pi * s * s) ** 1.5
+    exact = special.erf(R / (math.sqrt(2) * s)) / (4 * math.pi * R)
+    errs = []
+    for P in (2, 4, 6, 8, 10):
+        d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, rhs_scale=-1.0, sigma=2 * h, kernel=f"G{P}")
+        psi, _ = oracle.solve(d, om[None])
+        errs.append(np.max(np.abs(psi[0] - exact)) / np.max(np.abs(exact)))
+    assert all(errs[i + 1] < 0.5 * errs[i] for i in range(4)), errs
+
+
+def test_g4_matches_its_closed_form():
+    # order 4 in 3D: G4 = G2 + exp(-rho^2/2) / (2 (2 pi)^{3/2} sigma), rho = r / sigma
+    sig = 0.3
+    r = np.array([0.0, 0.05, 0.3, 0.9, 2.0])
+    ref = green.g2_3d(r, sig) + np.exp(-(r / sig) ** 2 / 2) / (2 * (2 * math.pi) ** 1.5 * sig)
+    np.testing.assert_allclose(green.green(3, r, sig, "G4"), ref, rtol=1e-14)
