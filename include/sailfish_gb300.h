@@ -58,7 +58,11 @@ typedef enum { SF_OP_NONE = 0, SF_OP_GRAD = 1, SF_OP_DIV = 2, SF_OP_CURL = 3, SF
 typedef enum { SF_EIG_PS = 0, SF_EIG_FD2 = 1 } sf_eig;
 
 /* Regularised Green's function for unbounded axes (Sec. 2.6.2): order-2 Gaussian. */
-typedef enum { SF_GREEN_G2 = 0 } sf_green;
+/* Unbounded kernels (Sec. 2.6.2): Gaussian regularisation of order 2 to 10.
+ * G_P = G2 + sum_{j=1}^{P/2-1} sigma^{2j} / (2^j j!) (-lap)^{j-1} zeta_sigma, the
+ * kernel whose smoothing has the transform exp(-(k sigma)^2/2) times the Taylor
+ * series of exp(+(k sigma)^2/2) cut below order P (error O((k sigma)^P)). */
+typedef enum { SF_GREEN_G2 = 0, SF_GREEN_G4 = 1, SF_GREEN_G6 = 2, SF_GREEN_G8 = 3, SF_GREEN_G10 = 4 } sf_green;
 
 typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
 

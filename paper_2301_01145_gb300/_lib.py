@@ -112,8 +112,12 @@ def _check(status: int, where: str):
         raise SolverError(status, where, detail)
 
 
+KERNEL = {"G2": 0, "G4": 1, "G6": 2, "G8": 3, "G10": 4}
+
+
 def make_desc(dim, n, lo, hi, bc, grid="staggered", eig="PS", op="NONE", sigma=0.0, ncomp=1, prec="f32",
-              rhs_scale=1.0, flags=0, tune_radix=0, tune_tile=0, tune_slab=0, tune_lag=0) -> sf_plan_desc:
+              rhs_scale=1.0, flags=0, tune_radix=0, tune_tile=0, tune_slab=0, tune_lag=0,
+              kernel="G2") -> sf_plan_desc:
     d = sf_plan_desc()
     d.dim = dim
     for a in range(3):
@@ -128,7 +132,7 @@ def make_desc(dim, n, lo, hi, bc, grid="staggered", eig="PS", op="NONE", sigma=0
     d.grid = GRID[grid]
     d.eig = EIG[eig]
     d.op = OP[op]
-    d.green = 0
+    d.green = KERNEL[kernel]
     d.green_sigma = float(sigma)
     d.ncomp = int(ncomp)
     d.prec = PREC[prec]

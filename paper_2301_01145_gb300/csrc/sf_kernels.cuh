@@ -179,8 +179,32 @@ __device__ inline double sf_expint_e1(double x) {
 }
 
 // G octant [z][y][x] for offsets 0..n per axis (2D: nz = 0)
+// Correction of the order-P kernel over G2 (P = 2m): sigma^2 zeta_sigma(r) Q_m(u),
+// u = r^2 / sigma^2, with Q_m = sum_{j=1}^{m-1} p_{j-1}(u) / (2^j j!) and p_j the
+// polynomial of (-lap)^j zeta_sigma = zeta_sigma p_j(u) / sigma^{2j} in d
+// dimensions (p_0 = 1; 3D p_1 = 3 - u, p_2 = u^2 - 10u + 15, p_3 = -u^3 + 21u^2 -
+// 105u + 105; 2D p_1 = 2 - u, p_2 = u^2 - 8u + 8, p_3 = -u^3 + 18u^2 - 72u + 48).
+// Coefficients of Q_m in powers of u, m = 2..5:
+__device__ __forceinline__ double kernel_q(int dim, int m, double u) {
+  if (m <= 1) return 0.0;
+  if (dim == 3) {
+    switch (m) {
+      case 2: return 0.5;
+      case 3: return 7.0 / 8.0 - u / 8.0;
+      case 4: return 19.0 / 16.0 - u / 3.0 + u * u / 48.0;
+      default: return 187.0 / 128.0 - 233.0 * u / 384.0 + 29.0 * u * u / 384.0 - u * u * u / 384.0;
+    }
+  }
+  switch (m) {
+    case 2: return 0.5;
+    case 3: return 0.75 - u / 8.0;
+    case 4: return 11.0 / 12.0 - 7.0 * u / 24.0 + u * u / 48.0;
+    default: return 25.0 / 24.0 - 23.0 * u / 48.0 + 13.0 * u * u / 192.0 - u * u * u / 384.0;
+  }
+}
+
 static __global__ void k_green_octant(double *out, int nx, int ny, int nz, double hx, double hy, double hz, double sigma,
-                               int dim) {
+                               int dim, int order) {
   const size_t total = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
   const double pi = 3.14159265358979323846264338327950288;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -198,6 +222,11 @@ static __global__ void k_green_octant(double *out, int nx, int ny, int nz, doubl
       const double euler = 0.57721566490153286060651209008240243;
       if (r == 0.0) g = (0.5 * euler - log(sqrt(2.0) * sigma)) / (2.0 * pi);
       else g = -(log(r) + 0.5 * sf_expint_e1(r * r / (2.0 * sigma * sigma))) / (2.0 * pi);
+    }
+    if (order > 2) {  // higher-order Gaussian kernel: G2 + sigma^2 zeta_sigma(r) Q_m(u)
+      const double u = r * r / (sigma * sigma);
+      const double zeta = exp(-0.5 * u) / (dim == 3 ? pow(2.0 * pi * sigma * sigma, 1.5) : 2.0 * pi * sigma * sigma);
+      g += sigma * sigma * zeta * kernel_q(dim, order / 2, u);
     }
     out[i] = g;
   }
