@@ -1,4 +1,5 @@
-"""Gaussian-regularised Green's functions (Sec. 2.6.2, kernels "G2" to "G10").
+"""Regularised Green's functions (Sec. 2.6.2): Gaussian kernels "G2" to "G10" and the
+3D spectral kernel "SPECT" (a sharp cut-off at the grid wavenumber pi / max h).
 
 Convention: -lap G = zeta_sigma, the normalised Gaussian of width sigma, so
 that G > 0 and the solution of lap(psi) = s f is psi = -s (G * f).
@@ -70,7 +71,20 @@ def gaussian(dim: int, r: np.ndarray, sigma: float) -> np.ndarray:
     return np.exp(-r * r / (2.0 * sigma * sigma)) / (2.0 * math.pi * sigma * sigma) ** (dim / 2.0)
 
 
-def green(dim: int, r: np.ndarray, sigma: float, kernel: str = "G2") -> np.ndarray:
+def spectral_3d(r: np.ndarray, kc: float) -> np.ndarray:
+    """Sharp spectral cut-off in 3D: G^(k) = 1/k^2 for |k| <= kc, 0 beyond, i.e.
+    G(r) = Si(kc r) / (2 pi^2 r), G(0) = kc / (2 pi^2).  Si from scipy.special.sici."""
+    r = np.asarray(r, dtype=np.float64)
+    safe = np.where(r > 0.0, r, 1.0)
+    val = special.sici(kc * safe)[0] / (2.0 * math.pi ** 2 * safe)
+    return np.where(r > 0.0, val, kc / (2.0 * math.pi ** 2))
+
+
+def green(dim: int, r: np.ndarray, sigma: float, kernel: str = "G2", kc: float = 0.0) -> np.ndarray:
+    if kernel == "SPECT":
+        if dim != 3:
+            raise ValueError("the spectral kernel is 3D only")
+        return spectral_3d(r, kc)
     g = g2_3d(r, sigma) if dim == 3 else g2_2d(r, sigma)
     order = int(kernel[1:])
     if kernel[0] != "G" or order not in (2, 4, 6, 8, 10):

@@ -28,6 +28,11 @@ from .desc import Desc
 from .green import green
 
 
+def spectral_cutoff(desc: Desc) -> float:
+    """Cut-off wavenumber of the spectral kernel: the largest wavenumber every axis resolves, pi / max h."""
+    return float(np.pi / max(desc.h(a) for a in range(desc.dim)))
+
+
 def green_table(desc: Desc) -> np.ndarray:
     """G on the doubled grid, [2Nz][2Ny][2Nx] (or [2Ny][2Nx])."""
     r2 = 0.0
@@ -36,7 +41,7 @@ def green_table(desc: Desc) -> np.ndarray:
         m = np.arange(M)
         d = np.minimum(m, M - m) * desc.h(ax)
         r2 = r2 + ops._bcast(d * d, desc.dim, ax)
-    return green(desc.dim, np.sqrt(r2), desc.sigma, desc.kernel)
+    return green(desc.dim, np.sqrt(r2), desc.sigma, desc.kernel, spectral_cutoff(desc))
 
 
 def green_hat(desc: Desc) -> np.ndarray:
@@ -50,7 +55,7 @@ def _check(desc: Desc):
         raise NotImplementedError("all axes must be unbounded")
     if not desc.staggered:
         raise NotImplementedError("unbounded solves use the staggered grid")
-    if desc.sigma <= 0:
+    if desc.sigma <= 0 and desc.kernel != "SPECT":
         raise ValueError("sigma must be positive")
 
 
@@ -121,7 +126,7 @@ def derivative_tables(desc: Desc):
             else:
                 d = np.arange(desc.n[ax] + 1) * desc.h(ax)
             r2 = r2 + ops._bcast(d * d, dim, ax)
-        g = green(dim, np.sqrt(r2), desc.sigma, desc.kernel)
+        g = green(dim, np.sqrt(r2), desc.sigma, desc.kernel, spectral_cutoff(desc))
         nax = dim - 1 - a
         M = 2 * desc.n[a]
         mult = ops.deriv_multiplier(M, M * desc.h(a))
@@ -172,7 +177,7 @@ def sample_points(desc: Desc, f: np.ndarray, points, tables=None):
             o = ops._bcast(o, dim, ax)
             offs.append(o)
             r2 = r2 + (o * desc.h(ax)) ** 2
-        g = green(dim, np.sqrt(r2), desc.sigma, desc.kernel)
+        g = green(dim, np.sqrt(r2), desc.sigma, desc.kernel, spectral_cutoff(desc))
         psi_out.append([scale * np.sum(g * f[c]) for c in range(ncomp)])
         if desc.op in ("GRAD", "DIV", "CURL"):
             K = [_gather(tables[a], dim, offs, a) for a in range(dim)]
