@@ -62,7 +62,12 @@ typedef enum { SF_EIG_PS = 0, SF_EIG_FD2 = 1 } sf_eig;
  * G_P = G2 + sum_{j=1}^{P/2-1} sigma^{2j} / (2^j j!) (-lap)^{j-1} zeta_sigma, the
  * kernel whose smoothing has the transform exp(-(k sigma)^2/2) times the Taylor
  * series of exp(+(k sigma)^2/2) cut below order P (error O((k sigma)^P)). */
-typedef enum { SF_GREEN_G2 = 0, SF_GREEN_G4 = 1, SF_GREEN_G6 = 2, SF_GREEN_G8 = 3, SF_GREEN_G10 = 4 } sf_green;
+/* SF_GREEN_SPECTRAL (3D only): the sharp spectral cut-off G^(k) = 1/k^2 for
+ * |k| <= kc = pi / max_axis h, zero beyond, i.e. G(r) = Si(kc r) / (2 pi^2 r);
+ * green_sigma is not used. */
+typedef enum {
+  SF_GREEN_G2 = 0, SF_GREEN_G4 = 1, SF_GREEN_G6 = 2, SF_GREEN_G8 = 3, SF_GREEN_G10 = 4, SF_GREEN_SPECTRAL = 5
+} sf_green;
 
 typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
 

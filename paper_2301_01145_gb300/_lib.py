@@ -112,7 +112,7 @@ def _check(status: int, where: str):
         raise SolverError(status, where, detail)
 
 
-KERNEL = {"G2": 0, "G4": 1, "G6": 2, "G8": 3, "G10": 4}
+KERNEL = {"G2": 0, "G4": 1, "G6": 2, "G8": 3, "G10": 4, "SPECT": 5}
 
 
 def make_desc(dim, n, lo, hi, bc, grid="staggered", eig="PS", op="NONE", sigma=0.0, ncomp=1, prec="f32",

@@ -761,8 +761,9 @@ static sf_status validate(const sf_plan_desc &d) {
   if (ncp && nreal) return fail(SF_ERR_UNSUPPORTED, "mixing periodic/unbounded with Dirichlet/Neumann axes");
   if (nunb && nunb != d.dim) return fail(SF_ERR_UNSUPPORTED, "semi-unbounded domains");
   if (nunb && d.grid != SF_GRID_STAGGERED) return fail(SF_ERR_UNSUPPORTED, "unbounded solves need the staggered grid");
-  if (nunb && (d.green < SF_GREEN_G2 || d.green > SF_GREEN_G10)) return fail(SF_ERR_ARG, "bad kernel");
-  if (nunb && !(d.green_sigma > 0.0)) return fail(SF_ERR_ARG, "green_sigma must be positive");
+  if (nunb && (d.green < SF_GREEN_G2 || d.green > SF_GREEN_SPECTRAL)) return fail(SF_ERR_ARG, "bad kernel");
+  if (nunb && d.green == SF_GREEN_SPECTRAL && d.dim != 3) return fail(SF_ERR_UNSUPPORTED, "the spectral kernel is 3D only");
+  if (nunb && d.green != SF_GREEN_SPECTRAL && !(d.green_sigma > 0.0)) return fail(SF_ERR_ARG, "green_sigma must be positive");
   if (ncp && d.bc[0][0] == SF_BC_PERIODIC && (d.n[0] % 2)) return fail(SF_ERR_UNSUPPORTED, "odd periodic x length");
   if (d.op != SF_OP_NONE) {
     if (nreal) return fail(SF_ERR_UNSUPPORTED, "spectral operators on Dirichlet/Neumann axes");
@@ -992,8 +993,11 @@ template <typename T> sf_status PlanImpl<T>::build_green() {
   SF_TRY(tmem.alloc(&A, cnt * sizeof(double)));
   SF_TRY(tmem.alloc(&I1, cnt * sizeof(double)));
   SF_TRY(tmem.alloc(&out, cnt * sizeof(double)));
+  // Gaussian kernels: their order P; spectral kernel: order 0 with the cut-off pi / max h
+  const int korder = d.green == SF_GREEN_SPECTRAL ? 0 : 2 * (d.green - SF_GREEN_G2) + 2;
+  const double kc = kPi / std::max(h[0], std::max(h[1], dim == 3 ? h[2] : 0.0));
   sfg::k_green_octant<<<1024, 256, 0, stream>>>((double *)oct, nx, ny, nz, h[0], h[1], h[2], d.green_sigma, dim,
-                                                 2 * (d.green - SF_GREEN_G2) + 2);
+                                                 korder, kc);
   SF_CK(cudaGetLastError());
   // FP64 real-path problem: regular-Neumann (DCT-I) on every axis, forward only
   Prob<double> G{};

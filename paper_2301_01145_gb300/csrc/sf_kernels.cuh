@@ -179,6 +179,56 @@ __device__ inline double sf_expint_e1(double x) {
 }
 
 // G octant [z][y][x] for offsets 0..n per axis (2D: nz = 0)
+// Sine integral Si(x), x >= 0, in FP64 (set-up of the spectral kernel).
+//   x <= 4: the power series sum_n (-1)^n x^(2n+1) / ((2n+1) (2n+1)!)  (A&S 5.2.14);
+//   x >  4: Si(x) = pi/2 + Im E1(i x), with E1(z) = e^-z / (z + 1 - 1/(z + 3 - 4/(z + 5 - ...)))
+//           (the continued fraction of A&S 5.1.22 in even form), evaluated by the
+//           modified Lentz method in complex arithmetic (at most 200 terms).
+__host__ __device__ inline double sf_sine_integral(double x) {
+  const double half_pi = 1.57079632679489661923132169163975144;
+  if (x <= 4.0) {
+    double p = x, sum = x;  // p = (-1)^n x^(2n+1) / (2n+1)!
+    for (int n = 1; n < 40; ++n) {
+      p *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+      const double t = p / (2.0 * n + 1.0);
+      sum += t;
+      if (fabs(t) < 1e-18 * fabs(sum)) break;
+    }
+    return sum;
+  }
+  // complex numbers as (re, im) pairs; z = i x
+  const double tiny = 1e-300;
+  double br = 1.0, bi = x;  // b_1 = z + 1
+  double cr = 1.0 / tiny, ci = 0.0;
+  double den = br * br + bi * bi;
+  double dr = br / den, di = -bi / den;  // d = 1 / b
+  double hr = dr, hi = di;
+  for (int k = 1; k < 200; ++k) {
+    const double a = -(double)k * (double)k;
+    br += 2.0;  // b_{k+1} = z + 2k + 1
+    // d = 1 / (a d + b)
+    double tr = a * dr + br, ti = a * di + bi;
+    den = tr * tr + ti * ti;
+    dr = tr / den;
+    di = -ti / den;
+    // c = b + a / c
+    den = cr * cr + ci * ci;
+    const double qr = a * cr / den, qi = -a * ci / den;
+    cr = br + qr;
+    ci = bi + qi;
+    // h *= c d
+    const double er = cr * dr - ci * di, ei = cr * di + ci * dr;
+    const double nhr = hr * er - hi * ei, nhi = hr * ei + hi * er;
+    hr = nhr;
+    hi = nhi;
+    if (fabs(er - 1.0) + fabs(ei) < 1e-16) break;
+  }
+  // E1(ix) = e^{-ix} h
+  const double c = cos(x), s = sin(x);
+  const double eim = -s * hr + c * hi;  // Im((c - i s)(hr + i hi))
+  return half_pi + eim;
+}
+
 // Correction of the order-P kernel over G2 (P = 2m): sigma^2 zeta_sigma(r) Q_m(u),
 // u = r^2 / sigma^2, with Q_m = sum_{j=1}^{m-1} p_{j-1}(u) / (2^j j!) and p_j the
 // polynomial of (-lap)^j zeta_sigma = zeta_sigma p_j(u) / sigma^{2j} in d
@@ -203,8 +253,9 @@ __device__ __forceinline__ double kernel_q(int dim, int m, double u) {
   }
 }
 
+// order: 2..10 for the Gaussian kernels, 0 for the 3D spectral cut-off at kc
 static __global__ void k_green_octant(double *out, int nx, int ny, int nz, double hx, double hy, double hz, double sigma,
-                               int dim, int order) {
+                               int dim, int order, double kc) {
   const size_t total = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
   const double pi = 3.14159265358979323846264338327950288;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -215,7 +266,9 @@ static __global__ void k_green_octant(double *out, int nx, int ny, int nz, doubl
     const double dx = x * hx, dy = y * hy, dz = z * hz;
     const double r = sqrt(dx * dx + dy * dy + dz * dz);
     double g;
-    if (dim == 3) {
+    if (order == 0) {  // spectral: Si(kc r) / (2 pi^2 r)
+      g = r == 0.0 ? kc / (2.0 * pi * pi) : sf_sine_integral(kc * r) / (2.0 * pi * pi * r);
+    } else if (dim == 3) {
       if (r == 0.0) g = sqrt(2.0) / (4.0 * pi * sqrt(pi) * sigma);
       else g = erf(r / (sigma * sqrt(2.0))) / (4.0 * pi * r);
     } else {

@@ -97,6 +97,8 @@ def test_status_strings_and_version(lib):
     (dict(n=(4096, 16, 16)), -2),      # FFT length above 2048
     (dict(n=(2, 16, 16)), -2),         # periodic FFT length 2 is below 4
     (dict(n=(17, 16, 16)), -2),        # odd periodic x length
+    (dict(dim=2, bc="UU", kernel="SPECT"), -2),  # the spectral kernel is 3D only
+    (dict(bc="UUU", sigma=0.0, kernel="G6"), -1),  # Gaussian kernels need sigma > 0
 ])
 def test_descriptor_validation_without_gpu(lib, mutate, expect):
     from paper_2301_01145_gb300 import _lib

@@ -31,7 +31,7 @@ def plan_and_desc(dim, n, kernel, op="NONE", ncomp=1, prec="f32", generic=False)
     return plan, d
 
 
-@pytest.mark.parametrize("kernel", ["G4", "G6", "G8", "G10"])
+@pytest.mark.parametrize("kernel", ["G4", "G6", "G8", "G10", "SPECT"])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_kernels_3d_curl(kernel, prec):
     n = (16, 12, 24)
@@ -69,6 +69,21 @@ def test_kernel_g6_fast_path_samples():
     psi, u = plan(to_dev(f, "f32"))
     plan.sync()
     pts = sample_idx(n, 12, 5)
+    ref_psi, ref_u = unbounded.sample_points(d, f, pts)
+    check_samples(to_np(psi), to_np(u), ref_psi, ref_u, pts, 1e-5)
+    plan.close()
+
+
+def test_spectral_kernel_fast_path_samples():
+    # the sharp spectral cut-off on the register fast path (128^3 padded to 256^3)
+    from oracle import unbounded
+    from tests.test_gpu_fullsize import check_samples, sample_idx
+    n = 128
+    plan, d = plan_and_desc(3, (n,) * 3, "SPECT", "CURL", 3, "f32")
+    f = workloads.gaussian_blobs(n)["omega"]
+    psi, u = plan(to_dev(f, "f32"))
+    plan.sync()
+    pts = sample_idx(n, 12, 6)
     ref_psi, ref_u = unbounded.sample_points(d, f, pts)
     check_samples(to_np(psi), to_np(u), ref_psi, ref_u, pts, 1e-5)
     plan.close()
