@@ -8,6 +8,8 @@
 // to the plan's precision.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -322,12 +324,16 @@ template <typename T> struct ExecList {
   }
 };
 
+// kernel attributes are per device: set them once on each device that launches
 template <typename T> sf_status set_kernel_attrs() {
-  static bool done = false;
-  if (done) return SF_OK;
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  SF_CK(cudaGetDevice(&dev));
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load() & bit)) return SF_OK;
   SF_CK(cudaFuncSetAttribute(k_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   SF_CK(cudaFuncSetAttribute(k_exec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  done = true;
+  done.fetch_or(bit);
   return SF_OK;
 }
 

@@ -35,6 +35,8 @@
 // the y inverse forms u = curl psi from them in y-spectral space.
 #pragma once
 
+#include <atomic>
+
 #include "sf_kernels.cuh"
 
 namespace sfg {
@@ -1147,17 +1149,20 @@ template <int E, int OPS> size_t fast_yz_smem(int npass) {
 }
 
 template <int E, int NC, bool PAD, int OPS> int fast_launch_yz(const FastLaunch &fl, const IOArgs<float> &io) {
-  static bool attr = false;
+  static std::atomic<unsigned long long> attr{0};  // devices whose attributes are set
   if (fl.npass > SF_FAST_MAXPASS) return (int)cudaErrorInvalidValue;
   const size_t smyz = fast_yz_smem<E, OPS>(fl.npass);
   cudaError_t e;
-  if (!attr) {
+  int adev = 0;
+  if ((e = cudaGetDevice(&adev)) != cudaSuccess) return (int)e;
+  const unsigned long long abit = adev < 64 ? 1ull << adev : 0ull;
+  if (!abit || !(attr.load() & abit)) {
     e = cudaFuncSetAttribute(k_fyz<E, NC, PAD, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)fast_yz_smem<E, OPS>(SF_FAST_MAXPASS));
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_fyz<E, NC, PAD, OPS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return (int)e;
-    attr = true;
+    attr.fetch_or(abit);
   }
   int dev = 0, nsm = 0, per = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
@@ -1174,9 +1179,12 @@ template <int E, int NC, bool PAD, int OPS> int fast_launch_yz(const FastLaunch 
 template <int E, bool PAD> int fast_launch_all(const FastLaunch &fl, const IOArgs<float> &io, int *launches) {
   const Prob<float> &Q = *fl.h_prob;
   const size_t smx = fast_x_smem<E>(), smxi = smx;
-  static bool attr = false;
+  static std::atomic<unsigned long long> attr{0};  // devices whose attributes are set
   cudaError_t e;
-  if (!attr) {
+  int adev = 0;
+  if ((e = cudaGetDevice(&adev)) != cudaSuccess) return (int)e;
+  const unsigned long long abit = adev < 64 ? 1ull << adev : 0ull;
+  if (!abit || !(attr.load() & abit)) {
     if ((e = cudaFuncSetAttribute(k_fx<E, PAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess)
       return (int)e;
     if ((e = cudaFuncSetAttribute(k_fxi<E, PAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smxi)) != cudaSuccess)
@@ -1185,7 +1193,7 @@ template <int E, bool PAD> int fast_launch_all(const FastLaunch &fl, const IOArg
       return (int)e;
     if ((e = cudaFuncSetAttribute(k_fxi<E, PAD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
       return (int)e;
-    attr = true;
+    attr.fetch_or(abit);
   }
   cudaEvent_t *mk = fl.front && fl.back ? fl.marks : nullptr;
   if (mk && (e = cudaEventRecord(mk[0], fl.stream)) != cudaSuccess) return (int)e;
