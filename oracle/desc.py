@@ -41,7 +41,7 @@ class Desc:
 
     def nodes(self, ax: int) -> int:
         """Node count of the input/output array along an axis (Sec. 2.4.2)."""
-        if self.bc[ax] in ("D", "N", "DN", "ND") and not self.staggered:
+        if self.bc[ax] in ("D", "N", "DN", "ND", "U") and not self.staggered:
             return self.n[ax] + 1
         return self.n[ax]
 

@@ -13,8 +13,12 @@ Steps, in the paper's order:
 
 On a staggered grid the result equals the aperiodic discrete convolution
 psi_i = -rhs_scale h^d sum_j G(x_i - x_j) f_j exactly: offsets only span
--(N-1)..(N-1), so the wrap index N is never used.  Only staggered grids are
-handled (a regular grid would need 2N_c+1 points; not in this build).
+-(N-1)..(N-1), so the wrap index N is never used.  A regular grid carries
+N_c + 1 nodes per axis, so offsets span -N_c..N_c and the padded length must
+be at least 2 N_c + 1 (Sec. 4.3 notes the grid type is otherwise immaterial);
+our reading takes the smallest length of the form 2^p or 3 * 2^p that is at
+least that (the same rule fixes the wavenumbers of the spectral operators).
+With "2N" below read as that padded length M per axis.
 
 Pinned in tests/test_oracle_unbounded.py by brute-force direct summation and
 the closed-form potential of a Gaussian blob.
@@ -33,11 +37,26 @@ def spectral_cutoff(desc: Desc) -> float:
     return float(np.pi / max(desc.h(a) for a in range(desc.dim)))
 
 
+def padded_length(desc: Desc, ax: int) -> int:
+    """Length M of the doubled axis: 2 N_c (staggered), else the smallest 2^p or 3 * 2^p >= 2 N_c + 1."""
+    n = desc.n[ax]
+    if desc.staggered:
+        return 2 * n
+    need = max(2 * n + 1, 4)
+    best = None
+    for base in (1, 3):
+        m = base
+        while m < need:
+            m *= 2
+        best = m if best is None else min(best, m)
+    return best
+
+
 def green_table(desc: Desc) -> np.ndarray:
     """G on the doubled grid, [2Nz][2Ny][2Nx] (or [2Ny][2Nx])."""
     r2 = 0.0
     for ax in range(desc.dim):
-        M = 2 * desc.n[ax]
+        M = padded_length(desc, ax)
         m = np.arange(M)
         d = np.minimum(m, M - m) * desc.h(ax)
         r2 = r2 + ops._bcast(d * d, desc.dim, ax)
@@ -53,8 +72,6 @@ def green_hat(desc: Desc) -> np.ndarray:
 def _check(desc: Desc):
     if not all(b == "U" for b in desc.bc[: desc.dim]):
         raise NotImplementedError("all axes must be unbounded")
-    if not desc.staggered:
-        raise NotImplementedError("unbounded solves use the staggered grid")
     if desc.sigma <= 0 and desc.kernel != "SPECT":
         raise ValueError("sigma must be positive")
 
@@ -62,7 +79,7 @@ def _check(desc: Desc):
 def multipliers(desc: Desc):
     mults, laps = [], []
     for ax in range(desc.dim):
-        M = 2 * desc.n[ax]
+        M = padded_length(desc, ax)
         period = M * desc.h(ax)
         mults.append(ops.deriv_multiplier(M, period))
         laps.append(ops.laplace_multiplier_1d(M, period))
@@ -78,7 +95,7 @@ def solve_unbounded(desc: Desc, f: np.ndarray, g_hat: np.ndarray = None):
     ncomp = f.shape[0]
     dim = desc.dim
     axes = [1 + (dim - 1 - ax) for ax in range(dim)]
-    padded = tuple(2 * desc.n[ax] for ax in reversed(range(dim)))
+    padded = tuple(padded_length(desc, ax) for ax in reversed(range(dim)))
     fp = np.zeros((ncomp,) + padded)
     fp[(slice(None),) + tuple(slice(0, n) for n in f.shape[1:])] = f
     if g_hat is None:
@@ -119,7 +136,7 @@ def derivative_tables(desc: Desc):
     for a in range(dim):
         r2 = 0.0
         for ax in range(dim):
-            M = 2 * desc.n[ax]
+            M = padded_length(desc, ax)
             if ax == a:
                 m = np.arange(M)
                 d = np.minimum(m, M - m) * desc.h(ax)
@@ -128,7 +145,7 @@ def derivative_tables(desc: Desc):
             r2 = r2 + ops._bcast(d * d, dim, ax)
         g = green(dim, np.sqrt(r2), desc.sigma, desc.kernel, spectral_cutoff(desc))
         nax = dim - 1 - a
-        M = 2 * desc.n[a]
+        M = padded_length(desc, a)
         mult = ops.deriv_multiplier(M, M * desc.h(a))
         shape = [1] * dim
         shape[nax] = -1
@@ -165,7 +182,7 @@ def sample_points(desc: Desc, f: np.ndarray, points, tables=None):
     for ax in range(dim):
         hd *= desc.h(ax)
     scale = -desc.rhs_scale * hd
-    src = [np.arange(desc.n[ax]) for ax in range(dim)]
+    src = [np.arange(desc.nodes(ax)) for ax in range(dim)]
     if desc.op not in ("NONE",) and desc.op != "NABLA" and tables is None:
         tables = derivative_tables(desc)
     psi_out, op_out = [], []

@@ -273,3 +273,53 @@ def test_spectral_kernel_beats_g2_on_a_resolved_blob():
         psi, _ = oracle.solve(d, om[None])
         errs[kern] = np.max(np.abs(psi[0] - exact)) / np.max(np.abs(exact))
     assert errs["SPECT"] < 0.1 * errs["G2"], errs
+
+
+# ---------------------------------------------------------------------------
+# regular grids (N_c + 1 nodes per axis, padded to the smallest 2^p or 3*2^p >= 2 N_c + 1)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n", [(3, 6), (3, 7), (2, 12), (2, 10)])
+def test_direct_sum_regular_grid(dim, n):
+    # the aperiodic sum over the N_c + 1 nodes of a regular grid, written out directly
+    rng = np.random.default_rng(n + 7 * dim)
+    d = Desc(dim, (n, n + 2, n)[:dim], (-0.5,) * dim, (0.5, 0.7, 0.4)[:dim], ("U",) * dim, False,
+             rhs_scale=-1.3, sigma=0.09)
+    f = rng.normal(size=d.shape())
+    psi, _ = oracle.solve(d, f)
+    h = [d.h(a) for a in range(dim)]
+    nodes = tuple(d.nodes(a) for a in reversed(range(dim)))
+    pts = np.argwhere(np.ones(nodes, dtype=bool))
+    ref = np.zeros(len(pts))
+    for i, p in enumerate(pts):
+        r2 = 0.0
+        for k in range(dim):
+            r2 = r2 + ((p[k] - pts[:, k]) * h[dim - 1 - k]) ** 2
+        ref[i] = 1.3 * np.prod(h) * np.sum(green.green(dim, np.sqrt(r2), 0.09) * f.reshape(-1))
+    assert np.max(np.abs(psi[0].reshape(-1) - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_padded_length_rule():
+    from oracle import unbounded
+    for n, M in ((6, 16), (7, 16), (8, 24), (12, 32), (16, 48), (127, 256), (128, 384), (255, 512), (256, 768)):
+        d = Desc(1, (n,), (0.0,), (1.0,), ("U",), False, sigma=0.1)
+        assert unbounded.padded_length(d, 0) == M
+    d = Desc(1, (12,), (0.0,), (1.0,), ("U",), True, sigma=0.1)
+    assert unbounded.padded_length(d, 0) == 24
+
+
+@pytest.mark.parametrize("op,ncomp,dim", [("CURL", 3, 3), ("GRAD", 1, 2)])
+def test_sampled_points_match_full_oracle_regular(op, ncomp, dim):
+    from oracle import unbounded
+    n = (10, 7, 6)[:dim]
+    d = Desc(dim, n, (-0.5,) * dim, (0.5, 0.4, 0.3)[:dim], ("U",) * dim, False, op=op, ncomp=ncomp,
+             rhs_scale=-1.0, sigma=0.12)
+    rng = np.random.default_rng(19)
+    f = rng.normal(size=(ncomp,) + d.shape())
+    psi, opo = oracle.solve(d, f)
+    pts = [tuple(int(rng.integers(0, d.nodes(a))) for a in range(dim)) for _ in range(6)]
+    pts += [tuple(0 for _ in n), tuple(d.nodes(a) - 1 for a in range(dim))]
+    ps, os_ = unbounded.sample_points(d, f, pts)
+    for i, p in enumerate(pts):
+        idx = tuple(reversed(p))
+        np.testing.assert_allclose(ps[i], psi[(slice(None),) + idx], rtol=1e-11, atol=1e-13)
+        np.testing.assert_allclose(os_[i], opo[(slice(None),) + idx], rtol=1e-10, atol=1e-12)
