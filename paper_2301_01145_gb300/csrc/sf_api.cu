@@ -80,7 +80,21 @@ struct AxisHost {
 };
 
 // per-axis transform geometry and tables (Table 1; Sec. 2.4.3 wavenumbers)
-AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, bool cpath, int maxr = 16) {
+// smallest FFT length of the form 2^p or 3 * 2^p (>= 4) that is at least m
+static int pad_length(int m) {
+  m = std::max(m, 4);
+  int best = 0;
+  for (int base : {1, 3}) {
+    int v = base;
+    while (v < m) v *= 2;
+    if (!best || v < best) best = v;
+  }
+  return best;
+}
+
+// regular: an unbounded axis on the regular grid (N_c + 1 nodes, padded to pad_length(2 N_c + 1))
+AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, bool cpath, int maxr = 16,
+                    bool regular = false) {
   AxisHost a{};
   a.kind = kind;
   a.n = n;
@@ -88,7 +102,13 @@ AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, b
   a.h = a.Ldom / n;
   switch (kind) {
     case AK_P: a.nodes = n; a.u0 = 0; a.nu = n; a.L = n; a.k0 = 0; break;
-    case AK_U: a.nodes = n; a.u0 = 0; a.nu = n; a.L = 2 * n; a.k0 = 0; break;
+    case AK_U:
+      a.nodes = regular ? n + 1 : n;
+      a.u0 = 0;
+      a.nu = a.nodes;
+      a.L = regular ? pad_length(2 * n + 1) : 2 * n;
+      a.k0 = 0;
+      break;
     case AK_DR: a.nodes = n + 1; a.u0 = 1; a.nu = n - 1; a.L = 2 * n; a.k0 = 1; break;
     case AK_NR: a.nodes = n + 1; a.u0 = 0; a.nu = n + 1; a.L = 2 * n; a.k0 = 0; break;
     case AK_DS: a.nodes = n; a.u0 = 0; a.nu = n; a.L = 2 * n; a.k0 = 1; break;
@@ -163,7 +183,7 @@ AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, b
     }
     if (cpath) {
       const int M = L;  // points of the periodic (possibly doubled) axis
-      const double period = (kind == AK_U) ? 2.0 * a.Ldom : a.Ldom;
+      const double period = (kind == AK_U) ? L * a.h : a.Ldom;  // the padded axis for unbounded
       const int k = i;
       int ks = (k <= M / 2) ? k : k - M;
       const double kap2v = std::pow(2.0 * kPi * std::min(k, M - k) / period, 2);
@@ -758,7 +778,10 @@ static sf_status validate(const sf_plan_desc &d) {
     const int n = d.n[a];
     const int minn = (bc == SF_BC_DIRICHLET && d.grid == SF_GRID_REGULAR && !mixed) ? 3 : 2;
     if (n < minn) return fail(SF_ERR_ARG, "too few cells on an axis");
-    const int L = bc == SF_BC_PERIODIC ? n : (mixed ? 4 * n : 2 * n);
+    const int L = bc == SF_BC_PERIODIC ? n
+                  : mixed                  ? 4 * n
+                  : (bc == SF_BC_UNBOUNDED && d.grid == SF_GRID_REGULAR) ? pad_length(2 * n + 1)
+                                           : 2 * n;
     if (!valid_len(L)) return fail(SF_ERR_UNSUPPORTED, "FFT length " + std::to_string(L) + " is not 2^p or 3*2^p in [4, 2048]");
     if (bc == SF_BC_PERIODIC || bc == SF_BC_UNBOUNDED) ++ncp;
     else ++nreal;
@@ -766,7 +789,6 @@ static sf_status validate(const sf_plan_desc &d) {
   }
   if (ncp && nreal) return fail(SF_ERR_UNSUPPORTED, "mixing periodic/unbounded with Dirichlet/Neumann axes");
   if (nunb && nunb != d.dim) return fail(SF_ERR_UNSUPPORTED, "semi-unbounded domains");
-  if (nunb && d.grid != SF_GRID_STAGGERED) return fail(SF_ERR_UNSUPPORTED, "unbounded solves need the staggered grid");
   if (nunb && (d.green < SF_GREEN_G2 || d.green > SF_GREEN_SPECTRAL)) return fail(SF_ERR_ARG, "bad kernel");
   if (nunb && d.green == SF_GREEN_SPECTRAL && d.dim != 3) return fail(SF_ERR_UNSUPPORTED, "the spectral kernel is 3D only");
   if (nunb && d.green != SF_GREEN_SPECTRAL && !(d.green_sigma > 0.0)) return fail(SF_ERR_ARG, "green_sigma must be positive");
@@ -819,7 +841,7 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   for (int a = 0; a < 3; ++a) {
     if (a < d.dim) {
       ah[a] = build_axis(axis_kind(d.bc[a][0], d.grid, d.bc[a][1]), d.n[a], d.lo[a], d.hi[a], d.eig, a == 0, p.cpath,
-                         d.tune_radix);
+                         d.tune_radix, d.grid == SF_GRID_REGULAR);
       prodL *= ah[a].L;
       hd *= ah[a].h;
     } else {  // unused z axis of a 2D problem: a trivial periodic axis of one point
@@ -915,8 +937,8 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   sticky = (unsigned *)tmp;
   SF_CK(cudaMemset(sticky, 0, sizeof(unsigned)));
   if (p.green) {
-    p.gny = d.n[1] + 1;
-    p.gnz = d.dim == 3 ? d.n[2] + 1 : 1;
+    p.gny = ah[1].L / 2 + 1;  // octant of the padded axes
+    p.gnz = d.dim == 3 ? ah[2].L / 2 + 1 : 1;
     SF_TRY(build_green());
     (void)hd;
   }
@@ -984,13 +1006,14 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
 // the FP64 kernels, scaled by -rhs_scale h^d / prod(L) and rounded to T.
 template <typename T> sf_status PlanImpl<T>::build_green() {
   const int dim = d.dim;
-  const int nx = d.n[0], ny = d.n[1], nz = dim == 3 ? d.n[2] : 0;
+  // octant of the padded grid: L/2 + 1 offsets per axis (L = 2 N_c on staggered grids)
+  const int nx = P.ax[0].L / 2, ny = P.ax[1].L / 2, nz = dim == 3 ? P.ax[2].L / 2 : 0;
   double h[3] = {0, 0, 0};
   double hd = 1.0, prodL = 1.0;
   for (int a = 0; a < dim; ++a) {
     h[a] = (d.hi[a] - d.lo[a]) / d.n[a];
     hd *= h[a];
-    prodL *= 2.0 * d.n[a];
+    prodL *= (double)P.ax[a].L;
   }
   const size_t cnt = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
   DevMem<double> tmem;
@@ -1014,7 +1037,7 @@ template <typename T> sf_status PlanImpl<T>::build_green() {
   G.cpath = 0;
   for (int a = 0; a < 3; ++a) {
     if (a < dim) {
-      AxisHost ah = build_axis(AK_NR, d.n[a], 0.0, 1.0, SF_EIG_PS, a == 0, false);
+      AxisHost ah = build_axis(AK_NR, P.ax[a].L / 2, 0.0, 1.0, SF_EIG_PS, a == 0, false);
       SF_TRY(fill_axis<double>(G.ax[a], ah, tmem));
     } else {
       G.ax[a] = Axis<double>{};

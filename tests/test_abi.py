@@ -82,7 +82,7 @@ def test_status_strings_and_version(lib):
     (dict(bc=(("U", "N"), "D", "D")), -2),
     (dict(bc=(("D", "N"), "P", "P")), -2),  # a Dirichlet / Neumann axis mixed with periodic axes
     (dict(rhs_scale=0.0), -1),
-    (dict(bc="UUU", grid="regular"), -2),
+    (dict(bc="UUU", grid="regular", n=(1100, 16, 16)), -2),  # regular unbounded: pad 2n+1 > 2048
     (dict(bc="UUU", sigma=0.0), -1),
     (dict(op="CURL", ncomp=1), -1),
     (dict(op="GRAD", bc="DDD"), -2),

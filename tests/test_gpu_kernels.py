@@ -87,3 +87,62 @@ def test_spectral_kernel_fast_path_samples():
     ref_psi, ref_u = unbounded.sample_points(d, f, pts)
     check_samples(to_np(psi), to_np(u), ref_psi, ref_u, pts, 1e-5)
     plan.close()
+
+
+# ---------------------------------------------------------------------------
+# unbounded solves on regular grids (N_c + 1 nodes, padded to 2^p or 3*2^p >= 2 N_c + 1)
+# ---------------------------------------------------------------------------
+def regular_plan(dim, n, op="NONE", ncomp=1, prec="f32", kernel="G2", generic=False):
+    import paper_2301_01145_gb300 as sf
+    lo, hi = (-0.5,) * dim, (0.5, 0.75, 0.6)[:dim]
+    sigma = 2.0 / max(n)
+    plan = sf.Plan(dim, n, lo, hi, "U" * dim, grid="regular", op=op, ncomp=ncomp, sigma=sigma, rhs_scale=-1.0,
+                   prec=prec, kernel=kernel, generic=generic)
+    d = Desc(dim, tuple(n), lo, hi, ("U",) * dim, False, op=op, ncomp=ncomp, rhs_scale=-1.0, sigma=sigma,
+             kernel=kernel)
+    return plan, d
+
+
+@pytest.mark.parametrize("n", [(15, 11, 9), (16, 8, 12)])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_regular_grid_unbounded_3d_curl(n, prec):
+    plan, d = regular_plan(3, n, "CURL", 3, prec)
+    f = np.random.default_rng(21).normal(size=(3,) + d.shape())
+    psi, u = plan(to_dev(f, prec))
+    plan.sync()
+    rp, ru = oracle.solve(d, f)
+    for c in range(3):
+        assert rel_l2(to_np(psi)[c], rp[c]) <= TOL[prec]
+        assert rel_l2(to_np(u)[c], ru[c]) <= TOL[prec]
+    plan.close()
+
+
+@pytest.mark.parametrize("kernel", ["G2", "G6"])
+def test_regular_grid_unbounded_2d(kernel):
+    plan, d = regular_plan(2, (47, 20), "GRAD", 1, "f32", kernel)
+    f = np.random.default_rng(22).normal(size=(1,) + d.shape())
+    psi, g = plan(to_dev(f, "f32"))
+    plan.sync()
+    rp, rg = oracle.solve(d, f)
+    assert rel_l2(to_np(psi)[0], rp[0]) <= TOL["f32"]
+    for c in range(2):
+        assert rel_l2(to_np(g)[c], rg[c]) <= TOL["f32"]
+    plan.close()
+
+
+@pytest.mark.parametrize("n", [127, 255])
+def test_regular_grid_unbounded_fast_path_samples(n):
+    # 128 / 256 nodes per axis padded to 256 / 512: the register fast path, against point samples
+    from oracle import unbounded
+    from tests.test_gpu_fullsize import check_samples
+    plan, d = regular_plan(3, (n,) * 3, "CURL", 3, "f32")
+    rng = np.random.default_rng(n)
+    f = workloads.lowpass_noise(d.shape(), 40 + n)
+    f = np.stack([f, np.roll(f, 7, 0), np.roll(f, 5, 2)])
+    psi, u = plan(to_dev(f, "f32"))
+    plan.sync()
+    m = n + 1
+    pts = [tuple(int(v) for v in rng.integers(0, m, size=3)) for _ in range(10)] + [(0, 0, 0), (n, n, n)]
+    ref_psi, ref_u = unbounded.sample_points(d, f, pts)
+    check_samples(to_np(psi), to_np(u), ref_psi, ref_u, pts, 1e-5)
+    plan.close()
