@@ -187,8 +187,8 @@ template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfo
 // dependency chains overlap (wsm: M consecutive buffers of E*33 elements).
 // Twiddles come from the lane-contiguous table twf of the axis:
 //   twf[k1 * 32 + t]          = W_L^{t k1}       (step 1, one 256-byte row per k1)
-//   twf[L + j * G + q]        = W_L^{q j E}      (step 3, E-point stage; the kernels use the
-//                                                 equal constants W_32^{q j} of w_stage2)
+//   twf[L + j * G + q]        = W_L^{q j E}      (step 3, E-point stage; with G = 2 the kernels
+//                                                 use the equal constants W_32^{q j} of w_stage2)
 //   twf[L + 32 + mm - 1 + r]  = W_{2 mm}^r       (step 3, lane stage mm)
 template <typename T, int E, bool HALFIN, int M>
 __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const cx<T> *__restrict__ tw) {
@@ -232,7 +232,8 @@ __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
   for (int m = 0; m < M; ++m) dftR<E, false>(v[m]);
 #pragma unroll
   for (int j = 1; j < E; ++j) {
-    const V w = w_stage2<G, V>(q, j);
+    // two lanes per group: constants and one select; more lanes: one table load
+    const V w = G == 2 ? w_stage2<G, V>(q, j) : __ldg(&tw[L + j * G + q]);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[m][j] = cmul(v[m][j], w);
   }
@@ -277,7 +278,7 @@ __device__ __forceinline__ void wfft_inv_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
   }
 #pragma unroll
   for (int j = 1; j < E; ++j) {
-    const V w = w_stage2<G, V>(q, j);
+    const V w = G == 2 ? w_stage2<G, V>(q, j) : __ldg(&tw[L + j * G + q]);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[m][j] = cmulc(v[m][j], w);
   }
@@ -346,9 +347,9 @@ template <int E, int M> __host__ __device__ constexpr int fast_wsm_elems() { ret
 #define SF_YF_ROWS 16  // z rows per YF tile
 #define SF_ZS_ROWS 8   // ky rows per ZS tile (one per warp)
 #define SF_YI_COLS 16  // z columns per YI tile
-#ifndef SF_YI_SPLIT_ROWS
-#define SF_YI_SPLIT_ROWS 32  // z rows per YI tile of the split curl (4 per warp)
-#endif
+// z rows per YI tile of the split curl: 4 per warp on 512-point axes, 2 on
+// 256-point axes (whose smaller slabs would otherwise leave CTAs idle)
+__host__ __device__ constexpr int fast_yi_split_rows(int L) { return L == 512 ? 32 : 16; }
 template <typename T> __host__ __device__ inline int fast_tiles_yf(const Prob<T> &Q, int nkx) {
   return Q.nin * nkx * cdiv(Q.nuz, SF_YF_ROWS);
 }
@@ -359,7 +360,7 @@ template <typename T> __host__ __device__ inline bool fast_split_curl(const Prob
 }
 __host__ __device__ inline int fast_tiles_zs(int nkx, int L) { return nkx * (L / SF_ZS_ROWS); }
 template <typename T> __host__ __device__ inline int fast_tiles_yi(const Prob<T> &Q, int nkx) {
-  return Q.nout * nkx * cdiv(Q.nuz, fast_split_curl(Q) ? SF_YI_SPLIT_ROWS : SF_YI_COLS);
+  return Q.nout * nkx * cdiv(Q.nuz, fast_split_curl(Q) ? fast_yi_split_rows(Q.ax[1].L) : SF_YI_COLS);
 }
 
 // ---------------------------------------------------------------------------
@@ -893,7 +894,7 @@ __device__ __forceinline__ void fast_zs_split(const Prob<float> &P, const FastGe
 // YI of the split path: whole ky rows of the transposed I2 [f][kxl][z][ky],
 // loaded directly in the k layout of the inverse transform (for every
 // register j the 32 lanes cover two runs of 16 consecutive ky), the curl
-// outputs combined in y-spectral space on the way in; SF_YI_SPLIT_ROWS / 8 z rows per warp.
+// outputs combined in y-spectral space on the way in; fast_yi_split_rows(L) / 8 z rows per warp.
 template <int E, bool PAD>
 __device__ __forceinline__ void fast_yi_rows(const Prob<float> &P, const FastGeo &g, const FPass &ps, int tile,
                                              cx<float> *wsm) {
@@ -901,9 +902,10 @@ __device__ __forceinline__ void fast_yi_rows(const Prob<float> &P, const FastGeo
   constexpr int L = 32 * E;
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   const int nuy = P.nuy, nuz = P.nuz, nsx = P.nsx;
-  constexpr int RPW = SF_YI_SPLIT_ROWS / (SF_FAST_THREADS / 32);  // rows per warp
-  static_assert(RPW >= 1 && RPW * (SF_FAST_THREADS / 32) == SF_YI_SPLIT_ROWS, "rows per YI tile");
-  const int tz = cdiv(nuz, SF_YI_SPLIT_ROWS);
+  constexpr int ROWS = fast_yi_split_rows(L);
+  constexpr int RPW = ROWS / (SF_FAST_THREADS / 32);  // rows per warp
+  static_assert(RPW >= 1 && RPW * (SF_FAST_THREADS / 32) == ROWS, "rows per YI tile");
+  const int tz = cdiv(nuz, ROWS);
   const int iz = tile % tz;
   const int rest = tile / tz;
   const int kxl = rest % ps.nkx;
@@ -920,7 +922,7 @@ __device__ __forceinline__ void fast_yi_rows(const Prob<float> &P, const FastGeo
   const float ky1 = __ldg(&P.ax[1].kap[1]);
 #pragma unroll 1
   for (int h = 0; h < RPW; ++h) {
-    const int z = iz * SF_YI_SPLIT_ROWS + RPW * warp + h;
+    const int z = iz * ROWS + RPW * warp + h;
     if (z >= nuz) break;  // uniform over the warp
     const V *ra = I2 + (((size_t)fa * g.S + kxl) * nuz + z) * L;
     const V *rb = I2 + (((size_t)fb * g.S + kxl) * nuz + z) * L;
