@@ -42,7 +42,8 @@ typedef enum {
   SF_ERR_CUDA = -3,        /* a CUDA runtime call failed (detail in sf_last_error)   */
   SF_ERR_OOM = -4,         /* device allocation failed                               */
   SF_ERR_STATE = -5,       /* call out of order (e.g. solve without a source)        */
-  SF_ERR_TIMEOUT = -6      /* a bounded device-side wait in the scheduler gave up    */
+  SF_ERR_TIMEOUT = -6,     /* a bounded device-side wait in the scheduler gave up    */
+  SF_ERR_CORRUPT = -7      /* SF_FLAG_DEBUG_CHECKS: a workspace guard band was overwritten */
 } sf_status;
 
 /* Boundary type of an axis (Sec. 2.4.1 solver types; Sec. 2.5 bounded, 2.6 unbounded). */
@@ -74,6 +75,13 @@ typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
 /* Plan flags (sf_plan_desc.flags). */
 #define SF_FLAG_UNFUSED 1u /* one kernel launch per pass instead of one persistent launch */
 #define SF_FLAG_GENERIC 2u /* always use the general shared-memory FFT engine (no register fast path) */
+/* Debug checks: every device buffer of the plan (workspace and tables) is
+ * allocated with a 4 KB guard band on each side, filled with the byte 0xA5;
+ * sf_sync scans the bands after the stream drains and returns SF_ERR_CORRUPT if
+ * any byte changed (an out-of-range write by the library).  The slack between a
+ * buffer's end and the next 256-byte boundary is not guarded.  Costs one 4 KB
+ * device-to-host copy per band on every sf_sync. */
+#define SF_FLAG_DEBUG_CHECKS 4u
 
 /*
  * Problem description (Sec. 2.4 solver options, Sec. 2.5.1 Table 1).
@@ -81,9 +89,11 @@ typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
  *   n[a]       cell count N_c per axis a = x, y, z (n[2] ignored in 2D).  Every
  *              FFT length used (N_c for periodic, 4 N_c for an axis with a
  *              Dirichlet and a Neumann face, 2 N_c otherwise) must be of the
- *              form 2^p or 3*2^p and lie in [4, 2048]; N_c >= 2 (>= 3 for
- *              regular Dirichlet on both faces).
- *   lo, hi     domain bounds X_l, X_u per axis.
+ *              form 2^p or 3*2^p and lie in [4, 2048]; 2 <= N_c <= 2048
+ *              (N_c >= 3 for regular Dirichlet on both faces).  An unbounded
+ *              axis on the regular grid (N_c + 1 nodes) is padded to the
+ *              smallest 2^p or 3*2^p >= 2 N_c + 1.
+ *   lo, hi     domain bounds X_l < X_u per axis (finite, finite difference).
  *   bc[a][s]   boundary type of axis a on its lower (s = 0) and upper (s = 1)
  *              face.  The faces of an axis agree, or one is Dirichlet and the
  *              other Neumann: that axis is then transformed in the quarter-wave
@@ -94,17 +104,18 @@ typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
  *              Dirichlet face node is filled from the face data and a Neumann
  *              face node is solved for.  Either every axis is
  *              periodic/unbounded, or every axis is Dirichlet/Neumann.
- *   grid       REGULAR or STAGGERED.  Unbounded axes need STAGGERED.
+ *   grid       REGULAR (N_c + 1 nodes per axis) or STAGGERED (N_c cell centres).
  *   eig        PS or FD2 (bounded axes; ignored when unbounded).
  *   op         spectral operator on psi; needs periodic or unbounded axes.
  *              GRAD: ncomp 1 -> dim outputs.  DIV: ncomp = dim -> 1 output.
  *              CURL: 3D ncomp 3 -> 3 outputs; 2D ncomp 1 -> 2 outputs.
  *              NABLA: ncomp -> ncomp outputs.
- *   green      kernel for unbounded solves; green_sigma its Gaussian width.
+ *   green      kernel for unbounded solves; green_sigma its Gaussian width
+ *              (positive and finite; ignored by SF_GREEN_SPECTRAL).
  *   ncomp      number of field components solved together (1..3).
  *   prec       arithmetic of the solve (tables are always built in FP64).
  *   rhs_scale  the plan solves lap(psi) = rhs_scale * f.
- *   flags      SF_FLAG_* bits, 0 by default.
+ *   flags      SF_FLAG_* bits, 0 by default; any other bit is SF_ERR_ARG.
  */
 typedef struct {
   int32_t dim;
@@ -289,6 +300,18 @@ sf_status sf_solve_static(const sf_plan_desc *d, const void *dev_f, void *dev_ps
  * SF_ERR_TIMEOUT when the failure was detected as designed (SF_OK would mean
  * the wait did not give up).  No work is done on user data. */
 sf_status sf_selftest_timeout(int timeout_ms, void *cuda_stream);
+
+/* Test hooks for failure handling (the paper has no counterpart).
+ * sf_debug_fail_alloc(after): every device allocation the library makes from
+ *   now on fails with SF_ERR_OOM once `after` more allocations have succeeded
+ *   (after < 0 turns the injection off).  Plan creation then returns SF_ERR_OOM
+ *   and releases what it had allocated.  Process-wide; not thread-safe.
+ * sf_debug_corrupt_guard(p): overwrites one byte of the first guard band of a
+ *   plan created with SF_FLAG_DEBUG_CHECKS (a host-issued cudaMemset into the
+ *   plan's own allocation, so no kernel writes out of range); the next sf_sync
+ *   must report SF_ERR_CORRUPT.  SF_ERR_STATE for a plan without debug checks. */
+sf_status sf_debug_fail_alloc(int after);
+sf_status sf_debug_corrupt_guard(sf_plan p);
 
 /* Measured FP32 FMA throughput of the current device in TFLOP/s (one FMA =
  * 2 flop): 8 independent FMA chains per thread on 8 CTAs x 256 threads per

@@ -33,12 +33,13 @@ class Plan:
                  grid: str = "staggered", eig: str = "PS", op: str = "NONE", sigma: float = 0.0, ncomp: int = 1,
                  prec: str = "f32", rhs_scale: float = 1.0, fused: bool = True, generic: bool = False, stream=None,
                  tune_radix: int = 0, tune_tile: int = 0, tune_slab: int = 0, tune_lag: int = 0,
-                 kernel: str = "G2"):
+                 kernel: str = "G2", debug_checks: bool = False):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2301_01145_gb300 needs a CUDA device")
         bc = list(bc) if isinstance(bc, str) else list(bc)
-        flags = (0 if fused else _lib.FLAG_UNFUSED) | (_lib.FLAG_GENERIC if generic else 0)
+        flags = (0 if fused else _lib.FLAG_UNFUSED) | (_lib.FLAG_GENERIC if generic else 0) | \
+            (_lib.FLAG_DEBUG_CHECKS if debug_checks else 0)
         self.desc = _lib.make_desc(dim, n, lo, hi, bc, grid, eig, op, sigma, ncomp, prec, rhs_scale, flags,
                                    tune_radix, tune_tile, tune_slab, tune_lag, kernel)
         self.dim, self.ncomp, self.op = dim, ncomp, op

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libsailfish_gb300.so")
 
 SF_OK = 0
 STATUS = {0: "SF_OK", -1: "SF_ERR_ARG", -2: "SF_ERR_UNSUPPORTED", -3: "SF_ERR_CUDA", -4: "SF_ERR_OOM",
-          -5: "SF_ERR_STATE", -6: "SF_ERR_TIMEOUT"}
+          -5: "SF_ERR_STATE", -6: "SF_ERR_TIMEOUT", -7: "SF_ERR_CORRUPT"}
 
 BC = {"P": 0, "D": 1, "N": 2, "U": 3}
 GRID = {"regular": 0, "staggered": 1}
@@ -27,6 +27,7 @@ EIG = {"PS": 0, "FD2": 1}
 PREC = {"f32": 0, "f64": 1}
 FLAG_UNFUSED = 1
 FLAG_GENERIC = 2
+FLAG_DEBUG_CHECKS = 4
 
 
 class SolverError(RuntimeError):
@@ -80,6 +81,8 @@ SIGNATURES = {
     "sf_solve_static": (c_int, [POINTER(sf_plan_desc), c_void_p, c_void_p, c_void_p]),
     "sf_plan_stats": (c_int, [c_void_p, POINTER(c_double)]),
     "sf_plan_timing": (c_int, [c_void_p, c_int]),
+    "sf_debug_fail_alloc": (c_int, [c_int]),
+    "sf_debug_corrupt_guard": (c_int, [c_void_p]),
     "sf_solve_host_many": (c_int, [c_void_p, c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p)]),
     "sf_probe_fp32_fma": (c_int, [POINTER(c_double), c_void_p]),
     "sf_plan_kernel_ms": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), POINTER(c_int)]),
@@ -266,6 +269,14 @@ def sf_probe_fp32_fma(stream=None) -> float:
     out = c_double(0.0)
     _check(load().sf_probe_fp32_fma(ctypes.byref(out), _stream(stream)), "sf_probe_fp32_fma")
     return out.value
+
+
+def sf_debug_fail_alloc(after: int):
+    _check(load().sf_debug_fail_alloc(int(after)), "sf_debug_fail_alloc")
+
+
+def sf_debug_corrupt_guard(plan):
+    _check(load().sf_debug_corrupt_guard(plan), "sf_debug_corrupt_guard")
 
 
 def sf_plan_destroy(plan):

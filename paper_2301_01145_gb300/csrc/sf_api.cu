@@ -10,6 +10,8 @@
 
 #include <atomic>
 
+#include <nvtx3/nvToolsExt.h>  // header-only NVTX v3: named ranges for profilers, a no-op without one
+
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -195,22 +197,45 @@ AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, b
   return a;
 }
 
+// allocation failure injection (sf_debug_fail_alloc): remaining successes, < 0 = off
+static std::atomic<long long> g_alloc_budget{-1};
+
+#define SF_GUARD_BYTES 4096
+#define SF_GUARD_BYTE 0xA5
+
 template <typename T> struct DevMem {
   std::vector<void *> ptrs;
+  bool guarded = false;  // SF_FLAG_DEBUG_CHECKS: guard bands around every allocation
+  std::vector<std::pair<unsigned char *, size_t>> guards;  // (start, bytes) of each band
   ~DevMem() {
     for (void *p : ptrs) cudaFree(p);
   }
   sf_status alloc(void **out, size_t bytes) {
     *out = nullptr;
     if (bytes == 0) return SF_OK;
-    cudaError_t e = cudaMalloc(out, bytes);
+    long long b = g_alloc_budget.load();
+    while (b >= 0) {
+      if (b == 0) return fail(SF_ERR_OOM, "device allocation refused by the failure injection hook");
+      if (g_alloc_budget.compare_exchange_weak(b, b - 1)) break;
+    }
+    const size_t pad = guarded ? SF_GUARD_BYTES : 0;
+    const size_t body = (bytes + 255) / 256 * 256;
+    void *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, body + 2 * pad);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      *out = nullptr;
       return fail(e == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA,
                   std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
-    ptrs.push_back(*out);
+    ptrs.push_back(base);
+    unsigned char *b8 = static_cast<unsigned char *>(base);
+    if (pad) {
+      SF_CK(cudaMemset(b8, SF_GUARD_BYTE, pad));
+      SF_CK(cudaMemset(b8 + pad + body, SF_GUARD_BYTE, pad));
+      guards.push_back({b8, pad});
+      guards.push_back({b8 + pad + body, pad});
+    }
+    *out = b8 + pad;
     return SF_OK;
   }
   template <typename U> sf_status upload(U **out, const std::vector<double> &v, bool complex_pairs) {
@@ -515,6 +540,7 @@ struct sf_plan_s {
   virtual sf_status set_face(int axis, int side, const void *p) = 0;
   virtual sf_status host_solve(const void *hf, void *hpsi, void *hop) = 0;
   virtual sf_status host_solve_many(int n, const void *const *hf, void *const *hpsi, void *const *hop) = 0;
+  virtual sf_status corrupt_guard() { return fail(SF_ERR_STATE, "not available on a batch"); }
   virtual ExecCtl *exec_ctl() = 0;
   const void *src = nullptr;
   bool solved = false;
@@ -600,6 +626,27 @@ template <typename T> struct PlanImpl : sf_plan_s {
       SF_CK(cudaMemset(sticky, 0, sizeof(unsigned)));
       return fail(SF_ERR_TIMEOUT, "a scheduler wait exceeded its bound; results are invalid");
     }
+    return check_guards();
+  }
+
+  // SF_FLAG_DEBUG_CHECKS: every guard band must still hold SF_GUARD_BYTE
+  sf_status check_guards() {
+    if (!mem.guarded) return SF_OK;
+    std::vector<unsigned char> h(SF_GUARD_BYTES);
+    for (size_t i = 0; i < mem.guards.size(); ++i) {
+      SF_CK(cudaMemcpy(h.data(), mem.guards[i].first, mem.guards[i].second, cudaMemcpyDeviceToHost));
+      for (size_t j = 0; j < mem.guards[i].second; ++j)
+        if (h[j] != SF_GUARD_BYTE)
+          return fail(SF_ERR_CORRUPT, "guard band " + std::to_string(i) + " of the plan's workspace overwritten at byte " +
+                                          std::to_string(j));
+    }
+    return SF_OK;
+  }
+
+  sf_status corrupt_guard() override {
+    if (!mem.guarded || mem.guards.empty()) return fail(SF_ERR_STATE, "plan has no guard bands (SF_FLAG_DEBUG_CHECKS)");
+    SF_CK(cudaStreamSynchronize(stream));
+    SF_CK(cudaMemset(mem.guards[0].first + 7, 0x00, 1));
     return SF_OK;
   }
 
@@ -759,6 +806,7 @@ static int op_outputs(int op, int dim, int ncomp) {
 
 static sf_status validate(const sf_plan_desc &d) {
   if (d.dim != 2 && d.dim != 3) return fail(SF_ERR_ARG, "dim must be 2 or 3");
+  if (d.flags & ~(SF_FLAG_UNFUSED | SF_FLAG_GENERIC | SF_FLAG_DEBUG_CHECKS)) return fail(SF_ERR_ARG, "unknown flag bits");
   if (d.prec != SF_F32 && d.prec != SF_F64) return fail(SF_ERR_ARG, "prec must be SF_F32 or SF_F64");
   if (d.grid != SF_GRID_REGULAR && d.grid != SF_GRID_STAGGERED) return fail(SF_ERR_ARG, "bad grid type");
   if (d.ncomp < 1 || d.ncomp > 3) return fail(SF_ERR_ARG, "ncomp must be 1..3");
@@ -774,10 +822,12 @@ static sf_status validate(const sf_plan_desc &d) {
     const bool mixed = d.bc[a][0] != d.bc[a][1];
     if (mixed && axis_kind(bc, d.grid, d.bc[a][1]) < 0)
       return fail(SF_ERR_UNSUPPORTED, "unequal faces on one axis: only a Dirichlet / Neumann pair is supported");
-    if (!(d.hi[a] > d.lo[a])) return fail(SF_ERR_ARG, "domain bounds need hi > lo");
+    if (!(d.hi[a] > d.lo[a]) || !std::isfinite(d.hi[a] - d.lo[a]))
+      return fail(SF_ERR_ARG, "domain bounds need finite lo < hi");
     const int n = d.n[a];
     const int minn = (bc == SF_BC_DIRICHLET && d.grid == SF_GRID_REGULAR && !mixed) ? 3 : 2;
     if (n < minn) return fail(SF_ERR_ARG, "too few cells on an axis");
+    if (n > 2048) return fail(SF_ERR_UNSUPPORTED, "more than 2048 cells on an axis");  // before any 2n / 4n
     const int L = bc == SF_BC_PERIODIC ? n
                   : mixed                  ? 4 * n
                   : (bc == SF_BC_UNBOUNDED && d.grid == SF_GRID_REGULAR) ? pad_length(2 * n + 1)
@@ -791,7 +841,8 @@ static sf_status validate(const sf_plan_desc &d) {
   if (nunb && nunb != d.dim) return fail(SF_ERR_UNSUPPORTED, "semi-unbounded domains");
   if (nunb && (d.green < SF_GREEN_G2 || d.green > SF_GREEN_SPECTRAL)) return fail(SF_ERR_ARG, "bad kernel");
   if (nunb && d.green == SF_GREEN_SPECTRAL && d.dim != 3) return fail(SF_ERR_UNSUPPORTED, "the spectral kernel is 3D only");
-  if (nunb && d.green != SF_GREEN_SPECTRAL && !(d.green_sigma > 0.0)) return fail(SF_ERR_ARG, "green_sigma must be positive");
+  if (nunb && d.green != SF_GREEN_SPECTRAL && !(d.green_sigma > 0.0 && std::isfinite(d.green_sigma)))
+    return fail(SF_ERR_ARG, "green_sigma must be positive and finite");
   if (ncp && d.bc[0][0] == SF_BC_PERIODIC && (d.n[0] % 2)) return fail(SF_ERR_UNSUPPORTED, "odd periodic x length");
   if (d.op != SF_OP_NONE) {
     if (nreal) return fail(SF_ERR_UNSUPPORTED, "spectral operators on Dirichlet/Neumann axes");
@@ -826,6 +877,7 @@ template <typename T> static void derive_extents(Prob<T> &P) {
 template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cudaStream_t st) {
   d = desc;
   stream = st;
+  mem.guarded = (d.flags & SF_FLAG_DEBUG_CHECKS) != 0;
   SF_TRY(set_kernel_attrs<T>());
   Prob<T> &p = P;
   p.dim = d.dim;
@@ -1223,6 +1275,12 @@ template <typename T> struct BatchImpl : sf_plan_s {
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+// NVTX range around one C-ABI call (shown by nsys / ncu range filters)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 extern "C" {
 
 const char *sf_version(void) { return "sailfish-gb300 0.1"; }
@@ -1236,6 +1294,7 @@ const char *sf_status_string(sf_status s) {
     case SF_ERR_OOM: return "SF_ERR_OOM";
     case SF_ERR_STATE: return "SF_ERR_STATE";
     case SF_ERR_TIMEOUT: return "SF_ERR_TIMEOUT";
+    case SF_ERR_CORRUPT: return "SF_ERR_CORRUPT";
   }
   return "unknown status";
 }
@@ -1243,6 +1302,7 @@ const char *sf_status_string(sf_status s) {
 const char *sf_last_error(void) { return g_err.c_str(); }
 
 sf_status sf_plan_create(sf_plan *out, const sf_plan_desc *d, void *cuda_stream) {
+  NvtxRange range_("sf_plan_create");
   if (!out || !d) return fail(SF_ERR_ARG, "null argument");
   *out = nullptr;
   SF_TRY(validate(*d));
@@ -1294,6 +1354,7 @@ sf_status sf_set_boundary(sf_plan p, int axis, int side, const void *dev_face) {
 }
 
 sf_status sf_solve(sf_plan p) {
+  NvtxRange range_("sf_solve");
   if (!p) return fail(SF_ERR_ARG, "null plan");
   if (p->is_batch) return fail(SF_ERR_STATE, "use sf_batch_solve on a batch");
   if (!p->src) return fail(SF_ERR_STATE, "no source set");
@@ -1303,6 +1364,7 @@ sf_status sf_solve(sf_plan p) {
 }
 
 sf_status sf_get_output(sf_plan p, void *dev_psi, void *dev_op_out) {
+  NvtxRange range_("sf_get_output");
   if (!p) return fail(SF_ERR_ARG, "null plan");
   if (p->is_batch) return fail(SF_ERR_STATE, "use sf_batch_solve on a batch");
   if (!p->solved) return fail(SF_ERR_STATE, "sf_get_output before sf_solve");
@@ -1312,6 +1374,7 @@ sf_status sf_get_output(sf_plan p, void *dev_psi, void *dev_op_out) {
 }
 
 sf_status sf_execute(sf_plan p, const void *dev_f, void *dev_psi, void *dev_op_out) {
+  NvtxRange range_("sf_execute");
   if (!p) return fail(SF_ERR_ARG, "null plan");
   if (p->is_batch) return fail(SF_ERR_STATE, "use sf_batch_solve on a batch");
   if (!dev_f || !dev_psi) return fail(SF_ERR_ARG, "null buffer");
@@ -1323,6 +1386,7 @@ sf_status sf_execute(sf_plan p, const void *dev_f, void *dev_psi, void *dev_op_o
 }
 
 sf_status sf_solve_host(sf_plan p, const void *host_f, void *host_psi, void *host_op_out) {
+  NvtxRange range_("sf_solve_host");
   if (!p) return fail(SF_ERR_ARG, "null plan");
   if (!host_f || !host_psi) return fail(SF_ERR_ARG, "null buffer");
   if (p->d.op != SF_OP_NONE && !host_op_out) return fail(SF_ERR_ARG, "plan has an operator: op output needed");
@@ -1331,6 +1395,7 @@ sf_status sf_solve_host(sf_plan p, const void *host_f, void *host_psi, void *hos
 
 sf_status sf_solve_host_many(sf_plan p, int n, const void *const *host_f, void *const *host_psi,
                              void *const *host_op_out) {
+  NvtxRange range_("sf_solve_host_many");
   if (!p) return fail(SF_ERR_ARG, "null plan");
   if (n < 0) return fail(SF_ERR_ARG, "n must be >= 0");
   if (n == 0) return SF_OK;
@@ -1345,12 +1410,14 @@ sf_status sf_solve_host_many(sf_plan p, int n, const void *const *host_f, void *
 }
 
 sf_status sf_solve_adjoint(sf_plan p, const void *g_psi, const void *g_op, void *g_f) {
+  NvtxRange range_("sf_solve_adjoint");
   if (!p) return fail(SF_ERR_ARG, "null plan");
   if (!g_f) return fail(SF_ERR_ARG, "null output");
   return p->adjoint(g_psi, g_op, g_f);
 }
 
 sf_status sf_batch_create(sf_plan *batch, const sf_plan *plans, int n, void *cuda_stream) {
+  NvtxRange range_("sf_batch_create");
   if (!batch || !plans || n < 1) return fail(SF_ERR_ARG, "bad batch arguments");
   *batch = nullptr;
   const int prec = plans[0] ? plans[0]->d.prec : -1;
@@ -1379,6 +1446,7 @@ sf_status sf_batch_create(sf_plan *batch, const sf_plan *plans, int n, void *cud
 }
 
 sf_status sf_batch_solve(sf_plan batch, const void *const *f, void *const *psi, void *const *op) {
+  NvtxRange range_("sf_batch_solve");
   if (!batch || !batch->is_batch) return fail(SF_ERR_ARG, "not a batch");
   if (!f || !psi) return fail(SF_ERR_ARG, "null buffer table");
   if (batch->d.prec == SF_F32) return static_cast<BatchImpl<float> *>(batch)->run(f, psi, op);
@@ -1386,6 +1454,7 @@ sf_status sf_batch_solve(sf_plan batch, const void *const *f, void *const *psi, 
 }
 
 sf_status sf_sync(sf_plan p) {
+  NvtxRange range_("sf_sync");
   if (!p) return fail(SF_ERR_ARG, "null plan");
   return p->sync();
 }
@@ -1440,6 +1509,16 @@ sf_status sf_selftest_timeout(int timeout_ms, void *cuda_stream) {
   SF_CK(cudaMemcpy(&s, sticky, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (s) return fail(SF_ERR_TIMEOUT, "scheduler wait gave up as designed");
   return SF_OK;
+}
+
+sf_status sf_debug_fail_alloc(int after) {
+  g_alloc_budget.store(after < 0 ? -1 : (long long)after);
+  return SF_OK;
+}
+
+sf_status sf_debug_corrupt_guard(sf_plan p) {
+  if (!p) return fail(SF_ERR_ARG, "null plan");
+  return p->corrupt_guard();
 }
 
 sf_status sf_plan_stats(sf_plan p, double out[24]) {

@@ -7,6 +7,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -99,6 +100,13 @@ def test_status_strings_and_version(lib):
     (dict(n=(17, 16, 16)), -2),        # odd periodic x length
     (dict(dim=2, bc="UU", kernel="SPECT"), -2),  # the spectral kernel is 3D only
     (dict(bc="UUU", sigma=0.0, kernel="G6"), -1),  # Gaussian kernels need sigma > 0
+    (dict(bc="UUU", sigma=float("inf")), -1),    # ... and finite
+    (dict(hi=(float("inf"), 1, 1)), -1),         # infinite extent
+    (dict(lo=(-1.7e308, 0, 0), hi=(1.7e308, 1, 1)), -1),  # extent overflows
+    (dict(lo=(float("nan"), 0, 0)), -1),
+    (dict(n=(1 << 30, 16, 16), bc="UUU", grid="regular"), -2),  # huge n rejected before 2n + 1 is formed
+    (dict(n=(1 << 29, 16, 16), bc=(("D", "N"), "D", "D")), -2),  # ... and before 4n
+    (dict(flags=8), -1),                         # unknown flag bit
 ])
 def test_descriptor_validation_without_gpu(lib, mutate, expect):
     from paper_2301_01145_gb300 import _lib
@@ -119,3 +127,45 @@ def test_null_arguments(lib):
     assert lib.sf_plan_create(None, None, None) == -1
     assert lib.sf_solve(None) == -1
     assert lib.sf_plan_destroy(None) == 0
+
+
+def test_descriptor_fuzz_without_gpu(lib):
+    # seeded random descriptors, most of them invalid: every call returns a defined
+    # status and no handle (validation rejects, or the valid ones fail at the first
+    # CUDA call on a host without a GPU); none crashes or hangs the host
+    from paper_2301_01145_gb300 import _lib
+    rng = np.random.default_rng(2301)
+    specials = [0.0, -1.0, 1.0, 1e-300, 1e300, float("inf"), float("-inf"), float("nan")]
+    nvals = [-5, 0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 31, 32, 64, 127, 128, 256, 512, 1024, 1025, 2048, 4096,
+             1 << 29, (1 << 31) - 1, -(1 << 31)]
+    seen = set()
+    for _ in range(3000):
+        d = _lib.sf_plan_desc()
+        d.dim = int(rng.choice([-1, 0, 1, 2, 3, 4, 3, 3, 2]))
+        for a in range(3):
+            d.n[a] = int(rng.choice(nvals))
+            d.lo[a] = float(rng.choice(specials)) if rng.random() < 0.2 else 0.0
+            d.hi[a] = float(rng.choice(specials)) if rng.random() < 0.2 else 1.0
+            f0 = int(rng.integers(-1, 6))
+            d.bc[a][0] = f0
+            d.bc[a][1] = f0 if rng.random() < 0.7 else int(rng.integers(-1, 6))
+        d.grid = int(rng.integers(-1, 3))
+        d.eig = int(rng.integers(-1, 3))
+        d.op = int(rng.integers(-1, 7))
+        d.green = int(rng.integers(-1, 8))
+        d.green_sigma = float(rng.choice(specials + [0.05]))
+        d.ncomp = int(rng.integers(-1, 5))
+        d.prec = int(rng.integers(-1, 3))
+        d.rhs_scale = float(rng.choice(specials))
+        d.flags = int(rng.choice([0, 1, 2, 3, 4, 7, 8, 1 << 31]))
+        d.tune_radix = int(rng.choice([0, 2, 3, 4, 16, 32]))
+        d.tune_tile = int(rng.choice([0, 1, 3, 8, 32]))
+        d.tune_slab = int(rng.choice([-1, 0, 1, 2, 1 << 30]))
+        d.tune_lag = int(rng.choice([-1, 0, 1, 8, 9]))
+        h = ctypes.c_void_p()
+        st = lib.sf_plan_create(ctypes.byref(h), ctypes.byref(d), None)
+        assert st in (-1, -2, -3, -4), st
+        assert not h.value
+        assert lib.sf_last_error()
+        seen.add(st)
+    assert {-1, -2} <= seen
