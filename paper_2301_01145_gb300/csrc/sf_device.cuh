@@ -49,6 +49,36 @@ template <typename V> __device__ __forceinline__ V czero() { return mk<V>(0, 0);
 template <bool INV, typename V> __device__ __forceinline__ V mul_mi(V a) { return INV ? mk<V>(-a.y, a.x) : mk<V>(a.y, -a.x); }
 // multiply by i
 template <typename V> __device__ __forceinline__ V mul_i(V a) { return mk<V>(-a.y, a.x); }
+// a + mul_mi(b) and a - mul_mi(b), written out so that the rotation stays a
+// renaming of components (no rotated value is ever formed)
+template <bool INV, typename V> __device__ __forceinline__ V cadd_mi(V a, V b) {
+  return INV ? mk<V>(a.x - b.y, a.y + b.x) : mk<V>(a.x + b.y, a.y - b.x);
+}
+template <bool INV, typename V> __device__ __forceinline__ V csub_mi(V a, V b) {
+  return INV ? mk<V>(a.x + b.y, a.y - b.x) : mk<V>(a.x - b.y, a.y + b.x);
+}
+
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+// Packed FP32x2 arithmetic (sm_100 and later): a complex add or subtract of
+// float2 values is one instruction instead of two.  Each component is rounded
+// exactly as by the scalar operation, so results are unchanged; the FFT
+// butterflies are issue-bound and mostly complex adds.  These overloads are
+// declared before the butterflies so that their unqualified calls bind here.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  float2 r;
+  asm("{.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+// s * a + b with one scalar s for both components
+__device__ __forceinline__ float2 cfma_s(float s, float2 a, float2 b) { return __ffma2_rn(make_float2(s, s), a, b); }
+#endif
+template <typename V> __device__ __forceinline__ V cfma_s(decltype(V::x) s, V a, V b) {
+  return mk<V>(fma(s, a.x, b.x), fma(s, a.y, b.y));
+}
 
 // ---------------------------------------------------------------------------
 // radix butterflies: y_k = sum_n x_n exp(-+ 2 pi i n k / R), in place, natural order
@@ -65,11 +95,20 @@ template <bool INV, typename V> __device__ __forceinline__ void dft2(V *x) {
 }
 
 template <bool INV, typename V> __device__ __forceinline__ void dft4v(V &a0, V &a1, V &a2, V &a3) {
-  V t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_mi<INV>(csub(a1, a3));
+  const V t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), d = csub(a1, a3);
   a0 = cadd(t0, t2);
   a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  a1 = cadd_mi<INV>(t1, d);
+  a3 = csub_mi<INV>(t1, d);
+}
+
+// dft4v of (a0, a1, mul_mi(a2), a3), the rotation folded into the adds
+template <bool INV, typename V> __device__ __forceinline__ void dft4v_r2(V &a0, V &a1, V &a2, V &a3) {
+  const V t0 = cadd_mi<INV>(a0, a2), t1 = csub_mi<INV>(a0, a2), t2 = cadd(a1, a3), d = csub(a1, a3);
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd_mi<INV>(t1, d);
+  a3 = csub_mi<INV>(t1, d);
 }
 
 template <bool INV, typename V> __device__ __forceinline__ void dft4(V *x) { dft4v<INV>(x[0], x[1], x[2], x[3]); }
@@ -78,12 +117,12 @@ template <bool INV, typename V> __device__ __forceinline__ void dft3(V *x) {
   typedef decltype(V::x) T;
   V t = cadd(x[1], x[2]);
   V d = csub(x[1], x[2]);
-  // u = (x1 - x2) * (-+ i sqrt3/2)
-  V u = mul_mi<INV>(cscale(d, (T)SF_SQRT3_2));
-  V m = csub(x[0], cscale(t, (T)0.5));
+  // y1,2 = x0 - t/2 +- (-+ i sqrt3/2) (x1 - x2)
+  const V u = cscale(d, (T)SF_SQRT3_2);
+  const V m = cfma_s<V>((T)-0.5, t, x[0]);
   x[0] = cadd(x[0], t);
-  x[1] = cadd(m, u);
-  x[2] = csub(m, u);
+  x[1] = cadd_mi<INV>(m, u);
+  x[2] = csub_mi<INV>(m, u);
 }
 
 template <bool INV, typename V> __device__ __forceinline__ V w8(V a, int j) {  // a * exp(-+ 2 pi i j / 8), j = 0..3
@@ -104,11 +143,10 @@ template <bool INV, typename V> __device__ __forceinline__ void dft8(V *x) {
   dft4v<INV>(e0, e1, e2, e3);
   dft4v<INV>(o0, o1, o2, o3);
   o1 = w8<INV>(o1, 1);
-  o2 = w8<INV>(o2, 2);
   o3 = w8<INV>(o3, 3);
   x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
   x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
-  x[2] = cadd(e2, o2); x[6] = csub(e2, o2);
+  x[2] = cadd_mi<INV>(e2, o2); x[6] = csub_mi<INV>(e2, o2);  // w8^2 = -+i
   x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
 }
 
@@ -144,10 +182,15 @@ template <bool INV, typename V> __device__ __forceinline__ void dft16(V *x) {
   for (int k1 = 0; k1 < 4; ++k1) {
     V t0 = f[0 * 4 + k1];
     V t1 = w16<INV>(f[1 * 4 + k1], 1 * k1);
-    V t2 = w16<INV>(f[2 * 4 + k1], 2 * k1);
     V t3 = w16<INV>(f[3 * 4 + k1], 3 * k1);
-    dft4v<INV>(t0, t1, t2, t3);
-    x[k1] = t0; x[k1 + 4] = t1; x[k1 + 8] = t2; x[k1 + 12] = t3;
+    if (k1 == 2) {
+      dft4v_r2<INV>(t0, t1, f[2 * 4 + k1], t3);  // w16^4 = -+i
+      x[k1] = t0; x[k1 + 4] = t1; x[k1 + 8] = f[2 * 4 + k1]; x[k1 + 12] = t3;
+    } else {
+      V t2 = w16<INV>(f[2 * 4 + k1], 2 * k1);
+      dft4v<INV>(t0, t1, t2, t3);
+      x[k1] = t0; x[k1 + 4] = t1; x[k1 + 8] = t2; x[k1 + 12] = t3;
+    }
   }
 }
 

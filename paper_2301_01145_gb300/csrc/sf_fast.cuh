@@ -115,11 +115,10 @@ template <int E> __host__ __device__ constexpr int trows_elems() { return 32 * E
 // ---- pruned E-point DFTs ----------------------------------------------------
 // dft4 of (a0, a1, 0, 0)
 template <bool INV, typename V> __device__ __forceinline__ void dft4_2in(V a0, V a1, V &y0, V &y1, V &y2, V &y3) {
-  const V m = mul_mi<INV>(a1);
   y0 = cadd(a0, a1);
-  y1 = cadd(a0, m);
+  y1 = cadd_mi<INV>(a0, a1);
   y2 = csub(a0, a1);
-  y3 = csub(a0, m);
+  y3 = csub_mi<INV>(a0, a1);
 }
 
 // inputs x[E/2 .. E) are zero
@@ -132,21 +131,26 @@ template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfi
     for (int k1 = 0; k1 < 4; ++k1) {
       V t0 = f[k1];
       V t1 = w16<INV>(f[4 + k1], k1);
-      V t2 = w16<INV>(f[8 + k1], 2 * k1);
       V t3 = w16<INV>(f[12 + k1], 3 * k1);
-      dft4v<INV>(t0, t1, t2, t3);
-      x[k1] = t0; x[k1 + 4] = t1; x[k1 + 8] = t2; x[k1 + 12] = t3;
+      if (k1 == 2) {
+        V t2 = f[8 + k1];
+        dft4v_r2<INV>(t0, t1, t2, t3);  // w16^4 = -+i
+        x[k1] = t0; x[k1 + 4] = t1; x[k1 + 8] = t2; x[k1 + 12] = t3;
+      } else {
+        V t2 = w16<INV>(f[8 + k1], 2 * k1);
+        dft4v<INV>(t0, t1, t2, t3);
+        x[k1] = t0; x[k1 + 4] = t1; x[k1 + 8] = t2; x[k1 + 12] = t3;
+      }
     }
   } else {  // E == 8
     V e0, e1, e2, e3, o0, o1, o2, o3;
     dft4_2in<INV>(x[0], x[2], e0, e1, e2, e3);
     dft4_2in<INV>(x[1], x[3], o0, o1, o2, o3);
     o1 = w8<INV>(o1, 1);
-    o2 = w8<INV>(o2, 2);
     o3 = w8<INV>(o3, 3);
     x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
     x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
-    x[2] = cadd(e2, o2); x[6] = csub(e2, o2);
+    x[2] = cadd_mi<INV>(e2, o2); x[6] = csub_mi<INV>(e2, o2);  // w8^2 = -+i
     x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
   }
 }
@@ -165,10 +169,16 @@ template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfo
     for (int k1 = 0; k1 < 4; ++k1) {
       const V t0 = f[k1];
       const V t1 = w16<INV>(f[4 + k1], k1);
-      const V t2 = w16<INV>(f[8 + k1], 2 * k1);
       const V t3 = w16<INV>(f[12 + k1], 3 * k1);
-      x[k1] = cadd(cadd(t0, t2), cadd(t1, t3));
-      x[k1 + 4] = cadd(csub(t0, t2), mul_mi<INV>(csub(t1, t3)));
+      if (k1 == 2) {  // w16^4 = -+i
+        const V t2 = f[8 + k1];
+        x[k1] = cadd(cadd_mi<INV>(t0, t2), cadd(t1, t3));
+        x[k1 + 4] = cadd_mi<INV>(csub_mi<INV>(t0, t2), csub(t1, t3));
+      } else {
+        const V t2 = w16<INV>(f[8 + k1], 2 * k1);
+        x[k1] = cadd(cadd(t0, t2), cadd(t1, t3));
+        x[k1 + 4] = cadd_mi<INV>(csub(t0, t2), csub(t1, t3));
+      }
     }
   } else {
     V e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
@@ -177,7 +187,7 @@ template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfo
     dft4v<INV>(o0, o1, o2, o3);
     x[0] = cadd(e0, o0);
     x[1] = cadd(e1, w8<INV>(o1, 1));
-    x[2] = cadd(e2, w8<INV>(o2, 2));
+    x[2] = cadd_mi<INV>(e2, o2);  // w8^2 = -+i
     x[3] = cadd(e3, w8<INV>(o3, 3));
   }
 }
@@ -246,7 +256,7 @@ __device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
 #pragma unroll
       for (int j = 0; j < E; ++j) {
         const V p = shfl_xor_c(v[m][j], mm);
-        V r = mk<V>(fmaf(sg, v[m][j].x, p.x), fmaf(sg, v[m][j].y, p.y));
+        V r = cfma_s<V>(sg, v[m][j], p);
         if (mm > 1 && (q & mm)) r = cmul(r, w);
         v[m][j] = r;
       }
@@ -273,7 +283,7 @@ __device__ __forceinline__ void wfft_inv_m(cx<T> (&v)[M][E], cx<T> *wsm, const c
         V mine = v[m][j];
         if (mm > 1 && hi) mine = cmulc(mine, w);
         const V p = shfl_xor_c(mine, mm);
-        v[m][j] = mk<V>(fmaf(sg, mine.x, p.x), fmaf(sg, mine.y, p.y));  // hi: p - mine, lo: p + mine
+        v[m][j] = cfma_s<V>(sg, mine, p);  // hi: p - mine, lo: p + mine
       }
   }
 #pragma unroll
