@@ -1025,11 +1025,18 @@ __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, 
 }
 
 // persistent YZ executor over the slab work list (same queue / bounded-wait
-// protocol as k_exec).  The pass table is packed into shared memory at start;
-// thread 0 claims items and waits for their dependencies, thread 32 publishes
-// the completion of the previous tile, so the two round trips to L2 overlap.
-// The per-tile descriptor is double-buffered: thread 0 fills slot (k+1) & 1
-// while thread 32 still reads slot k & 1.
+// protocol as k_exec).  The pass table is packed into shared memory at start.
+// Thread 0 prepares the next item while the other warps finish the current
+// tile: once its own warp's share of tile k is done it decodes item k + 1
+// (claimed one tile earlier) and probes that item's dependency counters once,
+// without blocking (item k + 1 may depend on the very tile this CTA is still
+// finishing).  The end-of-tile barrier then both completes tile k and
+// publishes the prepared descriptor, so an item whose dependencies were met
+// at the probe starts without a second barrier; otherwise thread 0 waits
+// (bounded) while the CTA holds at one extra barrier.  Thread 32 publishes
+// the completed tile with a release reduction after the barrier.  The
+// descriptor is double-buffered: slot k & 1 is read during tile k while slot
+// (k + 1) & 1 is written.
 template <int E, int NC, bool PAD, int OPS>
 __global__ void __launch_bounds__(SF_FAST_THREADS, OPS == 2 ? 2 : 1)
     k_fyz(const Prob<float> *probs, FastGeo g, const FPass *passes, const int *pass_start, int npass, unsigned *done,
@@ -1038,8 +1045,8 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS == 2 ? 2 : 1)
   extern __shared__ __align__(16) unsigned char fsm[];
   __shared__ __align__(16) Prob<float> sP;
   __shared__ FPass sPass[2];
-  __shared__ int s_item[2], s_pass[2], s_ok[2];
-  __shared__ unsigned long long s_tbusy[2];
+  __shared__ int s_item[2], s_pass[2], s_ok[2], s_ready[2];
+  __shared__ unsigned long long s_tprep[2];
   load_prob<float>(sP, probs, io);
   constexpr int MM = fast_yz_lines(OPS);  // interleaved lines per warp (warp buffer depth)
   V *wsm_all = reinterpret_cast<V *>(fsm);
@@ -1058,73 +1065,96 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS == 2 ? 2 : 1)
   }
   __syncthreads();
   const int total = s_start[npass];
-  int next_it = 0;  // thread 0: item claimed one iteration ahead (queue round trip overlaps a tile)
+  int next_it = 0;  // thread 0: item claimed one tile ahead (the queue round trip overlaps a tile)
   int cur = 0;      // thread 0: pass of the last item (items arrive in increasing order)
-  if (threadIdx.x == 0) next_it = (int)atomicAdd(&ctl->next, 1u);
-  for (int k = 0;; k ^= 1) {
-    if (threadIdx.x == 0) {
-      const int it = next_it;
-      if (it < total) next_it = (int)atomicAdd(&ctl->next, 1u);
-      s_item[k] = it;
-      s_ok[k] = 1;
-      if (it < total) {
-        while (s_start[cur + 1] <= it) ++cur;
-        const int lo = cur;
-        FPass &sp = sPass[k];
-        const int a = s_pa[lo], b = s_pb[lo];
-        sp.kind = a & 3;
-        sp.slot = (a >> 2) & 15;
-        sp.nkx = (a >> 6) & 1023;
-        sp.kx0 = a >> 16;
-        sp.ntiles = s_start[lo + 1] - s_start[lo];
-        s_pass[k] = lo;
-        const unsigned long long tw0 = global_ns();
-        for (int d = 0; d < 2; ++d) {
-          const int dp = ((d ? b >> 16 : b) & 0xffff) - 1;
-          if (dp < 0) continue;
-          const unsigned need = (unsigned)(s_start[dp + 1] - s_start[dp]);
-          unsigned iters = 0;
-          bool ok = true;
-          while (ld_acquire(&done[dp]) < need) {
-            __nanosleep(64);
-            if (((++iters) & 255u) == 0 && (global_ns() - tw0 > timeout_ns || iters > (1u << 28))) {
-              atomicCAS(&ctl->error, 0u, 6u);
-              atomicExch(&ctl->err_pass, (unsigned)lo);
-              atomicOr(sticky, 1u);
-              ok = false;
-              break;
-            }
-          }
-          if (!ok) {
-            s_ok[k] = 0;
-            break;
-          }
+
+  // thread 0: decode the claimed item into slot k, claim the one after it and
+  // probe the item's dependency counters once
+  auto prepare = [&](int k) {
+    const int it = next_it;
+    if (it < total) next_it = (int)atomicAdd(&ctl->next, 1u);
+    s_item[k] = it;
+    s_ok[k] = 1;
+    s_ready[k] = 1;
+    if (it >= total) return;
+    const unsigned long long t0 = global_ns();
+    s_tprep[k] = t0;
+    while (s_start[cur + 1] <= it) ++cur;
+    const int lo = cur;
+    FPass &sp = sPass[k];
+    const int a = s_pa[lo], b = s_pb[lo];
+    sp.kind = a & 3;
+    sp.slot = (a >> 2) & 15;
+    sp.nkx = (a >> 6) & 1023;
+    sp.kx0 = a >> 16;
+    sp.ntiles = s_start[lo + 1] - s_start[lo];
+    sp.dep[0] = (b & 0xffff) - 1;
+    sp.dep[1] = ((b >> 16) & 0xffff) - 1;
+    s_pass[k] = lo;
+    bool ready = true;
+    for (int d = 0; d < 2; ++d) {
+      const int dp = sp.dep[d];
+      if (dp >= 0 && ld_acquire(&done[dp]) < (unsigned)(s_start[dp + 1] - s_start[dp])) ready = false;
+    }
+    s_ready[k] = ready ? 1 : 0;
+    if (ready) atomicAdd(&ctl->wait_ns[a & 3], global_ns() - t0);
+  };
+  // thread 0: bounded wait for the dependencies of the item in slot k
+  auto wait_deps = [&](int k) {
+    const FPass &sp = sPass[k];
+    const unsigned long long tw0 = s_tprep[k];
+    for (int d = 0; d < 2; ++d) {
+      const int dp = sp.dep[d];
+      if (dp < 0) continue;
+      const unsigned need = (unsigned)(s_start[dp + 1] - s_start[dp]);
+      unsigned iters = 0;
+      while (ld_acquire(&done[dp]) < need) {
+        __nanosleep(64);
+        if (((++iters) & 255u) == 0 && (global_ns() - tw0 > timeout_ns || iters > (1u << 28))) {
+          atomicCAS(&ctl->error, 0u, 6u);
+          atomicExch(&ctl->err_pass, (unsigned)s_pass[k]);
+          atomicOr(sticky, 1u);
+          s_ok[k] = 0;
+          return;
         }
-        const unsigned long long tb = global_ns();
-        s_tbusy[k] = tb;
-        atomicAdd(&ctl->wait_ns[a & 3], tb - tw0);
       }
     }
-    __syncthreads();
+    atomicAdd(&ctl->wait_ns[sp.kind], global_ns() - tw0);
+  };
+
+  if (threadIdx.x == 0) {
+    next_it = (int)atomicAdd(&ctl->next, 1u);
+    prepare(0);
+  }
+  __syncthreads();
+  for (int k = 0;; k ^= 1) {
     const int it = s_item[k];
     if (it >= total) break;
+    // read before the slot can be rewritten (prepare(k) runs two tiles later)
+    const int my_pass = s_pass[k];
+    const int my_kind = sPass[k].kind;
+    if (!s_ready[k]) {  // uniform over the CTA
+      if (threadIdx.x == 0) wait_deps(k);
+      __syncthreads();
+    }
+    unsigned long long t_start = 0;  // thread 32: start of the tile (tracing)
+    if (threadIdx.x == 32) t_start = global_ns();
     if (s_ok[k]) {
       const FPass &ps = sPass[k];
-      const int tile = it - s_start[s_pass[k]];
-      const int kind = ps.kind;
-      if (kind == FK_YF) fast_yf<E, PAD, MM == 1 ? 1 : 2>(sP, g, ps, tile, wsm, T);
-      else if (kind == FK_ZS) {
+      const int tile = it - s_start[my_pass];
+      if (my_kind == FK_YF) fast_yf<E, PAD, MM == 1 ? 1 : 2>(sP, g, ps, tile, wsm, T);
+      else if (my_kind == FK_ZS) {
         if (OPS == 2) fast_zs_split<E, PAD>(sP, g, ps, tile, wsm, T);
         else fast_zs<E, NC, PAD, OPS>(sP, g, ps, tile, wsm);
       } else if (OPS == 2) fast_yi_rows<E, PAD>(sP, g, ps, tile, wsm);
       else fast_yi<E, PAD>(sP, g, ps, tile, wsm, T);
     }
+    if (threadIdx.x == 0) prepare(k ^ 1);
     __syncthreads();
     if (threadIdx.x == 32) {
-      red_release_add(&done[s_pass[k]], 1u);  // publishes the tile (cumulative over the barrier above)
-      const int kind = sPass[k].kind;
-      atomicAdd(&ctl->busy_ns[kind], global_ns() - s_tbusy[k]);
-      atomicAdd(&ctl->tiles[kind], 1ull);
+      red_release_add(&done[my_pass], 1u);  // publishes the tile (cumulative over the barrier above)
+      atomicAdd(&ctl->busy_ns[my_kind], global_ns() - t_start);
+      atomicAdd(&ctl->tiles[my_kind], 1ull);
     }
   }
 }
