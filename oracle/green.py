@@ -1,5 +1,6 @@
-"""Regularised Green's functions (Sec. 2.6.2): Gaussian kernels "G2" to "G10" and the
-3D spectral kernel "SPECT" (a sharp cut-off at the grid wavenumber pi / max h).
+"""Regularised Green's functions (Sec. 2.6.2): Gaussian kernels "G2" to "G10" (2D, 3D)
+and the spectral kernel "SPECT" in 1D and 3D (a sharp cut-off at the grid
+wavenumber pi / max h).
 
 Convention: -lap G = zeta_sigma, the normalised Gaussian of width sigma, so
 that G > 0 and the solution of lap(psi) = s f is psi = -s (G * f).
@@ -80,11 +81,27 @@ def spectral_3d(r: np.ndarray, kc: float) -> np.ndarray:
     return np.where(r > 0.0, val, kc / (2.0 * math.pi ** 2))
 
 
+def spectral_1d(r: np.ndarray, kc: float) -> np.ndarray:
+    """Sharp spectral cut-off in 1D (the only kernel the paper uses in 1D,
+    Sec. 4.3): -G'' = sin(kc x) / (pi x), the band-limited delta.  Integrating
+    twice, G(x) = -(1/pi) [|x| Si(kc |x|) + cos(kc x) / kc], with the free
+    constant fixed (our reading) so that G + |x|/2 -> 0 as |x| -> infinity:
+    the same far field as the 1D free-space kernel -|x|/2 of -d^2/dx^2.
+    G(0) = -1 / (pi kc).  Si from scipy.special.sici."""
+    r = np.abs(np.asarray(r, dtype=np.float64))
+    si, _ = special.sici(kc * r)
+    return -(r * si + np.cos(kc * r) / kc) / math.pi
+
+
 def green(dim: int, r: np.ndarray, sigma: float, kernel: str = "G2", kc: float = 0.0) -> np.ndarray:
     if kernel == "SPECT":
-        if dim != 3:
-            raise ValueError("the spectral kernel is 3D only")
-        return spectral_3d(r, kc)
+        if dim == 3:
+            return spectral_3d(r, kc)
+        if dim == 1:
+            return spectral_1d(r, kc)
+        raise ValueError("the spectral kernel is defined for 1D and 3D")
+    if dim == 1:
+        raise ValueError("1D unbounded solves use the spectral kernel (Sec. 4.3)")
     g = g2_3d(r, sigma) if dim == 3 else g2_2d(r, sigma)
     order = int(kernel[1:])
     if kernel[0] != "G" or order not in (2, 4, 6, 8, 10):
