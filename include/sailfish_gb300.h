@@ -58,14 +58,15 @@ typedef enum { SF_OP_NONE = 0, SF_OP_GRAD = 1, SF_OP_DIV = 2, SF_OP_CURL = 3, SF
 /* Eigenvalue type for bounded axes (Sec. 2.5.2, Table 1). */
 typedef enum { SF_EIG_PS = 0, SF_EIG_FD2 = 1 } sf_eig;
 
-/* Regularised Green's function for unbounded axes (Sec. 2.6.2): order-2 Gaussian. */
-/* Unbounded kernels (Sec. 2.6.2): Gaussian regularisation of order 2 to 10.
+/* Unbounded kernels (Sec. 2.6.2): Gaussian regularisation of order 2 to 10 (2D, 3D).
  * G_P = G2 + sum_{j=1}^{P/2-1} sigma^{2j} / (2^j j!) (-lap)^{j-1} zeta_sigma, the
  * kernel whose smoothing has the transform exp(-(k sigma)^2/2) times the Taylor
  * series of exp(+(k sigma)^2/2) cut below order P (error O((k sigma)^P)). */
-/* SF_GREEN_SPECTRAL (3D only): the sharp spectral cut-off G^(k) = 1/k^2 for
- * |k| <= kc = pi / max_axis h, zero beyond, i.e. G(r) = Si(kc r) / (2 pi^2 r);
- * green_sigma is not used. */
+/* SF_GREEN_SPECTRAL (1D and 3D; the only 1D kernel, Sec. 4.3): the sharp
+ * spectral cut-off G^(k) = 1/k^2 for |k| <= kc = pi / max_axis h, zero beyond,
+ * i.e. G(r) = Si(kc r) / (2 pi^2 r) in 3D and
+ * G(x) = -(|x| Si(kc |x|) + cos(kc x) / kc) / pi in 1D (constant chosen so that
+ * G + |x|/2 -> 0, the far field of -|x|/2); green_sigma is not used. */
 typedef enum {
   SF_GREEN_G2 = 0, SF_GREEN_G4 = 1, SF_GREEN_G6 = 2, SF_GREEN_G8 = 3, SF_GREEN_G10 = 4, SF_GREEN_SPECTRAL = 5
 } sf_green;
@@ -85,8 +86,8 @@ typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
 
 /*
  * Problem description (Sec. 2.4 solver options, Sec. 2.5.1 Table 1).
- *   dim        2 or 3.
- *   n[a]       cell count N_c per axis a = x, y, z (n[2] ignored in 2D).  Every
+ *   dim        1, 2 or 3 (Sec. 2.4: the 1D / 2D / 3D solver classes).
+ *   n[a]       cell count N_c per axis a = x, y, z (axes a >= dim ignored).  Every
  *              FFT length used (N_c for periodic, 4 N_c for an axis with a
  *              Dirichlet and a Neumann face, 2 N_c otherwise) must be of the
  *              form 2^p or 3*2^p and lie in [4, 2048]; 2 <= N_c <= 2048
@@ -108,8 +109,8 @@ typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
  *   eig        PS or FD2 (bounded axes; ignored when unbounded).
  *   op         spectral operator on psi; needs periodic or unbounded axes.
  *              GRAD: ncomp 1 -> dim outputs.  DIV: ncomp = dim -> 1 output.
- *              CURL: 3D ncomp 3 -> 3 outputs; 2D ncomp 1 -> 2 outputs.
- *              NABLA: ncomp -> ncomp outputs.
+ *              CURL: 3D ncomp 3 -> 3 outputs; 2D ncomp 1 -> 2 outputs; not 1D.
+ *              NABLA: ncomp -> ncomp outputs.  In 1D, GRAD and DIV are d/dx.
  *   green      kernel for unbounded solves; green_sigma its Gaussian width
  *              (positive and finite; ignored by SF_GREEN_SPECTRAL).
  *   ncomp      number of field components solved together (1..3).

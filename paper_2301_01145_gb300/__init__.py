@@ -46,7 +46,7 @@ class Plan:
         self.dtype = torch.float32 if prec == "f32" else torch.float64
         self.handle = sf_plan_create(self.desc, stream)
         ins, outs, ops, ws = sf_plan_query(self.handle)
-        trim = (lambda s: s if dim == 3 else (s[0],) + s[2:])
+        trim = (lambda s: (s[0],) + tuple(s[4 - dim:]))  # [ncomp] + the dim spatial extents
         self.in_shape = trim(tuple(ins))
         self.out_shape = trim(tuple(outs))
         self.op_shape = trim(tuple(ops)) if ops[0] else None

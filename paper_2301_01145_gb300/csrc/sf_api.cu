@@ -291,6 +291,7 @@ template <typename T> int pass_tiles(const Prob<T> &P, const Pass<T> &ps) {
     case PK_YSTAGE2: return cdiv(P.nsx, lines_per_tile(P.cpath, W));
     case PK_FILL: return cdiv(P.fill_count * P.nout, 4096);
     case PK_ZFWD: return P.nsx * cdiv(P.nsy, 2 * W);
+    case PK_MULT1D: return cdiv(P.nsx, SF_MULT1D_MODES);
   }
   return 0;
 }
@@ -307,7 +308,8 @@ template <typename T> void size_pass(const Prob<T> &P, Pass<T> &ps, int wcap) {
     case PK_ZSTAGE: L = P.ax[2].L; nbuf = P.ncomp + 2; lines = P.cpath ? P.nsy : cdiv(P.nsy, 2); break;
     case PK_YSTAGE2: L = P.ax[1].L; nbuf = P.ncomp + 2; lines = P.cpath ? P.nsx : cdiv(P.nsx, 2); break;
     case PK_ZFWD: L = P.ax[2].L; lines = cdiv(P.nsy, 2); break;
-    case PK_FILL: ps.W = 1; ps.Wp = 1; ps.nbuf = 0; ps.bufsz = 0; return;
+    case PK_FILL:
+    case PK_MULT1D: ps.W = 1; ps.Wp = 1; ps.nbuf = 0; ps.bufsz = 0; return;
   }
   int W = kMaxW;
   if (wcap >= 1 && wcap < kMaxW)
@@ -805,7 +807,7 @@ static int op_outputs(int op, int dim, int ncomp) {
 }
 
 static sf_status validate(const sf_plan_desc &d) {
-  if (d.dim != 2 && d.dim != 3) return fail(SF_ERR_ARG, "dim must be 2 or 3");
+  if (d.dim < 1 || d.dim > 3) return fail(SF_ERR_ARG, "dim must be 1, 2 or 3");
   if (d.flags & ~(SF_FLAG_UNFUSED | SF_FLAG_GENERIC | SF_FLAG_DEBUG_CHECKS)) return fail(SF_ERR_ARG, "unknown flag bits");
   if (d.prec != SF_F32 && d.prec != SF_F64) return fail(SF_ERR_ARG, "prec must be SF_F32 or SF_F64");
   if (d.grid != SF_GRID_REGULAR && d.grid != SF_GRID_STAGGERED) return fail(SF_ERR_ARG, "bad grid type");
@@ -840,7 +842,10 @@ static sf_status validate(const sf_plan_desc &d) {
   if (ncp && nreal) return fail(SF_ERR_UNSUPPORTED, "mixing periodic/unbounded with Dirichlet/Neumann axes");
   if (nunb && nunb != d.dim) return fail(SF_ERR_UNSUPPORTED, "semi-unbounded domains");
   if (nunb && (d.green < SF_GREEN_G2 || d.green > SF_GREEN_SPECTRAL)) return fail(SF_ERR_ARG, "bad kernel");
-  if (nunb && d.green == SF_GREEN_SPECTRAL && d.dim != 3) return fail(SF_ERR_UNSUPPORTED, "the spectral kernel is 3D only");
+  if (nunb && d.green == SF_GREEN_SPECTRAL && d.dim == 2)
+    return fail(SF_ERR_UNSUPPORTED, "the spectral kernel is defined for 1D and 3D");
+  if (nunb && d.dim == 1 && d.green != SF_GREEN_SPECTRAL)
+    return fail(SF_ERR_UNSUPPORTED, "1D unbounded solves use the spectral kernel (SF_GREEN_SPECTRAL)");
   if (nunb && d.green != SF_GREEN_SPECTRAL && !(d.green_sigma > 0.0 && std::isfinite(d.green_sigma)))
     return fail(SF_ERR_ARG, "green_sigma must be positive and finite");
   if (ncp && d.bc[0][0] == SF_BC_PERIODIC && (d.n[0] % 2)) return fail(SF_ERR_UNSUPPORTED, "odd periodic x length");
@@ -848,6 +853,7 @@ static sf_status validate(const sf_plan_desc &d) {
     if (nreal) return fail(SF_ERR_UNSUPPORTED, "spectral operators on Dirichlet/Neumann axes");
     if (d.op == SF_OP_GRAD && d.ncomp != 1) return fail(SF_ERR_ARG, "GRAD needs ncomp = 1");
     if (d.op == SF_OP_DIV && d.ncomp != d.dim) return fail(SF_ERR_ARG, "DIV needs ncomp = dim");
+    if (d.op == SF_OP_CURL && d.dim == 1) return fail(SF_ERR_ARG, "CURL needs dim 2 or 3");
     if (d.op == SF_OP_CURL && d.ncomp != (d.dim == 3 ? 3 : 1)) return fail(SF_ERR_ARG, "CURL needs ncomp 3 (3D) or 1 (2D)");
   }
   if (d.ncomp + op_outputs(d.op, d.dim, d.ncomp) > SF_MAXF) return fail(SF_ERR_ARG, "too many fields");
@@ -1016,8 +1022,10 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
       ex.add(Q, PK_YFWD, 0, (int)ex.passes.size() - 1);
       ex.add(Q, PK_ZSTAGE, 0, (int)ex.passes.size() - 1);
       ex.add(Q, PK_YINV, 0, (int)ex.passes.size() - 1);
-    } else {
+    } else if (d.dim == 2) {
       ex.add(Q, PK_YSTAGE2, 0, (int)ex.passes.size() - 1);
+    } else {
+      ex.add(Q, PK_MULT1D, 0, (int)ex.passes.size() - 1);
     }
   };
   auto back = [&](ExecList<T> &ex, const Prob<T> &Q, int dep) {
@@ -1106,7 +1114,7 @@ template <typename T> sf_status PlanImpl<T>::build_green() {
   SF_CK(cudaMemcpy(dprob, &G, sizeof(Prob<double>), cudaMemcpyHostToDevice));
   ExecList<double> ex;
   ex.add(G, PK_XFWD, 0);
-  ex.add(G, PK_YFWD, 0, 0);
+  if (dim >= 2) ex.add(G, PK_YFWD, 0, 0);
   if (dim == 3) ex.add(G, PK_ZFWD, 0, 1);
   SF_TRY(ex.upload(tmem));
   IOArgs<double> io{};
@@ -1116,7 +1124,8 @@ template <typename T> sf_status PlanImpl<T>::build_green() {
   void *gh;
   SF_TRY(mem.alloc(&gh, cnt * sizeof(T)));
   const double scale = -d.rhs_scale * hd / prodL;
-  sfg::k_convert_scale<T><<<1024, 256, 0, stream>>>((T *)gh, (const double *)out, cnt, scale);
+  // 1D: the x transform's output (A) is the table
+  sfg::k_convert_scale<T><<<1024, 256, 0, stream>>>((T *)gh, (const double *)(dim == 1 ? A : out), cnt, scale);
   SF_CK(cudaGetLastError());
   if (fastE && dim == 3) {
     void *ght;

@@ -247,6 +247,7 @@ enum PassKind : int {
   PK_YSTAGE2 = 5,  // 2D: y transform, multiply, operator, inverse y: A -> B
   PK_FILL = 6,     // Dirichlet boundary-plane fill of psi (regular grids)
   PK_ZFWD = 7,     // forward-only z transform (Green's table set-up): I1 -> fwd_out
+  PK_MULT1D = 8,   // 1D: multiply and operator in x-spectral space: A -> B
 };
 
 template <typename T> struct Axis {

@@ -253,7 +253,7 @@ __device__ __forceinline__ double kernel_q(int dim, int m, double u) {
   }
 }
 
-// order: 2..10 for the Gaussian kernels, 0 for the 3D spectral cut-off at kc
+// order: 2..10 for the Gaussian kernels (2D, 3D), 0 for the spectral cut-off at kc (1D, 3D)
 static __global__ void k_green_octant(double *out, int nx, int ny, int nz, double hx, double hy, double hz, double sigma,
                                int dim, int order, double kc) {
   const size_t total = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
@@ -266,7 +266,9 @@ static __global__ void k_green_octant(double *out, int nx, int ny, int nz, doubl
     const double dx = x * hx, dy = y * hy, dz = z * hz;
     const double r = sqrt(dx * dx + dy * dy + dz * dz);
     double g;
-    if (order == 0) {  // spectral: Si(kc r) / (2 pi^2 r)
+    if (order == 0 && dim == 1) {  // spectral, 1D: -(r Si(kc r) + cos(kc r) / kc) / pi
+      g = -(r * sf_sine_integral(kc * r) + cos(kc * r) / kc) / pi;
+    } else if (order == 0) {  // spectral, 3D: Si(kc r) / (2 pi^2 r)
       g = r == 0.0 ? kc / (2.0 * pi * pi) : sf_sine_integral(kc * r) / (2.0 * pi * pi * r);
     } else if (dim == 3) {
       if (r == 0.0) g = sqrt(2.0) / (4.0 * pi * sqrt(pi) * sigma);

@@ -782,6 +782,64 @@ template <typename T> __device__ void tile_fill(const Prob<T> &P, const Pass<T> 
   }
 }
 
+// ---------------------------------------------------------------------------
+// MULT1D: the spectral step of a 1D solve (Sec. 2.4), one thread per x mode
+// over SF_MULT1D_MODES modes per tile: psi^ = m(kx) f^ with the eigenvalue or
+// Green's multiplier, then the operator outputs (complex path: d/dx for GRAD
+// and DIV, -kappa^2 for NABLA).  The adjoint adds the conjugate-transposed
+// operator terms to the psi gradient before the (real) multiplier.
+// ---------------------------------------------------------------------------
+#define SF_MULT1D_MODES 256
+template <typename T> __device__ void tile_mult1d(const Prob<T> &P, const Pass<T> &ps, int t) {
+  typedef cx<T> V;
+  const Axis<T> &X = P.ax[0];
+  const int nk = P.nsx, ncomp = P.ncomp, nop = P.nop;
+  for (int e = threadIdx.x; e < SF_MULT1D_MODES; e += blockDim.x) {
+    const int kx = t * SF_MULT1D_MODES + e;
+    if (kx >= nk) break;
+    T m;
+    if (P.green) {
+      m = __ldg(&P.ghat[kx]);
+    } else {
+      const T lam = __ldg(&X.lam[kx]);
+      m = lam == (T)0 ? (T)0 : P.mscale / lam;
+    }
+    if (P.cpath) {
+      const V *A = reinterpret_cast<const V *>(P.A);
+      V *B = reinterpret_cast<V *>(P.B);
+      const T k = __ldg(&X.kap[kx]), k2 = __ldg(&X.kap2[kx]);
+      if (!P.adjoint) {
+        V psv[SF_MAXF];
+        for (int c = 0; c < ncomp; ++c) {
+          psv[c] = cscale(__ldcg(&A[(size_t)c * nk + kx]), m);
+          __stcg(&B[(size_t)c * nk + kx], psv[c]);
+        }
+        for (int o = 0; o < nop; ++o) {
+          const V v = P.op == OPK_NABLA ? cscale(psv[o], -k2) : mul_i(cscale(psv[0], k));
+          __stcg(&B[(size_t)(ncomp + o) * nk + kx], v);
+        }
+      } else {
+        for (int c = 0; c < ncomp; ++c) {
+          V g = __ldcg(&A[(size_t)c * nk + kx]);
+          for (int o = 0; o < nop; ++o) {
+            const V go = __ldcg(&A[(size_t)(ncomp + o) * nk + kx]);
+            if (P.op == OPK_NABLA) {
+              if (o == c) g = cadd(g, cscale(go, -k2));
+            } else if (c == 0) {
+              g = cadd(g, mul_i(cscale(go, -k)));
+            }
+          }
+          __stcg(&B[(size_t)c * nk + kx], cscale(g, m));
+        }
+      }
+    } else {
+      const T *A = reinterpret_cast<const T *>(P.A);
+      T *B = reinterpret_cast<T *>(P.B);
+      for (int c = 0; c < ncomp; ++c) __stcg(&B[(size_t)c * nk + kx], m * __ldcg(&A[(size_t)c * nk + kx]));
+    }
+  }
+}
+
 // dispatch one tile of a pass
 template <typename T> __device__ void run_tile(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
   switch (ps.kind) {
@@ -793,6 +851,7 @@ template <typename T> __device__ void run_tile(const Prob<T> &P, const Pass<T> &
     case PK_YSTAGE2: tile_ystage2<T>(P, ps, t, sm, bufsz); break;
     case PK_FILL: tile_fill<T>(P, ps, t); break;
     case PK_ZFWD: tile_zfwd<T>(P, ps, t, sm, bufsz); break;
+    case PK_MULT1D: tile_mult1d<T>(P, ps, t); break;
     default: break;
   }
 }

@@ -98,7 +98,10 @@ def test_status_strings_and_version(lib):
     (dict(n=(4096, 16, 16)), -2),      # FFT length above 2048
     (dict(n=(2, 16, 16)), -2),         # periodic FFT length 2 is below 4
     (dict(n=(17, 16, 16)), -2),        # odd periodic x length
-    (dict(dim=2, bc="UU", kernel="SPECT"), -2),  # the spectral kernel is 3D only
+    (dict(dim=2, bc="UU", kernel="SPECT"), -2),  # the spectral kernel is defined for 1D and 3D
+    (dict(dim=1, bc="U", kernel="G2", sigma=0.1), -2),  # 1D unbounded: the spectral kernel only
+    (dict(dim=1, op="CURL", ncomp=1), -1),       # no curl in 1D
+    (dict(dim=0), -1),
     (dict(bc="UUU", sigma=0.0, kernel="G6"), -1),  # Gaussian kernels need sigma > 0
     (dict(bc="UUU", sigma=float("inf")), -1),    # ... and finite
     (dict(hi=(float("inf"), 1, 1)), -1),         # infinite extent
