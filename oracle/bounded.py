@@ -9,7 +9,9 @@ Steps, in the paper's order (Sec. 2.4, the four-step solve):
      forward R2R type of Table 1 for Dirichlet/Neumann axes;
   4. divide by the eigenvalue sum lambda = sum_axis lambda_axis(k_axis); the
      zero eigenvalue gives a zero coefficient (Sec. 2.2: zero mean);
-  5. optional spectral operator on periodic axes (Sec. 2.4.3);
+  5. optional spectral operator (Sec. 2.4.3): on periodic axes a product in
+     spectral space; on Dirichlet / Neumann axes the derivative of the basis
+     series (bounded_ops.py);
   6. inverse transforms in reverse order with their normalisation;
   7. write the unknowns back and fill regular Dirichlet boundary nodes with the
      face values (x faces first, then y, then z; later faces overwrite shared
@@ -38,7 +40,7 @@ from typing import Dict, Optional, Tuple
 
 import numpy as np
 
-from . import eigen, fft, ops, r2r
+from . import bounded_ops, eigen, fft, ops, r2r
 from .desc import Desc
 
 
@@ -184,7 +186,8 @@ def solve_bounded(desc: Desc, f: np.ndarray, faces=None):
     fh = forward_transform(desc, rhs)
     psi_hat = fh * inverse_eigen(desc, shape_u)[None]
     op_hat = None
-    if desc.op != "NONE":
+    periodic = all(b == "P" for b in desc.bc[: desc.dim])
+    if desc.op != "NONE" and periodic:
         mults, laps = op_multipliers(desc, shape_u)
         op_hat = apply_operator(desc, psi_hat, mults, laps)
     psi_u = backward_transform(desc, psi_hat).real
@@ -196,4 +199,6 @@ def solve_bounded(desc: Desc, f: np.ndarray, faces=None):
         op_u = backward_transform(desc, op_hat).real
         op_out = np.zeros((op_u.shape[0],) + fields.shape[1:])
         op_out[usl] = op_u
+    elif desc.op != "NONE":  # Dirichlet / Neumann axes: derivatives of the basis series
+        op_out = bounded_ops.apply(desc, psi)
     return psi, op_out
