@@ -292,6 +292,11 @@ template <typename T> int pass_tiles(const Prob<T> &P, const Pass<T> &ps) {
     case PK_FILL: return cdiv(P.fill_count * P.nout, 4096);
     case PK_ZFWD: return P.nsx * cdiv(P.nsy, 2 * W);
     case PK_MULT1D: return cdiv(P.nsx, SF_MULT1D_MODES);
+    case PK_DERIV: {
+      const int a = ps.arg[0];
+      const int nlines = P.ax[a == 0 ? 1 : 0].nodes * P.ax[a == 2 ? 1 : 2].nodes;
+      return cdiv(nlines, 2 * W);
+    }
   }
   return 0;
 }
@@ -308,6 +313,12 @@ template <typename T> void size_pass(const Prob<T> &P, Pass<T> &ps, int wcap) {
     case PK_ZSTAGE: L = P.ax[2].L; nbuf = P.ncomp + 2; lines = P.cpath ? P.nsy : cdiv(P.nsy, 2); break;
     case PK_YSTAGE2: L = P.ax[1].L; nbuf = P.ncomp + 2; lines = P.cpath ? P.nsx : cdiv(P.nsx, 2); break;
     case PK_ZFWD: L = P.ax[2].L; lines = cdiv(P.nsy, 2); break;
+    case PK_DERIV: {
+      const int a = ps.arg[0];
+      L = P.ax[a].L;
+      lines = cdiv(P.ax[a == 0 ? 1 : 0].nodes * P.ax[a == 2 ? 1 : 2].nodes, 2);
+      break;
+    }
     case PK_FILL:
     case PK_MULT1D: ps.W = 1; ps.Wp = 1; ps.nbuf = 0; ps.bufsz = 0; return;
   }
@@ -338,10 +349,12 @@ template <typename T> struct ExecList {
   int total = 0;
   int wcap = 0;  // tile-width cap (tuning)
 
-  void add(const Prob<T> &P, int kind, int prob, int dep0 = -1, int dep1 = -1) {
+  void add(const Prob<T> &P, int kind, int prob, int dep0 = -1, int dep1 = -1, const int *args = nullptr) {
     Pass<T> ps{};
     ps.kind = kind;
     ps.prob = prob;
+    if (args)
+      for (int i = 0; i < 6; ++i) ps.arg[i] = args[i];
     size_pass<T>(P, ps, wcap);
     ps.ntiles = pass_tiles<T>(P, ps);
     ps.dep[0] = dep0;
@@ -610,6 +623,8 @@ template <typename T> struct PlanImpl : sf_plan_s {
   }
 
   sf_status adjoint(const void *gp, const void *go, void *gf) override {
+    if (!P.cpath && P.nop)
+      return fail(SF_ERR_UNSUPPORTED, "adjoint of an operator on Dirichlet / Neumann axes");
     IOArgs<T> io{};
     io.use = 1;
     for (int c = 0; c < P.ncomp; ++c) io.in[c] = gp ? (const T *)gp + c * field_elems : nullptr;
@@ -850,7 +865,6 @@ static sf_status validate(const sf_plan_desc &d) {
     return fail(SF_ERR_ARG, "green_sigma must be positive and finite");
   if (ncp && d.bc[0][0] == SF_BC_PERIODIC && (d.n[0] % 2)) return fail(SF_ERR_UNSUPPORTED, "odd periodic x length");
   if (d.op != SF_OP_NONE) {
-    if (nreal) return fail(SF_ERR_UNSUPPORTED, "spectral operators on Dirichlet/Neumann axes");
     if (d.op == SF_OP_GRAD && d.ncomp != 1) return fail(SF_ERR_ARG, "GRAD needs ncomp = 1");
     if (d.op == SF_OP_DIV && d.ncomp != d.dim) return fail(SF_ERR_ARG, "DIV needs ncomp = dim");
     if (d.op == SF_OP_CURL && d.dim == 1) return fail(SF_ERR_ARG, "CURL needs dim 2 or 3");
@@ -1000,9 +1014,34 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
     SF_TRY(build_green());
     (void)hd;
   }
+  // operators on Dirichlet / Neumann axes: dual bases (sine <-> cosine) and
+  // wavenumber units; the operator outputs are then derivative passes over psi
+  // (PK_DERIV) instead of spectral-stage outputs
+  for (int a = 0; a < 3; ++a) {
+    p.dkind[a] = p.ax[a].kind;
+    p.du0[a] = p.ax[a].u0;
+    p.dnu[a] = p.ax[a].nu;
+    p.dk0[a] = p.ax[a].k0;
+    p.dns[a] = p.ax[a].ns;
+    p.dphase[a] = p.ax[a].phase;
+    p.kunit[a] = 0;
+    if (a >= d.dim || p.cpath || d.op == SF_OP_NONE) continue;
+    static const int dual_of[10] = {AK_P, AK_U, AK_NR, AK_DR, AK_NS, AK_DS, AK_NDR, AK_NDS, AK_DNR, AK_DNS};
+    const int dk = dual_of[p.ax[a].kind];
+    AxisHost dh = build_axis(dk, d.n[a], d.lo[a], d.hi[a], d.eig, a == 0, false, d.tune_radix, d.grid == SF_GRID_REGULAR);
+    T *dph;
+    SF_TRY(mem.template upload<T>(&dph, dh.phase, true));
+    p.dkind[a] = dk;
+    p.du0[a] = dh.u0;
+    p.dnu[a] = dh.nu;
+    p.dk0[a] = dh.k0;
+    p.dns[a] = dh.ns;
+    p.dphase[a] = reinterpret_cast<const cx<T> *>(dph);
+    p.kunit[a] = (T)(2.0 * kPi / (ah[a].L * ah[a].h));
+  }
   // forward / adjoint variants
   p.nin = p.ncomp;
-  p.nout = nf;
+  p.nout = (p.cpath || d.op == SF_OP_NABLA) ? nf : p.ncomp;
   p.adjoint = 0;
   p.nrw = 0;
   PA = p;
@@ -1030,7 +1069,21 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   };
   auto back = [&](ExecList<T> &ex, const Prob<T> &Q, int dep) {
     ex.add(Q, PK_XINV, 0, dep);
+    const int xinv = (int)ex.passes.size() - 1;
     if (Q.fill_count) ex.add(Q, PK_FILL, 0);
+    if (Q.cpath || Q.op == OPK_NONE || Q.op == OPK_NABLA || Q.adjoint) return;
+    // operator outputs on Dirichlet / Neumann axes: derivative terms of psi,
+    // the terms of one output chained (the first writes, the others add)
+    for (int o = 0; o < Q.nop; ++o) {
+      int prev = -1;
+      auto term = [&](int ax, int c, int order, int sign) {
+        const int args[6] = {ax, c, o, order, sign, prev >= 0 ? 1 : 0};
+        ex.add(Q, PK_DERIV, 0, xinv, prev, args);
+        prev = (int)ex.passes.size() - 1;
+      };
+      for (int c = 0; c < Q.ncomp; ++c)
+        if (Q.opc[o][c] == 1 || Q.opc[o][c] == -1) term(Q.opa[o][c], c, 1, Q.opc[o][c]);
+    }
   };
   ex_front.wcap = ex_back.wcap = ex_all.wcap = ex_adj.wcap = d.tune_tile;
   front(ex_front, P);
@@ -1177,21 +1230,19 @@ template <typename T> struct BatchImpl : sf_plan_s {
     }
     // level-synchronous order: every problem's pass j before any pass j+1, so a
     // problem's dependency is (almost always) complete when its next pass starts
-    std::vector<std::vector<int>> kinds(n);
-    for (int i = 0; i < n; ++i) {
-      for (auto &p : plans[i]->ex_all.passes) kinds[i].push_back(p.kind);
-    }
+    std::vector<std::vector<Pass<T>>> lists(n);
+    for (int i = 0; i < n; ++i) lists[i] = plans[i]->ex_all.passes;
     std::vector<int> last(n, -1);
     ex.wcap = plans[0]->d.tune_tile;
     size_t maxlen = 0;
-    for (auto &k : kinds) maxlen = std::max(maxlen, k.size());
+    for (auto &k : lists) maxlen = std::max(maxlen, k.size());
     for (size_t lvl = 0; lvl < maxlen; ++lvl) {
       for (int i = 0; i < n; ++i) {
-        if (lvl >= kinds[i].size()) continue;
-        const int kind = kinds[i][lvl];
+        if (lvl >= lists[i].size()) continue;
+        const int kind = lists[i][lvl].kind;
         const int dep = (kind == PK_FILL) ? -1 : last[i];
         const size_t before = ex.passes.size();
-        ex.add(probs[i], kind, i, dep);
+        ex.add(probs[i], kind, i, dep, -1, lists[i][lvl].arg);
         if (ex.passes.size() > before && kind != PK_FILL) last[i] = (int)ex.passes.size() - 1;
       }
     }

@@ -248,6 +248,7 @@ enum PassKind : int {
   PK_FILL = 6,     // Dirichlet boundary-plane fill of psi (regular grids)
   PK_ZFWD = 7,     // forward-only z transform (Green's table set-up): I1 -> fwd_out
   PK_MULT1D = 8,   // 1D: multiply and operator in x-spectral space: A -> B
+  PK_DERIV = 9,    // Dirichlet / Neumann axes: one derivative term of an operator output
 };
 
 template <typename T> struct Axis {
@@ -297,6 +298,11 @@ template <typename T> struct Prob {
   int nsx, nuy, nuz, nsy, nsz;
   int gny, gnz;  // Green's table extents along y, z
   int fill_count;
+  // operators on Dirichlet / Neumann axes: the dual basis of each axis (sine <->
+  // cosine, same length and modes) and the wavenumber of FFT index 1
+  int dkind[3], du0[3], dnu[3], dk0[3], dns[3];
+  const cx<T> *dphase[3];
+  T kunit[3];
 };
 
 template <typename T> struct Pass {
@@ -309,6 +315,7 @@ template <typename T> struct Pass {
   int bufsz;  // complex elements per shared buffer
   int dep[2];
   int depcnt[2];
+  int arg[6];  // PK_DERIV: axis, psi component, output, order (1, 2), sign, accumulate
 };
 
 // executor control block (device)

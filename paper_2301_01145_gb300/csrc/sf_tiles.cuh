@@ -136,6 +136,22 @@ template <typename T> __device__ __forceinline__ T multiplier(const Prob<T> &P, 
   return lam == (T)0 ? (T)0 : P.mscale / lam;
 }
 
+// |kappa|^2 of a real-path mode (Dirichlet / Neumann axes): coefficient index ->
+// FFT index -> kunit * index per axis
+template <typename T> __device__ __forceinline__ T kap2_real(const Prob<T> &P, int kx, int ky, int kz) {
+  const T a = P.kunit[0] * (T)coef_index(P.ax[0], kx);
+  T s = a * a;
+  if (P.dim >= 2) {
+    const T b = P.kunit[1] * (T)coef_index(P.ax[1], ky);
+    s += b * b;
+  }
+  if (P.dim == 3) {
+    const T c = P.kunit[2] * (T)coef_index(P.ax[2], kz);
+    s += c * c;
+  }
+  return s;
+}
+
 // wavenumbers (Nyquist zeroed) and squared wavenumbers (Nyquist kept)
 template <typename T> struct Kap {
   T x, y, z, k2;
@@ -504,11 +520,16 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
     }
     for (int c = 0; c < ncomp; ++c) inv_field(c, c);
   } else {
-    // real path: two real lines per packed line; multiply coefficient-wise
+    // real path: two real lines per packed line; multiply coefficient-wise.
+    // NABLA (no basis change on Dirichlet / Neumann axes) is formed here as a
+    // spectral output, -|kappa|^2 psi^, in the spare buffer; first derivatives
+    // are derivative passes over psi (PK_DERIV).
     const int Wl = cdiv(nl, 2);
+    const bool nabla = P.op == OPK_NABLA && !P.adjoint;
     for (int c = 0; c < ncomp; ++c) {
       fwd_field(c, c);
       V *a = bufs[c];
+      V *an = bufs[ncomp];
       const int half = L / 2;
       const bool mixed = ak_mixed(ax.kind);
       const int cnt = Wl * (half + 1);
@@ -519,16 +540,18 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
         const V zm = a[((L - k) % L) * Wp + l];
         V ea = mk<V>((zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5);
         V eb = mk<V>((zk.y + zm.y) * (T)0.5, -(zk.x - zm.x) * (T)0.5);
-        T ma = 0, mb = 0;
+        T ma = 0, mb = 0, na = 0, nb = 0;
         V ph = czero<V>();
         if (ci >= 0 && ci < ax.ns) {
           ph = ax.phase[k];
           int kx, ky, kz;
           kof(2 * l, ci, kx, ky, kz);
           ma = multiplier<T>(P, kx, ky, kz);
+          if (nabla) na = -kap2_real<T>(P, kx, ky, kz);
           if (2 * l + 1 < nl) {
             kof(2 * l + 1, ci, kx, ky, kz);
             mb = multiplier<T>(P, kx, ky, kz);
+            if (nabla) nb = -kap2_real<T>(P, kx, ky, kz);
           }
         }
         const T ca = (ea.x * ph.x + ea.y * ph.y) * ma;
@@ -537,9 +560,15 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
         eb = cscale(ph, cb);
         a[k * Wp + l] = mk<V>(ea.x - eb.y, ea.y + eb.x);
         if (k >= 1 && k <= half - 1) a[(L - k) * Wp + l] = mk<V>(ea.x + eb.y, eb.x - ea.y);
+        if (nabla) {
+          const V fa = cscale(ea, na), fb = cscale(eb, nb);
+          an[k * Wp + l] = mk<V>(fa.x - fb.y, fa.y + fb.x);
+          if (k >= 1 && k <= half - 1) an[(L - k) * Wp + l] = mk<V>(fa.x + fb.y, fb.x - fa.y);
+        }
       }
       __syncthreads();
       inv_field(c, c);
+      if (nabla) inv_field(ncomp, ncomp + c);
     }
   }
 }
@@ -725,8 +754,8 @@ template <typename T> __device__ void tile_xinv(const Prob<T> &P, const Pass<T> 
     if (p >= nux) {  // boundary node x = 0 or x = n
       const int side = nbd == 2 ? p - nux : (dmask == 1 ? 0 : 1);
       xn = side == 0 ? 0 : X.n;
-      v = 0;
-      if (!P.adjoint && P.face[0][side]) v = P.face[0][side][(size_t)zn * ndy + yn];
+      v = 0;  // face data for psi; operator outputs (the series) vanish there
+      if (!P.adjoint && f < P.ncomp && P.face[0][side]) v = P.face[0][side][(size_t)zn * ndy + yn];
     } else {
       xn = p + X.u0;
       v = get_ext_r<T>(a, X, Wp, r, p);
@@ -766,7 +795,7 @@ template <typename T> __device__ void tile_fill(const Prob<T> &P, const Pass<T> 
       if (((zm & 1) && zn == 0) || ((zm & 2) && zn == Z.n)) continue;  // owned by the z planes
       const int yn = side == 0 ? 0 : Y.n;
       T v = 0;
-      if (!P.adjoint && P.face[1][side]) v = P.face[1][side][(size_t)zn * ndx + xn];
+      if (!P.adjoint && f < P.ncomp && P.face[1][side]) v = P.face[1][side][(size_t)zn * ndx + xn];
       dst[((size_t)zn * ndy + yn) * ndx + xn] = v;
     } else {
       g -= ny_pl;
@@ -776,7 +805,7 @@ template <typename T> __device__ void tile_fill(const Prob<T> &P, const Pass<T> 
       const int yn = g / ndx, xn = g - yn * ndx;
       const int zn = side == 0 ? 0 : Z.n;
       T v = 0;
-      if (!P.adjoint && P.face[2][side]) v = P.face[2][side][(size_t)yn * ndx + xn];
+      if (!P.adjoint && f < P.ncomp && P.face[2][side]) v = P.face[2][side][(size_t)yn * ndx + xn];
       dst[((size_t)zn * ndy + yn) * ndx + xn] = v;
     }
   }
@@ -835,8 +864,100 @@ template <typename T> __device__ void tile_mult1d(const Prob<T> &P, const Pass<T
     } else {
       const T *A = reinterpret_cast<const T *>(P.A);
       T *B = reinterpret_cast<T *>(P.B);
-      for (int c = 0; c < ncomp; ++c) __stcg(&B[(size_t)c * nk + kx], m * __ldcg(&A[(size_t)c * nk + kx]));
+      const T kap = P.kunit[0] * (T)coef_index(X, kx);
+      for (int c = 0; c < ncomp; ++c) {
+        const T v = m * __ldcg(&A[(size_t)c * nk + kx]);
+        __stcg(&B[(size_t)c * nk + kx], v);
+        if (P.op == OPK_NABLA && !P.adjoint) __stcg(&B[(size_t)(ncomp + c) * nk + kx], -kap * kap * v);
+      }
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// DERIV: one term of an operator output on Dirichlet / Neumann axes.  Along
+// axis a the solution's lines (unknown nodes) are expanded in the axis's
+// basis (forward R2R), each mode is scaled by sign * kappa (order 1) or
+// -kappa^2 (order 2), and the series is evaluated by the inverse R2R of the
+// dual basis (order 1: sine <-> cosine; the quarter-wave pair D-N <-> N-D,
+// whose doubled-axis representations differ by (-1)^m) or of the axis itself
+// (order 2) at that basis's unknown nodes; every other node of the output line
+// is zero, as are lines through regular Dirichlet face nodes of the other
+// axes (the series vanishes there).  Only modes present in both bases are
+// kept.  acc = 1 adds the term to the output instead of writing it.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
+  typedef cx<T> V;
+  const int ax = ps.arg[0], comp = ps.arg[1], o = ps.arg[2], order = ps.arg[3], sgn = ps.arg[4], acc = ps.arg[5];
+  const Axis<T> &X = P.ax[ax];
+  Axis<T> Dx = X;
+  if (order == 1) {
+    Dx.kind = P.dkind[ax];
+    Dx.u0 = P.du0[ax];
+    Dx.nu = P.dnu[ax];
+    Dx.k0 = P.dk0[ax];
+    Dx.ns = P.dns[ax];
+    Dx.phase = P.dphase[ax];
+  }
+  const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;  // the other two axes, ascending
+  const Axis<T> &B1 = P.ax[b1], &B2 = P.ax[b2];
+  const int nd0 = P.ax[0].nodes, nd1 = P.ax[1].nodes;
+  const size_t st[3] = {1, (size_t)nd0, (size_t)nd0 * nd1};
+  const int nlines = B1.nodes * B2.nodes;
+  const int W = ps.W, Wp = ps.Wp, RL = 2 * W, L = X.L, half = L / 2;
+  const int l0 = t * RL;
+  const T *src = P.out_ptr[comp];
+  T *dst = P.out_ptr[P.ncomp + o];
+  auto line_base = [&](int li, bool &inside) -> size_t {
+    const int u = li % B1.nodes, v = li / B1.nodes;
+    inside = u >= B1.u0 && u < B1.u0 + B1.nu && v >= B2.u0 && v < B2.u0 + B2.nu;
+    return (size_t)u * st[b1] + (size_t)v * st[b2];
+  };
+  V *a = sm, *b = sm + bufsz;
+  zero_buf<T>(a, L * Wp);
+  __syncthreads();
+  for (int e = threadIdx.x; e < RL * X.nu; e += blockDim.x) {
+    const int r = e / X.nu, q = e - r * X.nu, li = l0 + r;
+    if (li >= nlines) continue;
+    bool inside;
+    const size_t base = line_base(li, inside);
+    if (inside) put_ext_r<T>(a, X, Wp, r, q, src[base + (size_t)(q + X.u0) * st[ax]]);
+  }
+  __syncthreads();
+  fft_lines<T, false>(a, b, X, W, Wp);
+  const bool mixed = ak_mixed(X.kind);
+  const bool dlike = X.kind == AK_DR || X.kind == AK_DS || X.kind == AK_DNR || X.kind == AK_DNS;
+  const T invL = (T)1 / (T)L;
+  for (int e = threadIdx.x; e < W * (half + 1); e += blockDim.x) {
+    const int l = e % W, k = e / W;
+    const int ci = mixed ? ((k & 1) ? (k >> 1) : -1) : k - X.k0;
+    const int cd = mixed ? ci : k - Dx.k0;
+    V za = czero<V>(), zb = czero<V>();
+    if (ci >= 0 && ci < X.ns && cd >= 0 && cd < Dx.ns) {
+      const T kap = P.kunit[ax] * (T)k;
+      T fac;
+      if (order == 2) fac = -kap * kap * invL;
+      else fac = (T)sgn * (dlike ? kap : -kap) * ((mixed && (ci & 1)) ? (T)-1 : (T)1) * invL;
+      const T ca = coef_r<T>(a, X, Wp, 2 * l, ci) * fac, cb = coef_r<T>(a, X, Wp, 2 * l + 1, ci) * fac;
+      const V ph = Dx.phase[k];
+      const V ea = cscale(ph, ca), eb = cscale(ph, cb);
+      za = mk<V>(ea.x - eb.y, ea.y + eb.x);
+      zb = mk<V>(ea.x + eb.y, eb.x - ea.y);
+    }
+    b[k * Wp + l] = za;
+    if (k >= 1 && k <= half - 1) b[(L - k) * Wp + l] = zb;
+  }
+  __syncthreads();
+  fft_lines<T, true>(b, a, Dx, W, Wp);
+  for (int e = threadIdx.x; e < RL * X.nodes; e += blockDim.x) {
+    const int r = e / X.nodes, j = e - r * X.nodes, li = l0 + r;
+    if (li >= nlines) continue;
+    bool inside;
+    const size_t idx = line_base(li, inside) + (size_t)j * st[ax];
+    T v = 0;
+    if (inside && j >= Dx.u0 && j < Dx.u0 + Dx.nu) v = get_ext_r<T>(b, Dx, Wp, r, j - Dx.u0);
+    if (acc) dst[idx] += v;
+    else dst[idx] = v;
   }
 }
 
@@ -852,6 +973,7 @@ template <typename T> __device__ void run_tile(const Prob<T> &P, const Pass<T> &
     case PK_FILL: tile_fill<T>(P, ps, t); break;
     case PK_ZFWD: tile_zfwd<T>(P, ps, t, sm, bufsz); break;
     case PK_MULT1D: tile_mult1d<T>(P, ps, t); break;
+    case PK_DERIV: tile_deriv<T>(P, ps, t, sm, bufsz); break;
     default: break;
   }
 }

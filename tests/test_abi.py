@@ -86,7 +86,7 @@ def test_status_strings_and_version(lib):
     (dict(bc="UUU", grid="regular", n=(1100, 16, 16)), -2),  # regular unbounded: pad 2n+1 > 2048
     (dict(bc="UUU", sigma=0.0), -1),
     (dict(op="CURL", ncomp=1), -1),
-    (dict(op="GRAD", bc="DDD"), -2),
+    (dict(op="CURL", bc="DDD", ncomp=1), -1),  # curl in 3D needs three components
     (dict(tune_radix=3), -1),
     (dict(tune_tile=3), -1),
     (dict(tune_slab=-1), -1),

@@ -1,0 +1,166 @@
+"""GPU parity of the spectral operators on Dirichlet / Neumann axes (GRAD, DIV,
+CURL, NABLA as derivatives of the basis series, sine <-> cosine) against the
+FP64 oracle: 1D, 2D and 3D, regular and staggered grids, every face kind
+including the quarter-wave pairs, PS and FD2 (with inhomogeneous faces), FP32
+and FP64, the fused and unfused executors, a batch, and the refused adjoint.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle.desc import Desc
+from tests.gpu_helpers import TOL, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built(gpu_available):
+    import __graft_entry__ as g
+    g.build()
+
+
+def make(dim, n, bc, grid, eig, op, ncomp, prec, fused=True, rhs_scale=0.9):
+    import paper_2301_01145_gb300 as sf
+    lo, hi = (0.0,) * dim, (1.0, 1.4, 0.8)[:dim]
+    plan = sf.Plan(dim, n, lo, hi, list(bc), grid=grid, eig=eig, op=op, ncomp=ncomp, prec=prec, fused=fused,
+                   rhs_scale=rhs_scale)
+    d = Desc(dim, tuple(n), lo, hi, tuple(bc), grid == "staggered", eig, op, ncomp, rhs_scale, 0.0)
+    return plan, d
+
+
+# First derivatives on Dirichlet / Neumann axes differentiate the computed psi
+# (a derivative pass over it).  psi carries the rounding of several passes,
+# white across the modes at a few units u of the working precision, and the
+# derivative weights it by kappa.  Relative to a derivative dominated by the
+# lowest mode the error is therefore O(u kappa_max / kappa_1), and
+# kappa_max / kappa_1 is about n for n nodes (about 2 n on a quarter-wave D-N /
+# N-D axis, whose lowest mode is 1/2).  The bound is 2 u times that ratio on the
+# largest axis, never tighter than the stated target: 1e-5 FP32 up to 83 nodes
+# (42 quarter-wave), 6e-5 at 512; FP64 stays at 1e-12.  NABLA is formed in
+# spectral space and keeps the stated target.
+UNIT = {"f32": 2.0 ** -24, "f64": 2.0 ** -53}
+
+
+def op_tol(d, prec):
+    if d.op == "NABLA":
+        return TOL[prec]
+    ratio = max(d.nodes(a) * (2 if d.bc[a] in ("DN", "ND") else 1) for a in range(d.dim))
+    return max(TOL[prec], 2.0 * UNIT[prec] * ratio)
+
+
+def check(plan, d, f, prec, faces=None):
+    psi, opo = plan.empty_outputs()
+    if faces:
+        for (ax, side), g in faces.items():
+            plan.set_boundary(ax, side, to_dev(g, prec))
+    plan.execute(to_dev(f, prec), psi, opo)
+    plan.sync()
+    rp, ro = oracle.solve(d, f, faces)
+    for c in range(rp.shape[0]):
+        assert rel_l2(to_np(psi)[c], rp[c]) <= TOL[prec]
+    for o in range(ro.shape[0]):
+        assert rel_l2(to_np(opo)[o], ro[o]) <= op_tol(d, prec), o
+
+
+OPS3 = [("GRAD", 1), ("DIV", 3), ("CURL", 3), ("NABLA", 2)]
+BCS3 = [("D", "N", "DN"), ("ND", "D", "N"), ("N", "DN", "ND")]
+
+
+@pytest.mark.parametrize("op,ncomp", OPS3, ids=[o for o, _ in OPS3])
+@pytest.mark.parametrize("bc", BCS3, ids=lambda b: "-".join(b))
+@pytest.mark.parametrize("grid", ["regular", "staggered"])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_ops_3d(op, ncomp, bc, grid, prec):
+    n = (12, 16, 8)
+    plan, d = make(3, n, bc, grid, "PS", op, ncomp, prec)
+    f = np.random.default_rng(11).normal(size=(ncomp,) + d.shape())
+    check(plan, d, f, prec)
+    plan.close()
+
+
+@pytest.mark.parametrize("op,ncomp", [("GRAD", 1), ("DIV", 2), ("CURL", 1), ("NABLA", 1)])
+@pytest.mark.parametrize("bc", [("D", "N"), ("DN", "ND"), ("N", "N"), ("D", "D")], ids=lambda b: "-".join(b))
+@pytest.mark.parametrize("grid", ["regular", "staggered"])
+@pytest.mark.parametrize("eig", ["PS", "FD2"])
+def test_ops_2d(op, ncomp, bc, grid, eig):
+    n = (48, 24)
+    plan, d = make(2, n, bc, grid, eig, op, ncomp, "f32")
+    f = np.random.default_rng(5).normal(size=(ncomp,) + d.shape())
+    check(plan, d, f, "f32")
+    plan.close()
+
+
+@pytest.mark.parametrize("op", ["GRAD", "NABLA"])
+@pytest.mark.parametrize("bc", ["D", "N", "DN", "ND"])
+@pytest.mark.parametrize("grid", ["regular", "staggered"])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_ops_1d(op, bc, grid, prec):
+    plan, d = make(1, (96,), (bc,), grid, "PS", op, 1, prec)
+    f = np.random.default_rng(6).normal(size=(1,) + d.shape())
+    check(plan, d, f, prec)
+    plan.close()
+
+
+@pytest.mark.parametrize("bc", [("D", "DN", "D"), ("DN", "D", "ND")], ids=lambda b: "-".join(b))
+@pytest.mark.parametrize("grid", ["regular", "staggered"])
+@pytest.mark.parametrize("fused", [True, False])
+def test_grad_fd2_inhomogeneous_faces(bc, grid, fused):
+    import paper_2301_01145_gb300 as sf
+    n = (16, 12, 24)
+    man = workloads.manufactured(seed_index=17)
+    case = workloads.bounded_case(man, n, bc, grid == "staggered")
+    plan = sf.Plan(3, n, (0.0,) * 3, (1.0,) * 3, list(bc), grid=grid, eig="FD2", op="GRAD", fused=fused)
+    d = Desc(3, n, (0.0,) * 3, (1.0,) * 3, bc, grid == "staggered", "FD2", "GRAD", 1, 1.0, 0.0)
+    check(plan, d, case["f"][None], "f32", case["faces"])
+    plan.close()
+
+
+def test_larger_2d_grad():
+    plan, d = make(2, (512, 384), ("N", "D"), "staggered", "PS", "GRAD", 1, "f32")
+    f = np.random.default_rng(7).normal(size=(1,) + d.shape())
+    check(plan, d, f, "f32")
+    plan.close()
+
+
+def test_bounded_op_plans_in_a_batch():
+    import torch
+    import paper_2301_01145_gb300 as sf
+    plans, ds, fs, outs = [], [], [], []
+    for i, (dim, n, bc, op, nc) in enumerate([(3, (8, 12, 6), ("D", "N", "D"), "CURL", 3),
+                                              (2, (24, 16), ("DN", "N"), "GRAD", 1),
+                                              (1, (48,), ("ND",), "NABLA", 1),
+                                              (2, (16, 16), ("P", "P"), "GRAD", 1)]):
+        plan, d = make(dim, n, bc, "regular" if i % 2 == 0 else "staggered", "PS", op, nc, "f32")
+        if bc == ("P", "P"):
+            plan.close()
+            plan, d = make(dim, n, bc, "staggered", "PS", op, nc, "f32")
+        f = np.random.default_rng(20 + i).normal(size=(nc,) + d.shape())
+        plans.append(plan)
+        ds.append(d)
+        fs.append(to_dev(f, "f32"))
+        outs.append(plan.empty_outputs())
+    batch = sf.Batch(plans)
+    batch.solve(fs, [o[0] for o in outs], [o[1] for o in outs])
+    batch.sync()
+    for i, plan in enumerate(plans):
+        psi, opo = plan(fs[i])
+        plan.sync()
+        assert torch.equal(psi, outs[i][0]) and torch.equal(opo, outs[i][1])
+        rp, ro = oracle.solve(ds[i], to_np(fs[i]))
+        for o in range(ro.shape[0]):
+            assert rel_l2(to_np(opo)[o], ro[o]) <= op_tol(ds[i], "f32")
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def test_adjoint_with_bounded_operator_is_refused():
+    from paper_2301_01145_gb300 import _lib
+    plan, d = make(2, (16, 16), ("D", "N"), "staggered", "PS", "GRAD", 1, "f32")
+    g = to_dev(np.zeros((1,) + d.shape()), "f32")
+    with pytest.raises(_lib.SolverError) as e:
+        plan.adjoint(g, to_dev(np.zeros((2,) + d.shape()), "f32"))
+    assert e.value.status == -2  # SF_ERR_UNSUPPORTED
+    plan.close()
