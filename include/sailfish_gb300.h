@@ -107,7 +107,11 @@ typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
  *              periodic/unbounded, or every axis is Dirichlet/Neumann.
  *   grid       REGULAR (N_c + 1 nodes per axis) or STAGGERED (N_c cell centres).
  *   eig        PS or FD2 (bounded axes; ignored when unbounded).
- *   op         spectral operator on psi; needs periodic or unbounded axes.
+ *   op         spectral operator on psi.  On Dirichlet / Neumann axes a
+ *              derivative differentiates the axis's sine / cosine series
+ *              (sine <-> cosine) and is evaluated at every node (zero where the
+ *              series vanishes); sf_solve_adjoint then returns
+ *              SF_ERR_UNSUPPORTED.
  *              GRAD: ncomp 1 -> dim outputs.  DIV: ncomp = dim -> 1 output.
  *              CURL: 3D ncomp 3 -> 3 outputs; 2D ncomp 1 -> 2 outputs; not 1D.
  *              NABLA: ncomp -> ncomp outputs.  In 1D, GRAD and DIV are d/dx.
