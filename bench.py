@@ -405,6 +405,37 @@ def run_other(args):
         points, dtype = n ** 3, "f32"
         cfg = {"workload": "3D Dirichlet/Neumann/Dirichlet Poisson, 256^3 cells regular grid on the unit cube, "
                            "FD2 eigenvalues, inhomogeneous faces (manufactured sin/cos solution)", "grid": n}
+    elif args.workload == "c6":
+        n = 256
+        man = workloads.manufactured(seed_index=1)
+        case = workloads.bounded_case(man, (n, n, n), ("D", "N", "D"), False)
+        plan = sf.Plan(3, (n,) * 3, (0,) * 3, (1,) * 3, "DND", grid="regular", eig="FD2", op="GRAD", prec="f32")
+        for (ax, side), g in case["faces"].items():
+            plan.set_boundary(ax, side, dev(g))
+        f = dev(case["f"][None])
+        psi, grad = plan.empty_outputs()
+        step = lambda: plan.execute(f, psi, grad)
+        points, dtype = n ** 3, "f32"
+        cfg = {"workload": "3D Dirichlet/Neumann/Dirichlet Poisson 256^3 regular grid, FD2, inhomogeneous faces, "
+                           "plus the gradient on the bounded axes (three derivative passes over psi)", "grid": n}
+    elif args.workload == "c7":
+        rng = np.random.default_rng(7)
+        kinds = ["P", "D", "N", "DN", "ND", "U"]
+        plans, fs, ps = [], [], []
+        for i in range(1024):
+            bc = kinds[i % len(kinds)]
+            n1 = int(rng.choice([256, 384, 512])) if len(bc) == 1 else int(rng.choice([128, 256]))
+            grid = "staggered" if i % 2 == 0 or bc == "P" else "regular"
+            plans.append(sf.Plan(1, (n1,), (-0.5,), (0.5,), [bc], grid=grid, eig="PS",
+                                 kernel="SPECT" if bc == "U" else "G2", rhs_scale=-1.0 if bc == "U" else 1.0))
+            fs.append(dev(rng.normal(size=plans[-1].in_shape)))
+            ps.append(plans[-1].empty_outputs()[0])
+        batch = sf.Batch(plans)
+        step = lambda: batch.solve(fs, ps)
+        points, dtype = sum(int(np.prod(p.out_shape[1:])) for p in plans), "f32"
+        cfg = {"workload": "1024 uneven 1D problems (periodic, Dirichlet, Neumann, D-N, N-D, unbounded with the "
+                           "1D spectral kernel; 128..512 cells; both grids) in one persistent launch",
+               "problems": 1024, "points_per_step": points}
     elif args.workload == "c5":
         from paper_2301_01145_gb300.autograd import poisson_solve
         n = 128
@@ -477,10 +508,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--unfused", action="store_true")
     ap.add_argument("--n", type=int, default=N)
-    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5", "c6", "c7"],
                     help="c3 (default): the headline 256^3 unbounded curl solve; the others time the remaining "
                          "configurations (64^3 periodic FP64, 256^3 mixed D/N FD2, 512-problem batch, "
-                         "differentiable 128^3) and print their own line")
+                         "differentiable 128^3, 256^3 D/N FD2 with the gradient, 1024 batched 1D problems) "
+                         "and print their own line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
