@@ -39,8 +39,10 @@ __device__ __forceinline__ void load_prob(Prob<T> &dst, const Prob<T> *src, cons
 }
 
 // one launch = one pass; blockIdx.x is the tile
+// Both executors run two CTAs per SM (the shared-memory budget of a pass is
+// sized for that), so their register use is held to 65536 / (2 SF_THREADS).
 template <typename T>
-__global__ void __launch_bounds__(SF_THREADS) k_pass(const Prob<T> *probs, const Pass<T> *passes, int pass_idx, IOArgs<T> io) {
+__global__ void __launch_bounds__(SF_THREADS, 2) k_pass(const Prob<T> *probs, const Pass<T> *passes, int pass_idx, IOArgs<T> io) {
   extern __shared__ __align__(16) unsigned char sf_smem[];
   __shared__ __align__(16) Prob<T> sP;
   __shared__ Pass<T> sPass;
@@ -73,7 +75,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // depends on CTA residency.  A wait that gives up records SF_ERR_TIMEOUT and
 // the item is skipped (its counter still advances so nothing else hangs).
 template <typename T>
-__global__ void __launch_bounds__(SF_THREADS)
+__global__ void __launch_bounds__(SF_THREADS, 2)
     k_exec(const Prob<T> *probs, const Pass<T> *passes, const int *pass_start, int npass, unsigned *done, ExecCtl *ctl,
            unsigned *sticky, unsigned long long timeout_ns, IOArgs<T> io) {
   extern __shared__ __align__(16) unsigned char sf_smem[];
