@@ -913,11 +913,17 @@ template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T>
     inside = u >= B1.u0 && u < B1.u0 + B1.nu && v >= B2.u0 && v < B2.u0 + B2.nu;
     return (size_t)u * st[b1] + (size_t)v * st[b2];
   };
+  // x derivatives walk along the contiguous lines; y and z derivatives take
+  // consecutive lines (consecutive x) on consecutive threads, so that every
+  // warp access covers contiguous memory
+  const bool line_fast = ax != 0;
   V *a = sm, *b = sm + bufsz;
   zero_buf<T>(a, L * Wp);
   __syncthreads();
   for (int e = threadIdx.x; e < RL * X.nu; e += blockDim.x) {
-    const int r = e / X.nu, q = e - r * X.nu, li = l0 + r;
+    const int r = line_fast ? e % RL : e / X.nu;
+    const int q = line_fast ? e / RL : e - r * X.nu;
+    const int li = l0 + r;
     if (li >= nlines) continue;
     bool inside;
     const size_t base = line_base(li, inside);
@@ -950,7 +956,9 @@ template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T>
   __syncthreads();
   fft_lines<T, true>(b, a, Dx, W, Wp);
   for (int e = threadIdx.x; e < RL * X.nodes; e += blockDim.x) {
-    const int r = e / X.nodes, j = e - r * X.nodes, li = l0 + r;
+    const int r = line_fast ? e % RL : e / X.nodes;
+    const int j = line_fast ? e / RL : e - r * X.nodes;
+    const int li = l0 + r;
     if (li >= nlines) continue;
     bool inside;
     const size_t idx = line_base(li, inside) + (size_t)j * st[ax];
