@@ -13,7 +13,9 @@ by its plain (non-conjugate) transpose.  For y = Re(B x) with real x and g,
 real part once at the end.  Per-axis transposes:
   DFT matrix:     symmetric, so DFT^T = DFT and (DFT^-1)^T = DFT^-1;
   R2R matrices:   the explicit matrix of r2r.py, transposed;
-  multipliers:    diagonal (unchanged); operator matrices transposed per mode.
+  multipliers:    diagonal (unchanged); operator matrices transposed per mode;
+  operators on Dirichlet / Neumann axes: a linear map of psi (bounded_ops.py),
+                  transposed as a dense matrix.
 
 Pinned in tests/test_oracle_adjoint.py: the dense matrix of the forward map,
 built column by column, transposed and applied, and <A x, y> = <x, A^T y>.
@@ -22,7 +24,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import bounded, fft, ops, r2r
+from . import bounded, bounded_ops, fft, ops, r2r
 from .desc import Desc
 from .unbounded import _check, green_hat, multipliers
 
@@ -31,6 +33,21 @@ def _apply_matrix_T(kind: str, x: np.ndarray, axis: int, scale: float = 1.0) -> 
     xm = np.moveaxis(x, axis, -1)
     m = r2r.matrix(kind, xm.shape[-1]) * scale
     return np.moveaxis(xm @ m, -1, axis)  # (M^T applied) = x @ M
+
+
+def _bounded_op_transpose(desc: Desc, g_op) -> np.ndarray:
+    """D^T g_op for the operator D = bounded_ops.apply on [ncomp][nodes...]."""
+    shape_psi = (desc.ncomp,) + desc.shape()
+    size = int(np.prod(shape_psi))
+    nop = desc.op_components()
+    go = np.asarray(g_op, dtype=np.float64).reshape(nop, -1)
+    out = np.zeros(size)
+    for i in range(size):  # column i of D: its response to the unit field e_i
+        e = np.zeros(size)
+        e[i] = 1.0
+        col = bounded_ops.apply(desc, e.reshape(shape_psi)).reshape(nop, -1)
+        out[i] = np.sum(col * go)
+    return out.reshape(shape_psi)
 
 
 def _bounded_adjoint(desc: Desc, g_psi, g_op):
@@ -62,8 +79,14 @@ def _bounded_adjoint(desc: Desc, g_psi, g_op):
                 out = _apply_matrix_T(r2r.FORWARD[(desc.bc[ax], desc.staggered)], out, nax)
         return out
 
+    periodic = all(b == "P" for b in desc.bc[:dim])
+    if desc.op != "NONE" and g_op is not None and not periodic:
+        # Dirichlet / Neumann axes: the operator is a linear map D of psi
+        # (bounded_ops.py), so dL/dpsi gains D^T g_op; D^T is the transposed
+        # dense matrix of that map (small grids only)
+        gp = gp + _bounded_op_transpose(desc, g_op)
     acc = inv_T(gp[usl])
-    if desc.op != "NONE" and g_op is not None:
+    if desc.op != "NONE" and g_op is not None and periodic:
         nop = desc.op_components()
         go = np.asarray(g_op, dtype=np.float64).reshape((nop,) + desc.shape())
         gh = inv_T(go[usl])

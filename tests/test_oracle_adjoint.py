@@ -31,6 +31,12 @@ CASES = [
     Desc(2, (8, 6), (0,) * 2, (1,) * 2, ("P",) * 2, True, "FD2", op="DIV", ncomp=2),
     Desc(3, (4, 3, 4), (0,) * 3, (1,) * 3, ("DN", "N", "ND"), False, "FD2", rhs_scale=0.5),
     Desc(2, (5, 4), (0,) * 2, (1, 2), ("ND", "DN"), True, "PS"),
+    # operators on Dirichlet / Neumann axes (derivatives of the basis series)
+    Desc(3, (4, 3, 4), (0,) * 3, (1,) * 3, ("D", "N", "DN"), False, "FD2", op="GRAD", ncomp=1),
+    Desc(2, (5, 4), (0,) * 2, (1, 2), ("ND", "DN"), True, "PS", op="CURL", ncomp=1),
+    Desc(2, (6, 4), (0,) * 2, (1, 1.5), ("D", "N"), False, "PS", op="NABLA", ncomp=1, rhs_scale=0.7),
+    Desc(3, (4, 4, 3), (0,) * 3, (1,) * 3, ("N", "D", "N"), True, "PS", op="DIV", ncomp=3),
+    Desc(1, (8,), (0.0,), (1.0,), ("DN",), False, "PS", op="GRAD", ncomp=1),
 ]
 
 
