@@ -110,8 +110,7 @@ typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
  *   op         spectral operator on psi.  On Dirichlet / Neumann axes a
  *              derivative differentiates the axis's sine / cosine series
  *              (sine <-> cosine) and is evaluated at every node (zero where the
- *              series vanishes); sf_solve_adjoint then returns
- *              SF_ERR_UNSUPPORTED.
+ *              series vanishes).
  *              GRAD: ncomp 1 -> dim outputs.  DIV: ncomp = dim -> 1 output.
  *              CURL: 3D ncomp 3 -> 3 outputs; 2D ncomp 1 -> 2 outputs; not 1D.
  *              NABLA: ncomp -> ncomp outputs.  In 1D, GRAD and DIV are d/dx.

@@ -567,6 +567,12 @@ template <typename T> struct PlanImpl : sf_plan_s {
   Prob<T> PA{};  // adjoint problem
   Prob<T> *d_probs = nullptr;  // [0] forward, [1] adjoint
   ExecList<T> ex_front, ex_back, ex_all, ex_adj;
+  // first-derivative operators on Dirichlet / Neumann axes: the adjoint first
+  // forms h = g_psi + D^T g_op (derivative passes, ex_adjop) and then runs the
+  // transposed solve on h
+  ExecList<T> ex_adjop;
+  T *adj_h = nullptr;
+  bool deriv_ops = false;
   ExecCtl *ctl = nullptr;
   unsigned *sticky = nullptr;
   const T *faces[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
@@ -623,8 +629,22 @@ template <typename T> struct PlanImpl : sf_plan_s {
   }
 
   sf_status adjoint(const void *gp, const void *go, void *gf) override {
-    if (!P.cpath && P.nop)
-      return fail(SF_ERR_UNSUPPORTED, "adjoint of an operator on Dirichlet / Neumann axes");
+    if (deriv_ops) {
+      // h = g_psi + D^T g_op, then the transposed solve of h
+      const size_t hb = (size_t)P.ncomp * field_elems * sizeof(T);
+      if (gp) SF_CK(cudaMemcpyAsync(adj_h, gp, hb, cudaMemcpyDeviceToDevice, stream));
+      else SF_CK(cudaMemsetAsync(adj_h, 0, hb, stream));
+      if (go) {
+        IOArgs<T> hio{};
+        hio.use = 1;
+        for (int o = 0; o < P.nop; ++o) hio.in[P.ncomp + o] = (const T *)go + o * field_elems;
+        for (int c = 0; c < P.ncomp; ++c) hio.out[c] = adj_h + c * field_elems;
+        hio.has_face = 0;
+        SF_TRY(launch_list<T>(ex_adjop, d_probs, fused(), stream, ctl, sticky, hio, nullptr));
+      }
+      gp = adj_h;
+      go = nullptr;
+    }
     IOArgs<T> io{};
     io.use = 1;
     for (int c = 0; c < P.ncomp; ++c) io.in[c] = gp ? (const T *)gp + c * field_elems : nullptr;
@@ -1045,7 +1065,8 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   p.adjoint = 0;
   p.nrw = 0;
   PA = p;
-  PA.nin = nf;
+  deriv_ops = !p.cpath && d.op != SF_OP_NONE && d.op != SF_OP_NABLA;
+  PA.nin = deriv_ops ? p.ncomp : nf;  // derivative operators: their gradients enter through h
   PA.nout = p.ncomp;
   PA.adjoint = 1;
   for (int a = 0; a < d.dim; ++a)
@@ -1095,6 +1116,22 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
     front(ex, PA);
     back(ex, PA, (int)ex.passes.size() - 1);
     for (auto &ps : ex.passes) ps.prob = 0;  // d_probs + 1 is passed for the adjoint
+  }
+  if (deriv_ops) {
+    // transposed derivative terms, all accumulating into h (chained)
+    ex_adjop.wcap = d.tune_tile;
+    int prev = -1;
+    for (int o = 0; o < p.nop; ++o)
+      for (int c = 0; c < p.ncomp; ++c)
+        if (p.opc[o][c] == 1 || p.opc[o][c] == -1) {
+          const int args[6] = {p.opa[o][c], c, o, 3, p.opc[o][c], 1};
+          ex_adjop.add(p, PK_DERIV, 0, prev, -1, args);
+          prev = (int)ex_adjop.passes.size() - 1;
+        }
+    SF_TRY(ex_adjop.upload(mem));
+    void *hb;
+    SF_TRY(mem.alloc(&hb, (size_t)p.ncomp * field_elems * sizeof(T)));
+    adj_h = (T *)hb;
   }
   SF_TRY(ex_front.upload(mem));
   SF_TRY(ex_back.upload(mem));

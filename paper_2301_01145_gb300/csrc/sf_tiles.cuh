@@ -526,8 +526,10 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
     // are derivative passes over psi (PK_DERIV).
     const int Wl = cdiv(nl, 2);
     const bool nabla = P.op == OPK_NABLA && !P.adjoint;
+    const bool nabla_adj = P.op == OPK_NABLA && P.adjoint;  // psi gradient += -|kappa|^2 (operator gradient)
     for (int c = 0; c < ncomp; ++c) {
       fwd_field(c, c);
+      if (nabla_adj) fwd_field(ncomp + c, ncomp);
       V *a = bufs[c];
       V *an = bufs[ncomp];
       const int half = L / 2;
@@ -554,8 +556,22 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
             if (nabla) nb = -kap2_real<T>(P, kx, ky, kz);
           }
         }
-        const T ca = (ea.x * ph.x + ea.y * ph.y) * ma;
-        const T cb = (eb.x * ph.x + eb.y * ph.y) * mb;
+        T ca = ea.x * ph.x + ea.y * ph.y;
+        T cb = eb.x * ph.x + eb.y * ph.y;
+        if (nabla_adj && ci >= 0 && ci < ax.ns) {
+          const V gk = an[k * Wp + l], gm = an[((L - k) % L) * Wp + l];
+          const V ga = mk<V>((gk.x + gm.x) * (T)0.5, (gk.y - gm.y) * (T)0.5);
+          const V gb = mk<V>((gk.y + gm.y) * (T)0.5, -(gk.x - gm.x) * (T)0.5);
+          int kx, ky, kz;
+          kof(2 * l, ci, kx, ky, kz);
+          ca -= kap2_real<T>(P, kx, ky, kz) * (ga.x * ph.x + ga.y * ph.y);
+          if (2 * l + 1 < nl) {
+            kof(2 * l + 1, ci, kx, ky, kz);
+            cb -= kap2_real<T>(P, kx, ky, kz) * (gb.x * ph.x + gb.y * ph.y);
+          }
+        }
+        ca *= ma;
+        cb *= mb;
         ea = cscale(ph, ca);
         eb = cscale(ph, cb);
         a[k * Wp + l] = mk<V>(ea.x - eb.y, ea.y + eb.x);
@@ -866,7 +882,9 @@ template <typename T> __device__ void tile_mult1d(const Prob<T> &P, const Pass<T
       T *B = reinterpret_cast<T *>(P.B);
       const T kap = P.kunit[0] * (T)coef_index(X, kx);
       for (int c = 0; c < ncomp; ++c) {
-        const T v = m * __ldcg(&A[(size_t)c * nk + kx]);
+        T g = __ldcg(&A[(size_t)c * nk + kx]);
+        if (P.op == OPK_NABLA && P.adjoint) g -= kap * kap * __ldcg(&A[(size_t)(ncomp + c) * nk + kx]);
+        const T v = m * g;
         __stcg(&B[(size_t)c * nk + kx], v);
         if (P.op == OPK_NABLA && !P.adjoint) __stcg(&B[(size_t)(ncomp + c) * nk + kx], -kap * kap * v);
       }
@@ -889,9 +907,10 @@ template <typename T> __device__ void tile_mult1d(const Prob<T> &P, const Pass<T
 template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
   typedef cx<T> V;
   const int ax = ps.arg[0], comp = ps.arg[1], o = ps.arg[2], order = ps.arg[3], sgn = ps.arg[4], acc = ps.arg[5];
+  const bool adj = order == 3;  // transpose of the first derivative: dual basis in, own basis out
   const Axis<T> &X = P.ax[ax];
   Axis<T> Dx = X;
-  if (order == 1) {
+  if (order != 2) {
     Dx.kind = P.dkind[ax];
     Dx.u0 = P.du0[ax];
     Dx.nu = P.dnu[ax];
@@ -899,6 +918,8 @@ template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T>
     Dx.ns = P.dns[ax];
     Dx.phase = P.dphase[ax];
   }
+  const Axis<T> &Af = adj ? Dx : X;  // basis of the input lines (forward transform)
+  const Axis<T> &Ai = adj ? X : Dx;  // basis of the output lines (inverse transform)
   const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;  // the other two axes, ascending
   const Axis<T> &B1 = P.ax[b1], &B2 = P.ax[b2];
   const int nd0 = P.ax[0].nodes, nd1 = P.ax[1].nodes;
@@ -906,8 +927,9 @@ template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T>
   const int nlines = B1.nodes * B2.nodes;
   const int W = ps.W, Wp = ps.Wp, RL = 2 * W, L = X.L, half = L / 2;
   const int l0 = t * RL;
-  const T *src = P.out_ptr[comp];
-  T *dst = P.out_ptr[P.ncomp + o];
+  // forward: psi_comp -> operator output o; adjoint: gradient of output o -> h_comp
+  const T *src = adj ? P.in_ptr[P.ncomp + o] : P.out_ptr[comp];
+  T *dst = adj ? P.out_ptr[comp] : P.out_ptr[P.ncomp + o];
   auto line_base = [&](int li, bool &inside) -> size_t {
     const int u = li % B1.nodes, v = li / B1.nodes;
     inside = u >= B1.u0 && u < B1.u0 + B1.nu && v >= B2.u0 && v < B2.u0 + B2.nu;
@@ -920,17 +942,20 @@ template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T>
   V *a = sm, *b = sm + bufsz;
   zero_buf<T>(a, L * Wp);
   __syncthreads();
-  for (int e = threadIdx.x; e < RL * X.nu; e += blockDim.x) {
-    const int r = line_fast ? e % RL : e / X.nu;
-    const int q = line_fast ? e / RL : e - r * X.nu;
+  for (int e = threadIdx.x; e < RL * Af.nu; e += blockDim.x) {
+    const int r = line_fast ? e % RL : e / Af.nu;
+    const int q = line_fast ? e / RL : e - r * Af.nu;
     const int li = l0 + r;
     if (li >= nlines) continue;
     bool inside;
     const size_t base = line_base(li, inside);
-    if (inside) put_ext_r<T>(a, X, Wp, r, q, src[base + (size_t)(q + X.u0) * st[ax]]);
+    if (!inside) continue;
+    T v = src[base + (size_t)(q + Af.u0) * st[ax]];
+    if (adj && nr_node(Af.kind, q, Af.nu)) v *= (T)2;  // transpose of the forward end-point weights
+    put_ext_r<T>(a, Af, Wp, r, q, v);
   }
   __syncthreads();
-  fft_lines<T, false>(a, b, X, W, Wp);
+  fft_lines<T, false>(a, b, Af, W, Wp);
   const bool mixed = ak_mixed(X.kind);
   const bool dlike = X.kind == AK_DR || X.kind == AK_DS || X.kind == AK_DNR || X.kind == AK_DNS;
   const T invL = (T)1 / (T)L;
@@ -944,8 +969,9 @@ template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T>
       T fac;
       if (order == 2) fac = -kap * kap * invL;
       else fac = (T)sgn * (dlike ? kap : -kap) * ((mixed && (ci & 1)) ? (T)-1 : (T)1) * invL;
-      const T ca = coef_r<T>(a, X, Wp, 2 * l, ci) * fac, cb = coef_r<T>(a, X, Wp, 2 * l + 1, ci) * fac;
-      const V ph = Dx.phase[k];
+      const int cf = adj ? cd : ci;
+      const T ca = coef_r<T>(a, Af, Wp, 2 * l, cf) * fac, cb = coef_r<T>(a, Af, Wp, 2 * l + 1, cf) * fac;
+      const V ph = Ai.phase[k];
       const V ea = cscale(ph, ca), eb = cscale(ph, cb);
       za = mk<V>(ea.x - eb.y, ea.y + eb.x);
       zb = mk<V>(ea.x + eb.y, eb.x - ea.y);
@@ -954,7 +980,7 @@ template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T>
     if (k >= 1 && k <= half - 1) b[(L - k) * Wp + l] = zb;
   }
   __syncthreads();
-  fft_lines<T, true>(b, a, Dx, W, Wp);
+  fft_lines<T, true>(b, a, Ai, W, Wp);
   for (int e = threadIdx.x; e < RL * X.nodes; e += blockDim.x) {
     const int r = line_fast ? e % RL : e / X.nodes;
     const int j = line_fast ? e / RL : e - r * X.nodes;
@@ -963,7 +989,10 @@ template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T>
     bool inside;
     const size_t idx = line_base(li, inside) + (size_t)j * st[ax];
     T v = 0;
-    if (inside && j >= Dx.u0 && j < Dx.u0 + Dx.nu) v = get_ext_r<T>(b, Dx, Wp, r, j - Dx.u0);
+    if (inside && j >= Ai.u0 && j < Ai.u0 + Ai.nu) {
+      v = get_ext_r<T>(b, Ai, Wp, r, j - Ai.u0);
+      if (adj && nr_node(Ai.kind, j - Ai.u0, Ai.nu)) v *= (T)0.5;
+    }
     if (acc) dst[idx] += v;
     else dst[idx] = v;
   }
