@@ -3,6 +3,8 @@
   * C1 (64^3 periodic FP64) is covered element by element in test_gpu_parity.py.
   * C2 (257^3 regular nodes, Dirichlet/Neumann/Dirichlet, FD2, inhomogeneous
     faces, FP32): the full oracle is affordable, element by element.
+  * The same C2 solve with the gradient on its bounded axes (three derivative
+    passes over psi), element by element.
   * C3 (256^3 unbounded, 3 components, curl, FP32, register fast path with
     the slab-pipelined executor): psi and u at sampled output points computed
     one by one by the oracle's direct sums.
@@ -64,6 +66,28 @@ def test_c2_fullsize_elementwise():
     assert rel_l2(to_np(psi)[0], ref[0]) <= TOL["f32"]
     # and the discretisation error of the FD2 solve is the expected O(h^2) size
     assert np.max(np.abs(to_np(psi)[0] - case["psi_exact"])) < 2e-3
+    plan.close()
+
+
+def test_c6_fullsize_gradient_on_bounded_axes_elementwise():
+    # the 256^3 D/N/D FD2 solve with faces plus the gradient on the bounded axes,
+    # every node against the oracle (derivative bound 2 u n on 257 nodes, see
+    # tests/test_gpu_bounded_ops.py)
+    import paper_2301_01145_gb300 as sf
+    n = 256
+    man = workloads.manufactured(seed_index=1)
+    case = workloads.bounded_case(man, (n, n, n), ("D", "N", "D"), False)
+    plan = sf.Plan(3, (n,) * 3, (0,) * 3, (1,) * 3, "DND", grid="regular", eig="FD2", op="GRAD", prec="f32")
+    for (ax, side), g in case["faces"].items():
+        plan.set_boundary(ax, side, to_dev(g, "f32"))
+    psi, grad = plan(to_dev(case["f"][None], "f32"))
+    plan.sync()
+    d = Desc(3, (n,) * 3, (0,) * 3, (1,) * 3, ("D", "N", "D"), False, "FD2", op="GRAD")
+    ref, ref_g = oracle.solve(d, case["f"], case["faces"])
+    assert rel_l2(to_np(psi)[0], ref[0]) <= TOL["f32"]
+    tol = max(TOL["f32"], 2 * 2.0 ** -24 * (n + 1))
+    for a in range(3):
+        assert rel_l2(to_np(grad)[a], ref_g[a]) <= tol, a
     plan.close()
 
 
