@@ -903,6 +903,12 @@ template <typename T> __device__ void tile_mult1d(const Prob<T> &P, const Pass<T
 // is zero, as are lines through regular Dirichlet face nodes of the other
 // axes (the series vanishes there).  Only modes present in both bases are
 // kept.  acc = 1 adds the term to the output instead of writing it.
+// order = 3 is the transpose of the order-1 term (the adjoint): the operator
+// gradient's lines are read in the dual basis, doubled on that basis's
+// regular-grid Neumann face nodes, transformed, scaled by the same factor,
+// inverse transformed in the axis's own basis, halved on its Neumann face
+// nodes and added to the psi gradient (for these transforms F^T = V G / 2 and
+// G^T = 2 F V^-1 on the shared modes, V = 2 except 1 on those face nodes).
 // ---------------------------------------------------------------------------
 template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
   typedef cx<T> V;
