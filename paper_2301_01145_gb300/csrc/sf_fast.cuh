@@ -43,289 +43,8 @@ namespace sfg {
 
 #define SF_FAST_THREADS 256
 
-__device__ __forceinline__ int bitrev_lanes(int q, int G) {
-  int r = 0;
-  for (int b = 1; b < G; b <<= 1) {
-    r = (r << 1) | (q & 1);
-    q >>= 1;
-  }
-  return r;
-}
-
-template <typename V> __device__ __forceinline__ V shfl_xor_c(V v, int m) {
-  V r;
-  r.x = __shfl_xor_sync(0xffffffffu, v.x, m);
-  r.y = __shfl_xor_sync(0xffffffffu, v.y, m);
-  return r;
-}
-
-// W_32^m = exp(-2 pi i m / 32) for a compile-time m (folded to immediates
-// after unrolling): cos(2 pi r / 32), r = 0..8, and quadrant symmetry
-__host__ __device__ constexpr float cos32(int r) {
-  return r == 0 ? 1.0f
-       : r == 1 ? 0.980785280403230449126f
-       : r == 2 ? 0.923879532511286756128f
-       : r == 3 ? 0.831469612302545237078f
-       : r == 4 ? 0.707106781186547524401f
-       : r == 5 ? 0.555570233019602224742f
-       : r == 6 ? 0.382683432365089771728f
-       : r == 7 ? 0.195090322016128267848f
-                : 0.0f;
-}
-template <typename V> __device__ __forceinline__ V w32c(int m) {
-  m &= 31;
-  float c, sn;  // cos and sin of 2 pi m / 32
-  if (m <= 8) { c = cos32(m); sn = cos32(8 - m); }
-  else if (m <= 16) { c = -cos32(16 - m); sn = cos32(m - 8); }
-  else if (m <= 24) { c = -cos32(m - 16); sn = -cos32(24 - m); }
-  else { c = cos32(32 - m); sn = -cos32(m - 24); }
-  return mk<V>(c, -sn);
-}
-// twiddle W_L^{q j E} = W_32^{q j} of the E-point stage (L = 32 E, lane group index q < G)
-template <int G, typename V> __device__ __forceinline__ V w_stage2(int q, int j) {
-  if (G == 1) return w32c<V>(0);
-  if (G == 2) return q ? w32c<V>(j) : w32c<V>(0);
-  return q == 0 ? w32c<V>(0) : (q == 1 ? w32c<V>(j) : (q == 2 ? w32c<V>(2 * j) : w32c<V>(3 * j)));
-}
-
-// derivative wavenumber of FFT index k on a periodic or doubled axis of
-// length L: ks * kappa_1 with ks = k (k < L/2), k - L (k > L/2), 0 (Nyquist),
-// where kappa_1 = kap[1] of the axis; equals the kap table to one rounding
-template <int L> __device__ __forceinline__ float kap_of(int k, float kap1) {
-  const int ks = k < L / 2 ? k : (k > L / 2 ? k - L : 0);
-  return (float)ks * kap1;
-}
-
-// k index held in register j by this lane after a forward warp FFT
-template <int E> __device__ __forceinline__ int klayout(int lane, int j) {
-  constexpr int G = 32 / E;
-  const int k1 = lane / G, q = lane % G;
-  return k1 + E * (j + E * bitrev_lanes(q, G));
-}
-
-// row stride of the warp transpose buffer: 32 + G makes (k1 * stride + q) mod 16
-// a permutation over a half warp (8-byte elements), i.e. no bank conflicts
-template <int E> __host__ __device__ constexpr int wrow() { return 32 + 32 / E; }
-// Row of spectral index k in a 16-line transpose tile: stride 17, and the G
-// lane groups of the k layout (k / E^2) shifted by E/2 slots so that a half
-// warp writing one register of every lane hits 16 distinct bank pairs.
-template <int E> __device__ __forceinline__ int trow(int k) { return k * 17 + (k / (E * E)) * (E / 2); }
-template <int E> __host__ __device__ constexpr int trows_elems() { return 32 * E * 17 + 16; }
-
-// ---- pruned E-point DFTs ----------------------------------------------------
-// dft4 of (a0, a1, 0, 0)
-template <bool INV, typename V> __device__ __forceinline__ void dft4_2in(V a0, V a1, V &y0, V &y1, V &y2, V &y3) {
-  y0 = cadd(a0, a1);
-  y1 = cadd_mi<INV>(a0, a1);
-  y2 = csub(a0, a1);
-  y3 = csub_mi<INV>(a0, a1);
-}
-
-// inputs x[E/2 .. E) are zero
-template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfin(V *x) {
-  if (E == 16) {
-    V f[16];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) dft4_2in<INV>(x[s], x[s + 4], f[s * 4 + 0], f[s * 4 + 1], f[s * 4 + 2], f[s * 4 + 3]);
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-      V t0 = f[k1];
-      V t1 = w16<INV>(f[4 + k1], k1);
-      V t3 = w16<INV>(f[12 + k1], 3 * k1);
-      if (k1 == 2) {
-        V t2 = f[8 + k1];
-        dft4v_r2<INV>(t0, t1, t2, t3);  // w16^4 = -+i
-        x[k1] = t0; x[k1 + 4] = t1; x[k1 + 8] = t2; x[k1 + 12] = t3;
-      } else {
-        V t2 = w16<INV>(f[8 + k1], 2 * k1);
-        dft4v<INV>(t0, t1, t2, t3);
-        x[k1] = t0; x[k1 + 4] = t1; x[k1 + 8] = t2; x[k1 + 12] = t3;
-      }
-    }
-  } else {  // E == 8
-    V e0, e1, e2, e3, o0, o1, o2, o3;
-    dft4_2in<INV>(x[0], x[2], e0, e1, e2, e3);
-    dft4_2in<INV>(x[1], x[3], o0, o1, o2, o3);
-    o1 = w8<INV>(o1, 1);
-    o3 = w8<INV>(o3, 3);
-    x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
-    x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
-    x[2] = cadd_mi<INV>(e2, o2); x[6] = csub_mi<INV>(e2, o2);  // w8^2 = -+i
-    x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
-  }
-}
-
-// only outputs y[0 .. E/2) are needed
-template <int E, bool INV, typename V> __device__ __forceinline__ void dft_halfout(V *x) {
-  if (E == 16) {
-    V f[16];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      V a0 = x[s], a1 = x[s + 4], a2 = x[s + 8], a3 = x[s + 12];
-      dft4v<INV>(a0, a1, a2, a3);
-      f[s * 4 + 0] = a0; f[s * 4 + 1] = a1; f[s * 4 + 2] = a2; f[s * 4 + 3] = a3;
-    }
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-      const V t0 = f[k1];
-      const V t1 = w16<INV>(f[4 + k1], k1);
-      const V t3 = w16<INV>(f[12 + k1], 3 * k1);
-      if (k1 == 2) {  // w16^4 = -+i
-        const V t2 = f[8 + k1];
-        x[k1] = cadd(cadd_mi<INV>(t0, t2), cadd(t1, t3));
-        x[k1 + 4] = cadd_mi<INV>(csub_mi<INV>(t0, t2), csub(t1, t3));
-      } else {
-        const V t2 = w16<INV>(f[8 + k1], 2 * k1);
-        x[k1] = cadd(cadd(t0, t2), cadd(t1, t3));
-        x[k1 + 4] = cadd_mi<INV>(csub(t0, t2), csub(t1, t3));
-      }
-    }
-  } else {
-    V e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
-    V o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
-    dft4v<INV>(e0, e1, e2, e3);
-    dft4v<INV>(o0, o1, o2, o3);
-    x[0] = cadd(e0, o0);
-    x[1] = cadd(e1, w8<INV>(o1, 1));
-    x[2] = cadd_mi<INV>(e2, o2);  // w8^2 = -+i
-    x[3] = cadd(e3, w8<INV>(o3, 3));
-  }
-}
-
-// ---- warp FFTs -------------------------------------------------------------
-// M independent lines per warp, interleaved step by step so that their
-// dependency chains overlap (wsm: M consecutive buffers of E*33 elements).
-// Twiddles come from the lane-contiguous table twf of the axis:
-//   twf[k1 * 32 + t]          = W_L^{t k1}       (step 1, one 256-byte row per k1)
-//   twf[L + j * G + q]        = W_L^{q j E}      (step 3, E-point stage; with G = 2 the kernels
-//                                                 use the equal constants W_32^{q j} of w_stage2)
-//   twf[L + 32 + mm - 1 + r]  = W_{2 mm}^r       (step 3, lane stage mm)
-template <typename T, int E, bool HALFIN, int M>
-__device__ __forceinline__ void wfft_fwd_m(cx<T> (&v)[M][E], cx<T> *wsm, const cx<T> *__restrict__ tw) {
-  typedef cx<T> V;
-  constexpr int L = 32 * E, G = 32 / E, P = wrow<E>();
-  const int t = threadIdx.x & 31;
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    if (HALFIN) dft_halfin<E, false>(v[m]);
-    else dftR<E, false>(v[m]);
-  }
-  {
-    // W_L^{t k1}: rows k1 < 4 and k1 = 0 mod 4 are loaded, the others are one
-    // product W_L^{t (k1 & ~3)} W_L^{t (k1 & 3)} (one rounding more)
-    const V w1 = __ldg(&tw[1 * 32 + t]), w2 = __ldg(&tw[2 * 32 + t]), w3 = __ldg(&tw[3 * 32 + t]);
-#pragma unroll
-    for (int k1 = 1; k1 < E; ++k1) {
-      V w;
-      if ((k1 & 3) == 0 || k1 < 4) w = __ldg(&tw[k1 * 32 + t]);
-      else {
-        const V a = __ldg(&tw[(k1 & ~3) * 32 + t]);
-        const int b = k1 & 3;
-        w = cmul(a, b == 1 ? w1 : (b == 2 ? w2 : w3));
-      }
-#pragma unroll
-      for (int m = 0; m < M; ++m) v[m][k1] = cmul(v[m][k1], w);
-    }
-  }
-#pragma unroll
-  for (int m = 0; m < M; ++m)
-#pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) wsm[m * E * P + k1 * P + t] = v[m][k1];
-  __syncwarp();
-  const int k1 = t / G, q = t % G;
-#pragma unroll
-  for (int m = 0; m < M; ++m)
-#pragma unroll
-    for (int s = 0; s < E; ++s) v[m][s] = wsm[m * E * P + k1 * P + G * s + q];
-  __syncwarp();
-#pragma unroll
-  for (int m = 0; m < M; ++m) dftR<E, false>(v[m]);
-#pragma unroll
-  for (int j = 1; j < E; ++j) {
-    // two lanes per group: constants and one select; more lanes: one table load
-    const V w = G == 2 ? w_stage2<G, V>(q, j) : __ldg(&tw[L + j * G + q]);
-#pragma unroll
-    for (int m = 0; m < M; ++m) v[m][j] = cmul(v[m][j], w);
-  }
-#pragma unroll
-  for (int mm = G / 2; mm >= 1; mm >>= 1) {
-    const float sg = (q & mm) ? -1.f : 1.f;  // hi lane: partner - mine, lo lane: mine + partner
-    const V w = __ldg(&tw[L + 32 + mm - 1 + (q & (mm - 1))]);
-#pragma unroll
-    for (int m = 0; m < M; ++m)
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const V p = shfl_xor_c(v[m][j], mm);
-        V r = cfma_s<V>(sg, v[m][j], p);
-        if (mm > 1 && (q & mm)) r = cmul(r, w);
-        v[m][j] = r;
-      }
-  }
-}
-
-template <typename T, int E, bool HALFOUT, int M>
-__device__ __forceinline__ void wfft_inv_m(cx<T> (&v)[M][E], cx<T> *wsm, const cx<T> *__restrict__ tw) {
-  typedef cx<T> V;
-  constexpr int L = 32 * E, G = 32 / E, P = wrow<E>();
-  const int t = threadIdx.x & 31;
-  const int k1 = t / G, q = t % G;
-#pragma unroll
-  for (int mm = 1; mm < G; mm <<= 1) {
-    const bool hi = (q & mm) != 0;
-    const float sg = hi ? -1.f : 1.f;
-    const V w = __ldg(&tw[L + 32 + mm - 1 + (q & (mm - 1))]);
-#pragma unroll
-    for (int m = 0; m < M; ++m)
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        // pair (a = lo value, b = hi value): lo <- a + conj(w) b, hi <- a - conj(w) b.
-        // The hi lane twiddles its own value before the exchange.
-        V mine = v[m][j];
-        if (mm > 1 && hi) mine = cmulc(mine, w);
-        const V p = shfl_xor_c(mine, mm);
-        v[m][j] = cfma_s<V>(sg, mine, p);  // hi: p - mine, lo: p + mine
-      }
-  }
-#pragma unroll
-  for (int j = 1; j < E; ++j) {
-    const V w = G == 2 ? w_stage2<G, V>(q, j) : __ldg(&tw[L + j * G + q]);
-#pragma unroll
-    for (int m = 0; m < M; ++m) v[m][j] = cmulc(v[m][j], w);
-  }
-#pragma unroll
-  for (int m = 0; m < M; ++m) dftR<E, true>(v[m]);
-#pragma unroll
-  for (int m = 0; m < M; ++m)
-#pragma unroll
-    for (int s = 0; s < E; ++s) wsm[m * E * P + k1 * P + G * s + q] = v[m][s];
-  __syncwarp();
-#pragma unroll
-  for (int m = 0; m < M; ++m)
-#pragma unroll
-    for (int kk = 0; kk < E; ++kk) v[m][kk] = wsm[m * E * P + kk * P + t];
-  __syncwarp();
-  {
-    // conjugate of W_L^{t kk}, built as in the forward transform
-    const V w1 = __ldg(&tw[1 * 32 + t]), w2 = __ldg(&tw[2 * 32 + t]), w3 = __ldg(&tw[3 * 32 + t]);
-#pragma unroll
-    for (int kk = 1; kk < E; ++kk) {
-      V w;
-      if ((kk & 3) == 0 || kk < 4) w = __ldg(&tw[kk * 32 + t]);
-      else {
-        const V a = __ldg(&tw[(kk & ~3) * 32 + t]);
-        const int b = kk & 3;
-        w = cmul(a, b == 1 ? w1 : (b == 2 ? w2 : w3));
-      }
-#pragma unroll
-      for (int m = 0; m < M; ++m) v[m][kk] = cmulc(v[m][kk], w);
-    }
-  }
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    if (HALFOUT) dft_halfout<E, true>(v[m]);
-    else dftR<E, true>(v[m]);
-  }
-}
+// The warp FFT (wfft_fwd_m / wfft_inv_m, klayout, wrow) is defined in
+// sf_device.cuh, where the general engine also uses it for L = 256 / 512.
 
 // ---------------------------------------------------------------------------
 // fast pass descriptors (YZ executor)
