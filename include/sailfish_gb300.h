@@ -2,18 +2,19 @@
  * sailfish_gb300.h -- C ABI of the GB300 fast Poisson solver library
  * (libsailfish_gb300.so).
  *
- * The library solves  lap(psi) = rhs_scale * f  on a rectangular 2D or 3D
+ * The library solves  lap(psi) = rhs_scale * f  on a rectangular 1D, 2D or 3D
  * grid with the spectral method of SailFFish (Saverin, arXiv 2301.01145):
  * forward transform, point-wise multiply by the eigenvalues or by the
  * transformed Green's function, optional spectral operator, inverse
  * transform (Sec. 2.4, "Calculating and Retrieving the Solution").
  *
  * Conventions used by every call
- *  - Arrays are row-major [component][z][y][x] (x fastest), 2D: [component][y][x].
+ *  - Arrays are row-major [component][z][y][x] (x fastest), 2D: [component][y][x],
+ *    1D: [component][x].
  *  - Element type is float (SF_F32) or double (SF_F64), chosen per plan.
  *  - Device pointers must be CUDA device (or managed) memory on the current
  *    device, 16-byte aligned.  Host pointers are only accepted by
- *    sf_solve_host.  The caller owns every buffer it passes; the library
+ *    sf_solve_host and sf_solve_host_many.  The caller owns every buffer it passes; the library
  *    records pointers (no copies) and reads/writes them when the enqueued work
  *    runs on the plan's stream, so buffers must stay alive until then.
  *  - Every call returns an sf_status; no C++ exception crosses the ABI.
@@ -167,7 +168,7 @@ sf_status sf_plan_create(sf_plan *out, const sf_plan_desc *d, void *cuda_stream)
 /* Change the stream later work is enqueued on. */
 sf_status sf_plan_set_stream(sf_plan p, void *cuda_stream);
 
-/* Shapes as [ncomp][z][y][x] (2D: [ncomp][1][y][x]) of the source (in_shape),
+/* Shapes as [ncomp][z][y][x] (2D: [ncomp][1][y][x], 1D: [ncomp][1][1][x]) of the source (in_shape),
  * of psi (out_shape) and of the operator output (op_shape, all zero when op is
  * NONE), and the bytes of device workspace the plan holds.  Any pointer may be
  * NULL. */
@@ -180,7 +181,7 @@ sf_status sf_set_source(sf_plan p, const void *dev_f);
 /* Inhomogeneous boundary data for FD2 solves (Sec. 2.5.2, Sec. 4.2).
  * axis 0..dim-1, side 0 (X_l) or 1 (X_u).  dev_face holds one value per node
  * of the two other axes, row-major with the higher axis first ([z][y] for an x
- * face, [z][x] for a y face, [y][x] for a z face; 2D: [y] or [x]).
+ * face, [z][x] for a y face, [y][x] for a z face; 2D: [y] or [x]; 1D: one value).
  * Dirichlet: psi on the face; Neumann: d psi / d x_axis on the face.
  * NULL removes the face (homogeneous).  Only for ncomp == 1, FD2, D/N axes. */
 sf_status sf_set_boundary(sf_plan p, int axis, int side, const void *dev_face);
@@ -193,7 +194,9 @@ sf_status sf_solve(sf_plan p);
 
 /* Paper's Get_Output: enqueue the final inverse transform along x fused with
  * the extraction of the unpadded result and the Dirichlet boundary fill,
- * writing psi ([ncomp][...]) and, when op != NONE, the operator output. */
+ * writing psi ([ncomp][...]) and, when op != NONE, the operator output (for
+ * first derivatives on Dirichlet / Neumann axes, derivative passes over the
+ * written psi follow). */
 sf_status sf_get_output(sf_plan p, void *dev_psi, void *dev_op_out);
 
 /* Set_Input + solve + Get_Output in one call (one persistent kernel launch
@@ -226,7 +229,9 @@ sf_status sf_solve_host_many(sf_plan p, int n, const void *const *host_f, void *
  * affine in f; boundary data only shifts it, so it does not enter here.
  * Same pass structure as the solve with the multiplier applied to the
  * conjugate-transposed operator (the paper has no adjoint; this is the
- * exact transpose of the discrete map). */
+ * exact transpose of the discrete map).  For first derivatives on Dirichlet /
+ * Neumann axes the operator gradient is first mapped onto a psi gradient by
+ * transposed derivative passes into plan-owned workspace. */
 sf_status sf_solve_adjoint(sf_plan p, const void *dev_g_psi, const void *dev_g_op, void *dev_g_f);
 
 /* Batched solve of independent problems in one persistent kernel launch.
@@ -242,7 +247,8 @@ sf_status sf_batch_create(sf_plan *batch, const sf_plan *plans, int n, void *cud
 sf_status sf_batch_solve(sf_plan batch, const void *const *f, void *const *psi, void *const *op);
 
 /* Wait for the plan's stream and report device-side status (SF_ERR_TIMEOUT if
- * a scheduler wait gave up, SF_ERR_CUDA on an asynchronous CUDA error). */
+ * a scheduler wait gave up, SF_ERR_CUDA on an asynchronous CUDA error,
+ * SF_ERR_CORRUPT if a guard band of an SF_FLAG_DEBUG_CHECKS plan changed). */
 sf_status sf_sync(sf_plan p);
 
 /* Kernel launches one sf_execute / sf_batch_solve enqueues (for accounting). */
@@ -251,9 +257,10 @@ int sf_plan_launches(sf_plan p);
 /* Tracing of the last persistent-executor launch of a plan (waits for the
  * plan's stream).  For each of up to 8 pass kinds k (register path: 0 = y
  * forward, 1 = z stage, 2 = y inverse; general engine: the pass kind of the
- * tile): out[3k] = summed tile time (ns, over all CTAs), out[3k+1] = summed
- * time spent waiting for dependencies (ns), out[3k+2] = tiles.  out must hold
- * 24 doubles.  The paper times the solve steps separately (Sec. 5.3); this is
+ * tile, kinds 8 and 9 -- the 1D multiply and the derivative passes -- counted
+ * with kinds 0 and 1): out[3k] = summed tile time (ns, over all CTAs),
+ * out[3k+1] = summed time spent waiting for dependencies (ns), out[3k+2] =
+ * tiles.  out must hold 24 doubles.  The paper times the solve steps separately (Sec. 5.3); this is
  * the per-pass breakdown of the GPU schedule. */
 sf_status sf_plan_stats(sf_plan p, double out[24]);
 
