@@ -329,8 +329,8 @@ sf_status sf_debug_corrupt_guard(sf_plan p);
  * SM, one launch of about 30 ms timed with CUDA events on cuda_stream (NULL:
  * the legacy default stream), after one shorter warm-up launch.  It is the
  * measured counterpart of the unit-count FP32 peak against which the
- * register fast path (bound by FP32 issue) is quoted; the paper has no such
- * step.  SF_ERR_ARG for a null result pointer, SF_ERR_CUDA on a CUDA error. */
+ * register fast path (bound by instruction issue and the shared-memory pipe,
+ * not by DRAM) is quoted; the paper has no such step.  SF_ERR_ARG for a null result pointer, SF_ERR_CUDA on a CUDA error. */
 sf_status sf_probe_fp32_fma(double *tflops, void *cuda_stream);
 
 /* Release a plan or batch and its device memory (waits for its stream). */
