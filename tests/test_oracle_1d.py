@@ -7,8 +7,9 @@
     (x/2) erf(x/(sqrt2 s)) + s/sqrt(2 pi) exp(-x^2/(2 s^2)) of -d^2/dx^2 to
     rounding, and its exact derivative and Laplacian through GRAD / NABLA.
   * PS: single eigenmodes of every boundary type are solved exactly.
-  * FD2: a dense LU solve of the assembled 3-point system, and the stencil
-    residual with inhomogeneous face values.
+  * FD2: a dense LU solve of the assembled 3-point system, the stencil
+    residual with inhomogeneous face values, and second-order convergence to a
+    manufactured solution whose face data are its values and derivatives.
 """
 import math
 
@@ -112,3 +113,24 @@ def test_fd2_residual_inhomogeneous_1d(bc, stag):
     psi, _ = oracle.solve(d, f[None], faces)
     res = stencil_residual(d, psi[0], faces, f)
     assert np.max(np.abs(res)) < 1e-9 * np.max(np.abs(f))
+
+
+@pytest.mark.parametrize("bc", ["D", "DN", "ND"])
+@pytest.mark.parametrize("stag", [True, False])
+def test_fd2_second_order_with_inhomogeneous_faces_1d(bc, stag):
+    # psi = sin 2x + 0.3 x^2 on [0, 1.3]; Dirichlet faces carry psi, Neumann faces psi'
+    L = 1.3
+    psi_f = lambda x: np.sin(2 * x) + 0.3 * x * x
+    dpsi_f = lambda x: 2 * np.cos(2 * x) + 0.6 * x
+    errs = []
+    for n in (32, 64, 128):
+        d = Desc(1, (n,), (0.0,), (L,), (bc,), stag, "FD2")
+        x = coords(d)
+        f = -4 * np.sin(2 * x) + 0.6
+        faces = {}
+        for side, xf in ((0, 0.0), (1, L)):
+            faces[(0, side)] = np.array(psi_f(xf) if d.face(0, side) == "D" else dpsi_f(xf))
+        psi, _ = oracle.solve(d, f[None], faces)
+        errs.append(np.max(np.abs(psi[0] - psi_f(x))))
+    rate = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rate) > 1.8, (errs, rate)
