@@ -294,13 +294,17 @@ sf_status sf_plan_kernel_ms(sf_plan p, double ms[4], int *nslot, int *nsolve);
  * Workspace and tables live in one file-scope device array of 64 MiB that
  * every GPU loading this library holds until the process exits.  A problem
  * whose workspace does not fit returns SF_ERR_ARG (use sf_plan_create); other
- * unsupported options return SF_ERR_UNSUPPORTED.  No cudaMalloc, cudaFree or
- * other allocation is made.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) and must come before any stream
- * capture; the call is not thread-safe.  All calls share the array and it
- * keeps the last call's contents: calls that may overlap on the GPU (other
- * streams, other threads) race and corrupt each other's results.  Work is
- * enqueued on cuda_stream; the result is ready when that stream reaches it. */
+ * unsupported options return SF_ERR_UNSUPPORTED; sf_last_error gives the
+ * reason (for an oversized problem, the bytes it would need).  No cudaMalloc,
+ * cudaFree or other allocation is made.  Set-up: the first call in each CUDA
+ * context on a device (the first call on that device, and again the first
+ * after a cudaDeviceReset or in another driver-API context) looks up the
+ * array's device address (cudaGetSymbolAddress) and sets the kernel's shared
+ * memory attribute; that call must come before any stream capture.  All calls
+ * share the array and it keeps the last call's contents: calls that may
+ * overlap on the GPU (other streams, other threads) race and corrupt each
+ * other's results.  Work is enqueued on cuda_stream; the result is ready when
+ * that stream reaches it. */
 sf_status sf_solve_static(const sf_plan_desc *d, const void *dev_f, void *dev_psi, void *cuda_stream);
 
 /* Self-test of the bounded waits of the persistent scheduler: launches a

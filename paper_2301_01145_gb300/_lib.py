@@ -285,9 +285,7 @@ def sf_plan_destroy(plan):
 
 def sf_solve_static(desc: sf_plan_desc, f, psi, stream=None):
     """Allocation-free solve into the library's fixed device workspace (see the header)."""
-    st = int(load().sf_solve_static(ctypes.byref(desc), _ptr(f), _ptr(psi), _stream(stream)))
-    if st != SF_OK:
-        raise SolverError(st, "sf_solve_static", "see sailfish_gb300.h: FP32, scalar, P/D/N axes, workspace <= 64 MiB")
+    _check(int(load().sf_solve_static(ctypes.byref(desc), _ptr(f), _ptr(psi), _stream(stream))), "sf_solve_static")
 
 
 def sf_selftest_timeout(timeout_ms: int, stream=None) -> int:

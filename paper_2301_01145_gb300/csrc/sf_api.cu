@@ -33,6 +33,15 @@ sf_status fail(sf_status s, const std::string &msg) {
   return s;
 }
 
+}  // namespace
+
+// the text sf_last_error returns, set by entry points in other files
+namespace sfg {
+void set_last_error_text(const std::string &msg) { g_err = msg; }
+}  // namespace sfg
+
+namespace {
+
 #define SF_CK(call)                                                                                  \
   do {                                                                                               \
     cudaError_t e_ = (call);                                                                         \
@@ -46,7 +55,7 @@ sf_status fail(sf_status s, const std::string &msg) {
   } while (0)
 
 const double kPi = 3.14159265358979323846264338327950288;
-const size_t kSmemBudget = 112 * 1024;  // per CTA: two CTAs share one SM
+const size_t kSmemBudget = SF_SMEM_BUDGET;
 const int kMaxW = 16;
 const unsigned long long kTimeoutNs = 2000000000ull;  // 2 s bound on any scheduler wait
 

@@ -7,6 +7,8 @@
 namespace sfg {
 
 #define SF_THREADS 256
+// dynamic shared memory of one general-engine CTA: two CTAs share one SM
+#define SF_SMEM_BUDGET (112 * 1024)
 
 // Per-launch pointers: user buffers are kernel arguments so that every launch
 // (and every captured graph node) carries its own copy.

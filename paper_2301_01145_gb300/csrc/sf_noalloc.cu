@@ -13,10 +13,12 @@
 // workspace comes from differs.  The pass descriptors travel as kernel
 // arguments, and the twiddle / phase / eigenvalue tables are computed by a
 // small kernel into the array, so nothing is uploaded from host memory.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "../../include/sailfish_gb300.h"
@@ -29,13 +31,19 @@ using namespace sfg;
 
 // The array itself.  Host code must never pass its name to a kernel (in host
 // code it is only a stand-in for the symbol); the device address is obtained
-// with cudaGetSymbolAddress once per device.
+// with cudaGetSymbolAddress once per CUDA context on each device.
 static __device__ __align__(256) unsigned char sf_static_scratch[SF_STATIC_SCRATCH_BYTES];
+
+namespace sfg {
+void set_last_error_text(const std::string &msg);  // the text sf_last_error returns (sf_api.cu)
+}
 
 namespace {
 
-// the status is the whole report of this entry point (it keeps no error text)
-sf_status na_fail(sf_status s, const std::string &) { return s; }
+sf_status na_fail(sf_status s, const std::string &msg) {
+  set_last_error_text("sf_solve_static: " + msg);
+  return s;
+}
 
 #define NA_CK(call)                                                                                       \
   do {                                                                                                    \
@@ -43,19 +51,71 @@ sf_status na_fail(sf_status s, const std::string &) { return s; }
     if (e_ != cudaSuccess) return na_fail(SF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// device address of the array, looked up once per device (with that device current)
-unsigned char *g_scratch[SF_STATIC_MAX_DEVICES] = {nullptr};
+__global__ void __launch_bounds__(SF_THREADS) k_static_pass(Prob<float> prob, Pass<float> pass);
+
+// Device address of the array in the CUDA context current on each device.  An
+// address belongs to one context: after cudaDeviceReset (or in another
+// driver-API context on the same device) the module is loaded again and the
+// array may sit elsewhere.  Each entry is therefore keyed by the context's
+// unique ID (cuCtxGetId, reached through the runtime's driver entry-point
+// query, so the library does not link the driver directly); a call in a new
+// context repeats the set-up: the symbol lookup and the kernel's shared-memory
+// attribute.
+struct StaticState {
+  unsigned long long ctx_id;
+  unsigned char *addr;
+};
+StaticState g_state[SF_STATIC_MAX_DEVICES] = {};
+std::mutex g_state_mu;
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+// unique ID of the current context; false when it cannot be read
+bool current_ctx_id(unsigned long long *id) {
+  static PfnCtxGetCurrent get_cur = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<PfnCtxGetCurrent>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PfnCtxGetId>(p);
+  });
+  if (!get_cur || !get_id) return false;
+  CUcontext c = nullptr;
+  if (get_cur(&c) != CUDA_SUCCESS || !c) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
 
 sf_status scratch_for_current_device(unsigned char **out) {
   int dev = 0;
   NA_CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= SF_STATIC_MAX_DEVICES) return na_fail(SF_ERR_UNSUPPORTED, "device index too large");
-  if (!g_scratch[dev]) {
+  std::lock_guard<std::mutex> lk(g_state_mu);
+  StaticState &st = g_state[dev];
+  unsigned long long id = 0;
+  const bool have_id = st.addr && current_ctx_id(&id);
+  if (!have_id || id != st.ctx_id) {
+    // set-up in this context (the lookup also initialises the context when needed)
     void *p = nullptr;
     NA_CK(cudaGetSymbolAddress(&p, sf_static_scratch));
-    g_scratch[dev] = static_cast<unsigned char *>(p);
+    NA_CK(cudaFuncSetAttribute(k_static_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, SF_SMEM_BUDGET));
+    st.addr = static_cast<unsigned char *>(p);
+    // without a readable context ID the address is looked up on every call
+    st.ctx_id = current_ctx_id(&id) ? id : 0;
+    if (!st.ctx_id) {
+      *out = st.addr;
+      st.addr = nullptr;
+      return SF_OK;
+    }
   }
-  *out = g_scratch[dev];
+  *out = st.addr;
   return SF_OK;
 }
 
@@ -150,9 +210,9 @@ struct Carve {
 
 extern "C" sf_status sf_solve_static(const sf_plan_desc *d, const void *dev_f, void *dev_psi, void *cuda_stream) {
   if (!d || !dev_f || !dev_psi) return na_fail(SF_ERR_ARG, "null argument");
-  if (d->prec != SF_F32) return na_fail(SF_ERR_UNSUPPORTED, "sf_solve_static computes in FP32 only");
+  if (d->prec != SF_F32) return na_fail(SF_ERR_UNSUPPORTED, "computes in FP32 only");
   if (d->dim != 2 && d->dim != 3) return na_fail(SF_ERR_ARG, "dim must be 2 or 3");
-  if (d->ncomp != 1 || d->op != SF_OP_NONE) return na_fail(SF_ERR_UNSUPPORTED, "sf_solve_static: one component, no operator");
+  if (d->ncomp != 1 || d->op != SF_OP_NONE) return na_fail(SF_ERR_UNSUPPORTED, "one component, no operator");
   if (d->grid != SF_GRID_REGULAR && d->grid != SF_GRID_STAGGERED) return na_fail(SF_ERR_ARG, "bad grid type");
   if (d->eig != SF_EIG_PS && d->eig != SF_EIG_FD2) return na_fail(SF_ERR_ARG, "bad eigenvalue type");
   if (!(d->rhs_scale == d->rhs_scale) || d->rhs_scale == 0.0 || std::isinf(d->rhs_scale))
@@ -162,13 +222,14 @@ extern "C" sf_status sf_solve_static(const sf_plan_desc *d, const void *dev_f, v
   for (int a = 0; a < d->dim; ++a) {
     const int bc = d->bc[a][0];
     if (bc != d->bc[a][1]) return na_fail(SF_ERR_UNSUPPORTED, "different boundary types on one axis");
-    if (bc == SF_BC_UNBOUNDED) return na_fail(SF_ERR_UNSUPPORTED, "sf_solve_static: periodic, Dirichlet or Neumann axes only");
+    if (bc == SF_BC_UNBOUNDED) return na_fail(SF_ERR_UNSUPPORTED, "periodic, Dirichlet or Neumann axes only");
     if (bc < SF_BC_PERIODIC || bc > SF_BC_NEUMANN) return na_fail(SF_ERR_ARG, "bad boundary type");
     if (!(d->hi[a] > d->lo[a])) return na_fail(SF_ERR_ARG, "domain bounds need hi > lo");
     const bool stag = d->grid == SF_GRID_STAGGERED;
     kinds[a] = bc == SF_BC_PERIODIC ? AK_P : (bc == SF_BC_DIRICHLET ? (stag ? AK_DS : AK_DR) : (stag ? AK_NS : AK_NR));
     const int minn = kinds[a] == AK_DR ? 3 : 2;
     if (d->n[a] < minn) return na_fail(SF_ERR_ARG, "too few cells on an axis");
+    if (d->n[a] > 2048) return na_fail(SF_ERR_UNSUPPORTED, "more than 2048 cells on an axis");
     const int L = kinds[a] == AK_P ? d->n[a] : 2 * d->n[a];
     if (!len_ok(L)) return na_fail(SF_ERR_UNSUPPORTED, "FFT length " + std::to_string(L) + " is not 2^p or 3*2^p in [4, 2048]");
     if (bc == SF_BC_PERIODIC) ++nper;
@@ -280,7 +341,7 @@ extern "C" sf_status sf_solve_static(const sf_plan_desc *d, const void *dev_f, v
     for (;; W >>= 1) {
       const int Wp = W > 1 ? W + 1 : 1;
       const size_t bs = std::max((size_t)L * Wp, (size_t)(L + 2) * W);
-      if (W == 1 || nbuf * bs * sizeof(float2) <= 112 * 1024) {
+      if (W == 1 || nbuf * bs * sizeof(float2) <= SF_SMEM_BUDGET) {
         ps.W = W;
         ps.Wp = Wp;
         ps.nbuf = nbuf;
@@ -304,7 +365,6 @@ extern "C" sf_status sf_solve_static(const sf_plan_desc *d, const void *dev_f, v
     NA_CK(cudaGetLastError());
     return SF_OK;
   };
-  NA_CK(cudaFuncSetAttribute(k_static_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   sf_status s;
   if ((s = launch(PK_XFWD, P.ax[0].L, 2, cdiv(P.nuy, 2))) != SF_OK) return s;
   if (d->dim == 3) {

@@ -40,10 +40,21 @@ def test_static_matches_plan_twice(case):
     plan.sync()
     desc = _lib.make_desc(case["dim"], case["n"], case["lo"], case["hi"], list(case["bc"]), case["grid"],
                           case["eig"], rhs_scale=-1.5)
-    for _ in range(2):
+    for call in range(2):
         psi = torch.full(plan.out_shape, float("nan"), dtype=torch.float32, device="cuda")
-        _lib.sf_solve_static(desc, f, psi)
         torch.cuda.synchronize()
+        if call == 1:
+            # the second call must allocate nothing: the library's allocation hook
+            # refuses any allocation, and the device's free memory must not move
+            free_before = torch.cuda.mem_get_info()[0]
+            _lib.sf_debug_fail_alloc(0)
+        try:
+            _lib.sf_solve_static(desc, f, psi)
+            torch.cuda.synchronize()
+        finally:
+            _lib.sf_debug_fail_alloc(-1)
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free_before
         got = to_np(psi)
         assert np.all(np.isfinite(got))
         assert rel_l2(got[0], ref[0]) <= TOL["f32"]
@@ -58,3 +69,5 @@ def test_static_refuses_oversized_problem():
     with pytest.raises(_lib.SolverError) as e:
         _lib.sf_solve_static(desc, f, f)
     assert e.value.status == -1
+    # the refusal says how much workspace the problem would need
+    assert "bytes of workspace" in str(e.value)
