@@ -152,6 +152,17 @@ AxisHost build_axis(int kind, int n, double lo, double hi, int eig, bool is_x, b
       for (int q = 0; q < G; ++q) ang.push_back(-2.0 * kPi * (double)(q * j * E) / L);
     for (int mm = 1; mm < G; mm <<= 1)
       for (int r = 0; r < mm; ++r) ang.push_back(-2.0 * kPi * (double)r / (2.0 * mm));
+    if (L == 512) {
+      // parity-split stages (sf_par.cuh): W_512^{u (2 k1 + p)} as [p][k1][u], then as [p][u][k1]
+      ang.resize(SF_TWP_OFF, 0.0);
+      for (int tr = 0; tr < 2; ++tr)
+        for (int p = 0; p < 2; ++p)
+          for (int i = 0; i < 16; ++i)
+            for (int j = 0; j < 16; ++j) {
+              const int k1 = tr ? j : i, u = tr ? i : j;
+              ang.push_back(-2.0 * kPi * (double)(u * (2 * k1 + p)) / 512.0);
+            }
+    }
     a.twf.resize(2 * ang.size());
     for (size_t i = 0; i < ang.size(); ++i) {
       a.twf[2 * i] = std::cos(ang[i]);

@@ -202,6 +202,14 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dftR(V *x
   else if (R == 16) dft16<INV>(x);
 }
 
+// asynchronous global -> shared copies (4 bytes each), completed by cp_async_wait_all
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // problem description (device copy)
 // ---------------------------------------------------------------------------

@@ -38,10 +38,12 @@
 #include <atomic>
 
 #include "sf_kernels.cuh"
+#include "sf_par.cuh"
 
 namespace sfg {
 
 #define SF_FAST_THREADS 256
+static_assert(SF_FAST_THREADS == SF_PAR_THREADS, "one CTA size for every fast-path tile");
 
 // The warp FFT (wfft_fwd_m / wfft_inv_m, klayout, wrow) is defined in
 // sf_device.cuh, where the general engine also uses it for L = 256 / 512.
@@ -69,7 +71,7 @@ struct FastGeo {
 #define SF_YZ_MAXM 3  // interleaved lines per warp in the YZ executor (z stage with 3 components)
 // warp-buffer depth of an executor variant: the split-curl variant (OPS = 2)
 // keeps one line per warp so that two CTAs fit on an SM
-__host__ __device__ constexpr int fast_yz_lines(int ops) { return ops == 2 ? 1 : SF_YZ_MAXM; }
+__host__ __device__ constexpr int fast_yz_lines(int ops) { return ops >= 2 ? 1 : SF_YZ_MAXM; }
 template <int E, int M> __host__ __device__ constexpr int fast_wsm_elems() { return 8 * M * E * wrow<E>(); }
 
 // tiles of the YZ passes (the device decoders below use the same geometry)
@@ -88,8 +90,13 @@ template <typename T> __host__ __device__ inline bool fast_split_curl(const Prob
   return Q.op == OPK_CURL && Q.ncomp == 3 && Q.dim == 3 && !Q.adjoint;
 }
 __host__ __device__ inline int fast_tiles_zs(int nkx, int L) { return nkx * (L / SF_ZS_ROWS); }
+// forward 3D curl on zero-padded 512-point axes: the parity-split y / z stages (sf_par.cuh)
+template <typename T> __host__ __device__ inline bool fast_par(const Prob<T> &Q) {
+  return fast_split_curl(Q) && Q.ax[0].kind == AK_U && Q.ax[0].L == 512 && Q.ax[1].L == 512 && Q.ax[2].L == 512;
+}
 template <typename T> __host__ __device__ inline int fast_tiles_yi(const Prob<T> &Q, int nkx) {
-  return Q.nout * nkx * cdiv(Q.nuz, fast_split_curl(Q) ? fast_yi_split_rows(Q.ax[1].L) : SF_YI_COLS);
+  const int rows = fast_par(Q) ? SF_PAR_YI_ROWS : (fast_split_curl(Q) ? fast_yi_split_rows(Q.ax[1].L) : SF_YI_COLS);
+  return Q.nout * nkx * cdiv(Q.nuz, rows);
 }
 
 // ---------------------------------------------------------------------------
@@ -365,13 +372,6 @@ __device__ __forceinline__ void fast_yf(const Prob<float> &P, const FastGeo &g, 
 }
 
 // multiplier of the fast path: Green's table in [kx][ky'][kz'] order (kz fastest) or eigenvalue sum
-// asynchronous global -> shared copies (4 bytes each), completed by cp_async_wait_all
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // per-warp staging row of the Green's table in the z stage (floats; >= L / 2 + 1)
 #define SF_ZS_GROW 264
@@ -756,8 +756,14 @@ __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, 
 // the completed tile with a release reduction after the barrier.  The
 // descriptor is double-buffered: slot k & 1 is read during tile k while slot
 // (k + 1) & 1 is written.
+// OPS: 0 any operator (coefficient table), 1 curl written out, 2 split curl,
+// 3 split curl with the parity-split y / z stages (zero-padded 512-point axes)
+template <int E, int OPS> __host__ __device__ constexpr size_t fast_yz_region() {
+  return OPS == 3 ? par_smem_bytes() : (size_t)(fast_wsm_elems<E, fast_yz_lines(OPS)>() + trows_elems<E>()) * sizeof(float2);
+}
+
 template <int E, int NC, bool PAD, int OPS>
-__global__ void __launch_bounds__(SF_FAST_THREADS, OPS == 2 ? 2 : 1)
+__global__ void __launch_bounds__(SF_FAST_THREADS, OPS >= 2 ? 2 : 1)
     k_fyz(const Prob<float> *probs, FastGeo g, const FPass *passes, const int *pass_start, int npass, unsigned *done,
           ExecCtl *ctl, unsigned *sticky, unsigned long long timeout_ns, IOArgs<float> io) {
   typedef cx<float> V;
@@ -773,7 +779,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS == 2 ? 2 : 1)
   V *wsm = wsm_all + (threadIdx.x >> 5) * MM * E * wrow<E>();
   // packed pass table after the tile buffer: start[npass + 1], then per pass
   // a = kind | slot << 2 | nkx << 6 | kx0 << 16 and b = (dep0 + 1) | (dep1 + 1) << 16
-  int *s_start = reinterpret_cast<int *>(T + trows_elems<E>());
+  int *s_start = reinterpret_cast<int *>(fsm + fast_yz_region<E, OPS>());
   int *s_pa = s_start + npass + 1;
   int *s_pb = s_pa + npass;
   for (int i = threadIdx.x; i <= npass; i += blockDim.x) s_start[i] = pass_start[i];
@@ -861,12 +867,20 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS == 2 ? 2 : 1)
     if (s_ok[k]) {
       const FPass &ps = sPass[k];
       const int tile = it - s_start[my_pass];
-      if (my_kind == FK_YF) fast_yf<E, PAD, MM == 1 ? 1 : 2>(sP, g, ps, tile, wsm, T);
-      else if (my_kind == FK_ZS) {
-        if (OPS == 2) fast_zs_split<E, PAD>(sP, g, ps, tile, wsm, T);
-        else fast_zs<E, NC, PAD, OPS>(sP, g, ps, tile, wsm);
-      } else if (OPS == 2) fast_yi_rows<E, PAD>(sP, g, ps, tile, wsm);
-      else fast_yi<E, PAD>(sP, g, ps, tile, wsm, T);
+      if constexpr (OPS == 3) {
+        const size_t slot_off = (size_t)ps.slot * g.nfmax * g.S * 512 * sP.nuz;
+        float2 *X = reinterpret_cast<float2 *>(fsm);
+        if (my_kind == FK_YF) par_yf(sP, g.S, slot_off, ps.kx0, ps.nkx, tile, X);
+        else if (my_kind == FK_ZS) par_zs(sP, g.S, slot_off, ps.kx0, ps.nkx, tile, X);
+        else par_yi(sP, g.S, slot_off, ps.kx0, ps.nkx, tile, X);
+      } else {
+        if (my_kind == FK_YF) fast_yf<E, PAD, MM == 1 ? 1 : 2>(sP, g, ps, tile, wsm, T);
+        else if (my_kind == FK_ZS) {
+          if (OPS == 2) fast_zs_split<E, PAD>(sP, g, ps, tile, wsm, T);
+          else fast_zs<E, NC, PAD, OPS>(sP, g, ps, tile, wsm);
+        } else if (OPS == 2) fast_yi_rows<E, PAD>(sP, g, ps, tile, wsm);
+        else fast_yi<E, PAD>(sP, g, ps, tile, wsm, T);
+      }
     }
     if (threadIdx.x == 0) prepare(k ^ 1);
     __syncthreads();
@@ -905,8 +919,7 @@ template <int E> size_t fast_x_smem() { return (size_t)fast_xi_elems<E>() * size
 #define SF_FAST_MAXPASS 1024
 // dynamic shared memory of k_fyz: warp buffers, tile buffer, packed pass table
 template <int E, int OPS> size_t fast_yz_smem(int npass) {
-  return (size_t)(fast_wsm_elems<E, fast_yz_lines(OPS)>() + trows_elems<E>()) * sizeof(float2) +
-         (size_t)(3 * npass + 1) * sizeof(int);
+  return fast_yz_region<E, OPS>() + (size_t)(3 * npass + 1) * sizeof(int);
 }
 
 template <int E, int NC, bool PAD, int OPS> int fast_launch_yz(const FastLaunch &fl, const IOArgs<float> &io) {
@@ -965,7 +978,8 @@ template <int E, bool PAD> int fast_launch_all(const FastLaunch &fl, const IOArg
     if ((e = cudaMemsetAsync(fl.ctl, 0, sizeof(ExecCtl), fl.stream)) != cudaSuccess) return (int)e;
     if (mk && (e = cudaEventRecord(mk[1], fl.stream)) != cudaSuccess) return (int)e;
     int r;
-    if (fast_split_curl(Q)) r = fast_launch_yz<E, 3, PAD, 2>(fl, io);
+    if (E == 16 && PAD && fast_par(Q)) r = fast_launch_yz<E, 3, PAD, 3>(fl, io);
+    else if (fast_split_curl(Q)) r = fast_launch_yz<E, 3, PAD, 2>(fl, io);
     else if (Q.ncomp == 3 && Q.op == OPK_CURL) r = fast_launch_yz<E, 3, PAD, 1>(fl, io);
     else if (Q.ncomp == 3) r = fast_launch_yz<E, 3, PAD, 0>(fl, io);
     else if (Q.ncomp == 2) r = fast_launch_yz<E, 2, PAD, 0>(fl, io);
