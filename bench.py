@@ -53,9 +53,9 @@ def algorithmic_bytes(n: int, elem: int = 4):
     return b_io, b_method
 
 
-# FP32 lanes per SM and SM count of a GB300 (Blackwell Ultra); one FMA = 2 flops
+# FP32 lanes per SM of Blackwell (GB300); one FMA = 2 flops.  The SM count is
+# read from the device at run time.
 FP32_LANES_PER_SM = 128
-N_SM = 152
 
 
 def transform_flops(n: int):
@@ -233,64 +233,116 @@ def c3_config(n: int, world: int, unfused: bool = False):
             "parallelism": f"replicas x{world}"}
 
 
-def run_reference(args):
-    """FP64 CPU oracle on a reduced grid of the same workload (host cores)."""
-    world, rank, _ = dist_info()
-    if rank != 0:
-        return 0
-    import numpy as np
+def cpu_model() -> str:
+    """CPU model name of this host (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
+
+def _single_thread():
+    # one numerical thread per worker process: the pool supplies the parallelism
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+
+
+def _oracle_solves(job):
+    """Worker: `reps` oracle solves of the headline workload at n^3 (set-up untimed); returns seconds."""
+    n, reps = job
     import oracle
     import workloads
     from oracle.desc import Desc
-
-    n = args.ref_n
     d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, op="CURL", ncomp=3, rhs_scale=-1.0,
              sigma=2.0 / n)
     omega = workloads.vortex_ring(n)["omega"]
-    g_hat = oracle.green_hat(d)  # plan set-up, outside the timed region (Sec. 2.4.4)
-    for _ in range(args.warmup):
-        oracle.solve_unbounded(d, omega, g_hat)
+    g_hat = oracle.green_hat(d)  # plan set-up (Sec. 2.4.4)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(reps):
         oracle.solve_unbounded(d, omega, g_hat)
-    dt = time.perf_counter() - t0
-    value = n ** 3 * args.steps / dt
-    sample = (f"each step one oracle solve of the same workload on a {n}^3 grid (padded {2 * n}^3), psi + curl, "
-              f"FP64, one single-threaded process; value in the workload's unit (grid points/s)")
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """The FP64 oracle on every host core: one single-threaded worker process per core.
+
+    Started with the spawn method (workers share nothing with a CUDA context).
+    A step is one oracle solve per worker; throughput = cores x n^3 / wall time.
+    """
+
+    def __init__(self, cores: int = 0):
+        import multiprocessing as mp
+        self.cores = cores or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_single_thread)
+
+    def step_seconds(self, n: int, reps: int = 1) -> float:
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_solves, [(n, reps)] * self.cores, chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def run_reference(args):
+    """FP64 CPU oracle of the same workload on every host core (reduced grid)."""
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    n = args.ref_n
+    pool = OraclePool()
+    try:
+        for _ in range(args.warmup):
+            pool.step_seconds(n)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.step_seconds(n)
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+    value = pool.cores * n ** 3 * args.steps / dt
+    sample = (f"each step {pool.cores} oracle solves (one per worker process, one per host core) of the same "
+              f"workload on a {n}^3 grid (padded {2 * n}^3), psi + curl, FP64; CPU {cpu_model()}; value in the "
+              f"workload's unit (grid points/s)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": c3_config(N, world),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def cpu_baseline(n: int):
-    import numpy as np
-
-    import oracle
-    import workloads
-    from oracle.desc import Desc
-
-    d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, op="CURL", ncomp=3, rhs_scale=-1.0,
-             sigma=2.0 / n)
-    omega = workloads.vortex_ring(n)["omega"]
-    g_hat = oracle.green_hat(d)
-    reps = 0
-    t0 = time.perf_counter()
-    while True:
-        oracle.solve_unbounded(d, omega, g_hat)
-        reps += 1
-        el = time.perf_counter() - t0
-        if (el > 10.0 and reps >= 3) or reps >= 100:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": n ** 3 * reps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} oracle solve(s) of the same workload at {n}^3 (padded {2 * n}^3), psi + curl, "
-                      f"FP64, single-threaded numpy, {dt:.1f} s"}
+def cpu_baseline(n: int, pool=None, target_s: float = 15.0):
+    """The oracle on every host core: about target_s of solves at n^3 per worker."""
+    own = pool is None
+    pool = pool or OraclePool()
+    try:
+        pool.step_seconds(n)  # warm-up: imports and one solve per worker
+        t1 = pool.step_seconds(n)  # calibration: one solve per worker
+        reps = max(1, min(200, int(target_s / max(t1, 1e-3))))
+        dt = pool.step_seconds(n, reps)
+    finally:
+        if own:
+            pool.close()
+    return {"value": pool.cores * reps * n ** 3 / dt, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": f"{pool.cores} x {reps} oracle solve(s) of the same workload at {n}^3 (padded {2 * n}^3), "
+                      f"psi + curl, FP64, one single-threaded worker process per host core, {dt:.1f} s wall; "
+                      f"CPU {cpu_model()}"}
 
 
 def cpu_fast_baseline(n: int, gpu_psi=None, gpu_u=None):
@@ -351,6 +403,65 @@ def cpu_fast_baseline(n: int, gpu_psi=None, gpu_u=None):
     return out
 
 
+def cufft_context(n: int, omega, psi_ref, u_ref, steps: int = 10):
+    """The same unbounded curl solve as one library call chain on this GPU (context only).
+
+    torch.fft (cuFFT) in FP32: zero-padded real transforms of length 2n on every
+    axis (the padded arrays are materialised), psi_hat = g_hat * omega_hat with
+    g_hat = the real transform of h^3 G(r), G = erf(r / (sigma sqrt 2)) / (4 pi r)
+    sampled on the doubled grid (offset n taken as +n; the table is set-up,
+    outside the timed region), u_hat = i k x psi_hat on the doubled grid's
+    wavenumbers (Nyquist zero), inverse transforms, crop to [0, n).  Timed with
+    CUDA events after one warm-up; its relative L2 difference from the
+    library's own result is reported as a cross-check.
+    """
+    import torch
+    dev = omega.device
+    L, h = 2 * n, 1.0 / n
+    sigma = 2.0 * h
+    d = torch.arange(L, dtype=torch.float64, device=dev)
+    d = torch.where(d <= n, d, d - L) * h
+    r = torch.sqrt(d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2)
+    G = torch.special.erf(r / (sigma * math.sqrt(2.0))) / (4.0 * math.pi * r)
+    G[0, 0, 0] = math.sqrt(2.0) / (4.0 * math.pi ** 1.5 * sigma)
+    ghat = torch.fft.rfftn(G * h ** 3).real.float()
+    del G, r
+    k = torch.fft.fftfreq(L, d=2.0 / L, device=dev, dtype=torch.float64) * 2.0 * math.pi
+    k[L // 2] = 0.0
+    kr = torch.fft.rfftfreq(L, d=2.0 / L, device=dev, dtype=torch.float64) * 2.0 * math.pi
+    kr[-1] = 0.0
+    kz, ky, kx = k.float()[:, None, None], k.float()[None, :, None], kr.float()[None, None, :]
+
+    def solve():
+        ph = [torch.fft.rfftn(omega[c], s=(L, L, L)) * ghat for c in range(3)]
+        uh = [1j * (ky * ph[2] - kz * ph[1]), 1j * (kz * ph[0] - kx * ph[2]), 1j * (kx * ph[1] - ky * ph[0])]
+        psi = [torch.fft.irfftn(a, s=(L, L, L))[:n, :n, :n] for a in ph]
+        u = [torch.fft.irfftn(a, s=(L, L, L))[:n, :n, :n] for a in uh]
+        return psi, u
+
+    psi, u = solve()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        solve()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+
+    def rel(a, b):
+        num = sum(float((a[c].double() - b[c].double()).norm() ** 2) for c in range(3))
+        den = sum(float(b[c].double().norm() ** 2) for c in range(3))
+        return math.sqrt(num / den)
+
+    out = {"kind": "torch.fft (cuFFT), FP32, padded arrays materialised", "ms_per_step": ms,
+           "value": n ** 3 / (ms * 1e-3), "unit": UNIT, "steps": steps,
+           "rel_l2_vs_library": {"psi": rel(psi, psi_ref), "u": rel(u, u_ref)}}
+    del psi, u, ghat
+    torch.cuda.empty_cache()
+    return out
+
+
 def _events_time(fn, steps, stream):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -363,14 +474,237 @@ def _events_time(fn, steps, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def run_other(args):
-    """Timing line for the configurations other than the headline one."""
+def _rel_l2(got, ref):
+    import numpy as np
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = float(np.linalg.norm(ref))
+    return float(np.linalg.norm(got - ref)) / (den if den > 0 else 1.0)
+
+
+def _batch_kwargs(bp):
+    dim = bp.dim
+    return dict(dim=dim, n=bp.n_cells, lo=(-0.5,) * dim, hi=(0.5,) * dim, bc=bp.bc * dim,
+                grid="staggered" if bp.staggered else "regular", eig="PS",
+                sigma=2.0 / max(bp.n_cells) if bp.bc == "U" else 0.0, rhs_scale=-1.0 if bp.bc == "U" else 1.0)
+
+
+def config_case(name: str, world: int = 1, rank: int = 0):
+    """Plans, buffers and one step of a configuration other than the headline one.
+
+    Returns a dict: step (one step on device-resident buffers), points (output
+    grid points per step), dtype, cfg (the config description), check (a
+    function that compares the last step's result with the oracle and returns
+    the errors), close.
+    """
     import numpy as np
     import torch
 
-    import __graft_entry__ as ge
+    import oracle
     import paper_2301_01145_gb300 as sf
     import workloads
+    from oracle.desc import Desc
+
+    dev = lambda a, dt=torch.float32: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    host = lambda t: t.detach().double().cpu().numpy()
+    plans = []
+    extra = {}
+    if name == "c1":
+        pm = workloads.periodic_modes(64)
+        plan = sf.Plan(3, (64,) * 3, (0,) * 3, (2 * math.pi,) * 3, "PPP", eig="PS", prec="f64")
+        plans.append(plan)
+        f = dev(pm.f[None], torch.float64)
+        psi, _ = plan.empty_outputs()
+        step = lambda: plan.execute(f, psi)
+        points, dtype = 64 ** 3, "f64"
+        cfg = {"workload": "3D periodic scalar Poisson 64^3 cell-centred on [0,2pi)^3, pseudo-spectral, "
+                           "sum of 8 seeded sine modes", "grid": 64}
+
+        def check():
+            d = Desc(3, (64,) * 3, (0,) * 3, (2 * math.pi,) * 3, ("P",) * 3, True, "PS")
+            ref, _ = oracle.solve(d, pm.f[None])
+            got = host(psi)[0]
+            return {"psi": _rel_l2(got, ref[0]), "psi_vs_closed_form": _rel_l2(got, pm.psi_exact), "tol": 1e-12}
+    elif name in ("c2", "c6"):
+        n = 256
+        man = workloads.manufactured(seed_index=1)
+        case = workloads.bounded_case(man, (n, n, n), ("D", "N", "D"), False)
+        op = "GRAD" if name == "c6" else "NONE"
+        plan = sf.Plan(3, (n,) * 3, (0,) * 3, (1,) * 3, "DND", grid="regular", eig="FD2", op=op, prec="f32")
+        plans.append(plan)
+        for (ax, side), g in case["faces"].items():
+            plan.set_boundary(ax, side, dev(g))
+        f = dev(case["f"][None])
+        psi, grad = plan.empty_outputs()
+        step = lambda: plan.execute(f, psi, grad)
+        points, dtype = n ** 3, "f32"
+        if name == "c2":
+            cfg = {"workload": "3D Dirichlet/Neumann/Dirichlet Poisson, 256^3 cells regular grid on the unit cube, "
+                               "FD2 eigenvalues, inhomogeneous faces (manufactured sin/cos solution)", "grid": n}
+        else:
+            cfg = {"workload": "3D Dirichlet/Neumann/Dirichlet Poisson 256^3 regular grid, FD2, inhomogeneous "
+                               "faces, plus the gradient on the bounded axes (three derivative passes over psi)",
+                   "grid": n}
+
+        def check():
+            d = Desc(3, (n,) * 3, (0,) * 3, (1,) * 3, ("D", "N", "D"), False, "FD2", op=op)
+            ref, ref_g = oracle.solve(d, case["f"], case["faces"])
+            out = {"psi": _rel_l2(host(psi)[0], ref[0]), "tol": 1e-5}
+            if grad is not None:
+                g = host(grad)
+                out["grad"] = max(_rel_l2(g[a], ref_g[a]) for a in range(3))
+            return out
+    elif name == "c7":
+        rng = np.random.default_rng(7)
+        kinds = ["P", "D", "N", "DN", "ND", "U"]
+        fs, ps, descs = [], [], []
+        for i in range(1024):
+            bc = kinds[i % len(kinds)]
+            n1 = int(rng.choice([256, 384, 512])) if len(bc) == 1 else int(rng.choice([128, 256]))
+            grid = "staggered" if i % 2 == 0 or bc == "P" else "regular"
+            kw = dict(kernel="SPECT" if bc == "U" else "G2", rhs_scale=-1.0 if bc == "U" else 1.0)
+            plans.append(sf.Plan(1, (n1,), (-0.5,), (0.5,), [bc], grid=grid, eig="PS", **kw))
+            fs.append(dev(rng.normal(size=plans[-1].in_shape)))
+            ps.append(plans[-1].empty_outputs()[0])
+            descs.append((n1, bc, grid, kw["rhs_scale"]))
+        batch = sf.Batch(plans)
+        extra["batch"] = batch
+        step = lambda: batch.solve(fs, ps)
+        points, dtype = sum(int(np.prod(p.out_shape[1:])) for p in plans), "f32"
+        cfg = {"workload": "1024 uneven 1D problems (periodic, Dirichlet, Neumann, D-N, N-D, unbounded with the "
+                           "1D spectral kernel; 128..512 cells; both grids) in one persistent launch",
+               "problems": 1024, "points_per_step": points}
+
+        def check():
+            errs = []
+            for i in range(12):  # two of each boundary kind, both grids
+                n1, bc, grid, rs = descs[i]
+                d = Desc(1, (n1,), (-0.5,), (0.5,), (bc,), grid == "staggered", "PS", rhs_scale=rs,
+                         kernel="SPECT" if bc == "U" else "G2")
+                ref, _ = oracle.solve(d, host(fs[i]))
+                errs.append(_rel_l2(host(ps[i])[0], ref[0]))
+            return {"psi_max_over_sample": max(errs), "sample": "12 problems, two of each boundary kind", "tol": 1e-5}
+    elif name == "c5":
+        from paper_2301_01145_gb300.autograd import poisson_solve
+        from oracle import unbounded
+        n = 128
+        data = workloads.gaussian_blobs(n)
+        plan = sf.Plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=2.0 / n,
+                       rhs_scale=-1.0)
+        plans.append(plan)
+        om = dev(data["omega"])
+        w = dev(data["w"])
+        last = {}
+
+        def step():
+            x = om.detach().requires_grad_(True)
+            psi, u = poisson_solve(x, plan)
+            L = (w[None] * u * u).sum()
+            L.backward()
+            last["psi"], last["u"] = psi, u
+
+        points, dtype = n ** 3, "f32"
+        cfg = {"workload": "differentiable 3D unbounded curl solve 128^3 (padded 256^3), loss sum w|u|^2, "
+                           "forward + adjoint backward per step", "grid": n}
+
+        def check():
+            d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, op="CURL", ncomp=3, rhs_scale=-1.0,
+                     sigma=2.0 / n)
+            rng = np.random.default_rng(3)
+            pts = [tuple(int(v) for v in rng.integers(0, n, size=3)) for _ in range(12)]
+            ref_psi, ref_u = unbounded.sample_points(d, data["omega"], pts)
+            worst = 0.0
+            for got, ref in ((host(last["psi"]), ref_psi), (host(last["u"]), ref_u)):
+                for c in range(3):
+                    rms = float(np.sqrt(np.mean(got[c] ** 2)))
+                    for i, p in enumerate(pts):
+                        worst = max(worst, abs(got[c][p[2], p[1], p[0]] - ref[i][c]) / rms)
+            return {"psi_u_max_pointwise_over_rms": worst, "sample": "forward psi and u at 12 seeded points",
+                    "tol": 1e-5}
+    elif name == "c4":
+        from paper_2301_01145_gb300 import autotune
+        probs = workloads.batch_problems(512)
+        total_points = sum(bp.out_points() for bp in probs)
+        parallelism = None
+        if world > 1:
+            # independent problems: each rank solves its longest-processing-time share, no collective
+            mine = lpt_partition([problem_cost(bp) for bp in probs], world)[rank]
+            probs = [probs[i] for i in mine]
+            parallelism = f"problem shards x{world} (LPT by estimated cost)"
+        kwargs = [_batch_kwargs(bp) for bp in probs]
+        knobs = autotune.batch_knobs(kwargs)
+        fs, ps = [], []
+        for kw, bp, kn in zip(kwargs, probs, knobs):
+            plans.append(sf.Plan(**kw, **kn))
+            fs.append(dev(workloads.lowpass_noise(tuple(reversed(bp.node_counts())), bp.seed)[None]))
+            ps.append(plans[-1].empty_outputs()[0])
+        batch = sf.Batch(plans)
+        extra["batch"] = batch
+        step = lambda: batch.solve(fs, ps)
+        points, dtype = sum(bp.out_points() for bp in probs), "f32"
+        cfg = {"workload": "512 uneven problems in one persistent launch (CUDA graph): 2D 64^2..1024^2, 3D "
+                           "32^3..128^3, periodic/Dirichlet/Neumann/unbounded, regular/staggered, low-pass "
+                           "N(0,1) sources", "problems": 512, "points_per_step": total_points,
+               "knobs": autotune.describe_knobs(kwargs, knobs)}
+        if parallelism:
+            extra["parallelism"] = parallelism
+
+        def check():
+            picked, seen = [], set()
+            for i, bp in enumerate(probs):
+                key = (bp.dim, bp.bc, bp.staggered)
+                if key not in seen and bp.out_points() <= 300_000:
+                    seen.add(key)
+                    picked.append(i)
+            errs = []
+            for i in picked:
+                kw = kwargs[i]
+                dim = kw["dim"]
+                d = Desc(dim, tuple(kw["n"]), kw["lo"], kw["hi"], tuple(kw["bc"]), kw["grid"] == "staggered", "PS",
+                         rhs_scale=kw["rhs_scale"], sigma=kw["sigma"])
+                ref, _ = oracle.solve(d, host(fs[i]))
+                errs.append(_rel_l2(host(ps[i])[0], ref[0]))
+            return {"psi_max_over_sample": max(errs), "sample": f"{len(picked)} problems, one per (dimension, "
+                    "boundary type, grid)", "tol": 1e-5}
+    else:
+        raise ValueError(name)
+
+    def close():
+        if "batch" in extra:
+            extra["batch"].close()
+        for p in plans:
+            p.close()
+        torch.cuda.empty_cache()
+
+    return {"step": step, "points": points, "dtype": dtype, "cfg": cfg, "check": check, "close": close,
+            "parallelism": extra.get("parallelism")}
+
+
+def measure_config(name: str, steps: int, warmup: int, check: bool = True):
+    """Device time of one configuration (CUDA events, after warm-up) and its oracle errors."""
+    import torch
+    case = config_case(name)
+    try:
+        for _ in range(warmup):
+            case["step"]()
+        torch.cuda.synchronize()
+        ms = _events_time(case["step"], steps, torch.cuda.current_stream())
+        out = {"workload": case["cfg"]["workload"], "ms_per_step": ms, "value": case["points"] / (ms * 1e-3),
+               "unit": UNIT, "dtype": case["dtype"], "steps": steps}
+        if "knobs" in case["cfg"]:
+            out["knobs"] = case["cfg"]["knobs"]
+        if check:
+            out["oracle"] = case["check"]()
+        return out
+    finally:
+        case["close"]()
+
+
+def run_other(args):
+    """Timing line for the configurations other than the headline one."""
+    import torch
+
+    import __graft_entry__ as ge
 
     world, rank, local = dist_info()
     torch.cuda.set_device(local)
@@ -378,106 +712,13 @@ def run_other(args):
         torch.distributed.init_process_group("nccl")
     ge.build()
     stream = torch.cuda.current_stream()
-    dev = lambda a, dt=torch.float32: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
     line = {"unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
-    parallelism = f"replicas x{world}"
-    if args.workload == "c1":
-        pm = workloads.periodic_modes(64)
-        plan = sf.Plan(3, (64,) * 3, (0,) * 3, (2 * math.pi,) * 3, "PPP", eig="PS", prec="f64")
-        f = dev(pm.f[None], torch.float64)
-        psi, _ = plan.empty_outputs()
-        step = lambda: plan.execute(f, psi)
-        points, dtype = 64 ** 3, "f64"
-        cfg = {"workload": "3D periodic scalar Poisson 64^3 cell-centred on [0,2pi)^3, pseudo-spectral, "
-                           "sum of 8 seeded sine modes", "grid": 64}
-    elif args.workload == "c2":
-        n = 256
-        man = workloads.manufactured(seed_index=1)
-        case = workloads.bounded_case(man, (n, n, n), ("D", "N", "D"), False)
-        plan = sf.Plan(3, (n,) * 3, (0,) * 3, (1,) * 3, "DND", grid="regular", eig="FD2", prec="f32")
-        faces = {k: dev(v) for k, v in case["faces"].items()}
-        for (ax, side), g in faces.items():
-            plan.set_boundary(ax, side, g)
-        f = dev(case["f"][None])
-        psi, _ = plan.empty_outputs()
-        step = lambda: plan.execute(f, psi)
-        points, dtype = n ** 3, "f32"
-        cfg = {"workload": "3D Dirichlet/Neumann/Dirichlet Poisson, 256^3 cells regular grid on the unit cube, "
-                           "FD2 eigenvalues, inhomogeneous faces (manufactured sin/cos solution)", "grid": n}
-    elif args.workload == "c6":
-        n = 256
-        man = workloads.manufactured(seed_index=1)
-        case = workloads.bounded_case(man, (n, n, n), ("D", "N", "D"), False)
-        plan = sf.Plan(3, (n,) * 3, (0,) * 3, (1,) * 3, "DND", grid="regular", eig="FD2", op="GRAD", prec="f32")
-        for (ax, side), g in case["faces"].items():
-            plan.set_boundary(ax, side, dev(g))
-        f = dev(case["f"][None])
-        psi, grad = plan.empty_outputs()
-        step = lambda: plan.execute(f, psi, grad)
-        points, dtype = n ** 3, "f32"
-        cfg = {"workload": "3D Dirichlet/Neumann/Dirichlet Poisson 256^3 regular grid, FD2, inhomogeneous faces, "
-                           "plus the gradient on the bounded axes (three derivative passes over psi)", "grid": n}
-    elif args.workload == "c7":
-        rng = np.random.default_rng(7)
-        kinds = ["P", "D", "N", "DN", "ND", "U"]
-        plans, fs, ps = [], [], []
-        for i in range(1024):
-            bc = kinds[i % len(kinds)]
-            n1 = int(rng.choice([256, 384, 512])) if len(bc) == 1 else int(rng.choice([128, 256]))
-            grid = "staggered" if i % 2 == 0 or bc == "P" else "regular"
-            plans.append(sf.Plan(1, (n1,), (-0.5,), (0.5,), [bc], grid=grid, eig="PS",
-                                 kernel="SPECT" if bc == "U" else "G2", rhs_scale=-1.0 if bc == "U" else 1.0))
-            fs.append(dev(rng.normal(size=plans[-1].in_shape)))
-            ps.append(plans[-1].empty_outputs()[0])
-        batch = sf.Batch(plans)
-        step = lambda: batch.solve(fs, ps)
-        points, dtype = sum(int(np.prod(p.out_shape[1:])) for p in plans), "f32"
-        cfg = {"workload": "1024 uneven 1D problems (periodic, Dirichlet, Neumann, D-N, N-D, unbounded with the "
-                           "1D spectral kernel; 128..512 cells; both grids) in one persistent launch",
-               "problems": 1024, "points_per_step": points}
-    elif args.workload == "c5":
-        from paper_2301_01145_gb300.autograd import poisson_solve
-        n = 128
-        data = workloads.gaussian_blobs(n)
-        plan = sf.Plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=2.0 / n,
-                       rhs_scale=-1.0)
-        om = dev(data["omega"])
-        w = dev(data["w"])
-
-        def step():
-            x = om.detach().requires_grad_(True)
-            psi, u = poisson_solve(x, plan)
-            L = (w[None] * u * u).sum()
-            L.backward()
-
-        points, dtype = n ** 3, "f32"
-        cfg = {"workload": "differentiable 3D unbounded curl solve 128^3 (padded 256^3), loss sum w|u|^2, "
-                           "forward + adjoint backward per step", "grid": n}
-    else:  # c4
-        probs = workloads.batch_problems(512)
-        total_points = sum(bp.out_points() for bp in probs)
-        if world > 1:
-            # independent problems: each rank solves its longest-processing-time share, no collective
-            mine = lpt_partition([problem_cost(bp) for bp in probs], world)[rank]
-            probs = [probs[i] for i in mine]
-            parallelism = f"problem shards x{world} (LPT by estimated cost)"
-            line["scaling"] = "strong"
-        plans, fs, ps = [], [], []
-        for bp in probs:
-            dim = bp.dim
-            plans.append(sf.Plan(dim, bp.n_cells, (-0.5,) * dim, (0.5,) * dim, bp.bc * dim,
-                                 grid="staggered" if bp.staggered else "regular", eig="PS",
-                                 sigma=2.0 / max(bp.n_cells) if bp.bc == "U" else 0.0,
-                                 rhs_scale=-1.0 if bp.bc == "U" else 1.0, generic=True))
-            fs.append(dev(workloads.lowpass_noise(tuple(reversed(bp.node_counts())), bp.seed)[None]))
-            ps.append(plans[-1].empty_outputs()[0])
-        batch = sf.Batch(plans)
-        step = lambda: batch.solve(fs, ps)
-        points, dtype = sum(bp.out_points() for bp in probs), "f32"
-        cfg = {"workload": "512 uneven problems in one persistent launch (CUDA graph): 2D 64^2..1024^2, 3D "
-                           "32^3..128^3, periodic/Dirichlet/Neumann/unbounded, regular/staggered, low-pass "
-                           "N(0,1) sources", "problems": 512, "points_per_step": total_points}
+    case = config_case(args.workload, world, rank)
+    step, points, dtype, cfg = case["step"], case["points"], case["dtype"], case["cfg"]
+    cfg["parallelism"] = case["parallelism"] or f"replicas x{world}"
+    if case["parallelism"]:
+        line["scaling"] = "strong"
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -485,9 +726,11 @@ def run_other(args):
         torch.distributed.barrier()
     ms = max_over_ranks(_events_time(step, args.steps, stream))
     points_all = sum_over_ranks(float(points))  # units every rank processed in one step
-    cfg["parallelism"] = parallelism
     line.update({"metric": f"grid points/s ({args.workload})", "value": points_all / (ms * 1e-3), "ms_per_step": ms,
                  "dtype": dtype, "config": cfg})
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["oracle"] = case["check"]()
+    case["close"]()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -501,12 +744,14 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--ref-n", type=int, default=24)
+    ap.add_argument("--ref-n", type=int, default=32)
     ap.add_argument("--cpu-n", type=int, default=48)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--unfused", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--no-others", action="store_true")
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5", "c6", "c7"],
                     help="c3 (default): the headline 256^3 unbounded curl solve; the others time the remaining "
@@ -579,7 +824,8 @@ def main():
     # timed per launch by the events above; the other kernels and the whole
     # step against HBM for context
     hbm_peak, peak_kind, sm_mhz = read_peaks()
-    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    alu_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
     b_io, b_method = algorithmic_bytes(n)
     kb, kf = kernel_bytes(n), transform_flops(n)
     names = ["x_forward", "yz_executor", "x_inverse"]
@@ -595,7 +841,7 @@ def main():
                 "unit": "TFLOP/s", "frac": dom["alu_frac"],
                 "traffic": K_FYZ_TRAFFIC_256 if n == 256 else None, "algorithmic_bytes": kb["yz_executor"],
                 "algorithmic_flops": kf["yz_executor"],
-                "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz",
+                "peak_source": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz",
                 "peak_fma_measured": fma_tflops, "frac_of_fma_measured": dom["TFLOP/s"] / fma_tflops,
                 "kernels": kernels, "solves_timed": ksolves,
                 "step_hbm": {"achieved": b_method / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -664,13 +910,33 @@ def main():
                 "f32_rel_l2_vs_f64": {"psi": rel, "u": relu}}
         p64.close()
 
+    # the same solve as a cuFFT library call chain on this GPU (context for the hand-written transforms)
+    ctx = None
+    if rank == 0 and not args.no_cufft:
+        try:
+            ctx = cufft_context(n, omega, psi, u)
+        except Exception as exc:  # noqa: BLE001 - reported, not fatal
+            ctx = {"unavailable": f"{type(exc).__name__}: {exc}"}
+
     cpu = cpu_fast = None
+    psi_h, u_h = psi.cpu().numpy(), u.cpu().numpy()
+    plan.close()
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.cpu_n)
         try:
-            cpu_fast = cpu_fast_baseline(n, psi.cpu().numpy(), u.cpu().numpy())
+            cpu_fast = cpu_fast_baseline(n, psi_h, u_h)
         except ImportError as exc:  # scipy missing on the host
             cpu_fast = {"unavailable": str(exc)}
+
+    # the other configurations: device time and errors against the oracle
+    others = None
+    if rank == 0 and world == 1 and not args.no_others:
+        others = {}
+        for name in ("c1", "c2", "c4", "c5", "c6", "c7"):
+            try:
+                others[name] = measure_config(name, steps=10, warmup=3, check=not args.no_cpu)
+            except Exception as exc:  # noqa: BLE001 - reported per configuration
+                others[name] = {"error": f"{type(exc).__name__}: {exc}"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -678,9 +944,8 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": c3_config(n, world, args.unfused),
                 "gpu_launches": launches, "roofline": roof, "clocks": clocks, "e2e": e2e, "fp64": fp64,
-                "cpu_baseline": cpu, "cpu_fast": cpu_fast}
+                "cpu_baseline": cpu, "cpu_fast": cpu_fast, "cufft_context": ctx, "other_configs": others}
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

