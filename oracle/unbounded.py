@@ -210,3 +210,106 @@ def sample_points(desc: Desc, f: np.ndarray, points, tables=None):
     psi_arr = np.array(psi_out)
     op_arr = np.array(op_out) if op_out else None
     return psi_arr, op_arr
+
+
+# ---------------------------------------------------------------------------
+# whole lines (3D): direct sums across, exact aperiodic convolution along
+# ---------------------------------------------------------------------------
+# For a line parallel to axis L through (i_P, i_Q) on the other two axes,
+#   psi(i_L) = s sum_{j_P, j_Q} sum_{j_L} G(i - j) f(j),  s = -rhs_scale h^d.
+# The inner sum over j_L is an aperiodic 1D convolution, evaluated as the
+# circular convolution of length M (the doubled axis) of the zero-padded source
+# row with the kernel row of the doubled grid (mirrored distances, exactly the
+# row the full solve uses), i.e. as a product of the oracle's DFTs of the two
+# rows; the sums over j_P, j_Q are direct.  The derivative along L is the
+# doubled grid's i kappa applied to the line's DFT (the full solve applies it
+# to the whole padded solution, whose rows along L are these circular
+# convolutions); the derivatives across are direct sums with the derivative
+# tables K_a of sample_points, whose rows along L only enter at offsets
+# |j_L - i_L| < N_L.
+
+
+def _line_kernel_hat(rows: np.ndarray) -> np.ndarray:
+    """Real DFT (along the last axis) of kernel rows that are even in their last index."""
+    return fft.dft(rows, -1).real
+
+
+def sample_lines(desc: Desc, f: np.ndarray, axis: int, positions, tables=None):
+    """psi and op_out along whole lines parallel to `axis` (3D; op NONE, GRAD, DIV or CURL).
+
+    positions: (i_P, i_Q) index pairs on the two other axes P < Q.
+    Returns (psi [nlines][ncomp][N_axis], op [nlines][nop][N_axis] or None).
+    """
+    _check(desc)
+    if desc.dim != 3:
+        raise ValueError("sample_lines is for 3D problems")
+    if desc.op == "NABLA":
+        raise ValueError("NABLA is not sampled by lines")
+    f = np.asarray(f, dtype=np.float64)
+    if f.ndim == 3:
+        f = f[None]
+    ncomp = f.shape[0]
+    L = axis
+    P, Q = [a for a in range(3) if a != L]
+    ML = padded_length(desc, L)
+    NL, NP, NQ = desc.nodes(L), desc.nodes(P), desc.nodes(Q)
+    hL, hP, hQ = desc.h(L), desc.h(P), desc.h(Q)
+    hd = hL * hP * hQ
+    s = -desc.rhs_scale * hd
+    # sources as [c][j_P][j_Q][j_L], zero-padded to M along L, transformed along L
+    perm = (0,) + tuple(1 + (2 - a) for a in (P, Q, L))
+    fr = np.zeros((ncomp, NP, NQ, ML))
+    fr[..., :NL] = np.transpose(f, perm)
+    F = fft.dft(fr, -1)
+    del fr
+    # kernel rows of G on the doubled grid along L, for offsets (|o_P|, |o_Q|)
+    m = np.arange(ML)
+    dL = np.minimum(m, ML - m) * hL
+    oP = np.arange(NP) * hP
+    oQ = np.arange(NQ) * hQ
+    r = np.sqrt(oP[:, None, None] ** 2 + oQ[None, :, None] ** 2 + dL[None, None, :] ** 2)
+    Ghat = _line_kernel_hat(green(3, r, desc.sigma, desc.kernel, spectral_cutoff(desc)))
+    del r
+    need_op = desc.op in ("GRAD", "DIV", "CURL")
+    if need_op:
+        if tables is None:
+            tables = derivative_tables(desc)
+        MP, MQ = padded_length(desc, P), padded_length(desc, Q)
+        # rows along L of K_P (own axis P signed, mod M_P) and K_Q, zero beyond |o_L| < N_L
+        inside = (m < NL) | (m > ML - NL)
+        oL = np.where(inside, np.minimum(m, ML - m), 0)
+
+        def rows(a, Ma, No):
+            t = np.transpose(tables[a], tuple(2 - b for b in ((P, Q, L) if a == P else (Q, P, L))))
+            # t: [own axis a (M_a)][other cross axis (N + 1)][L (N + 1)]
+            r_ = t[:, :No, :][:, :, oL] * inside[None, None, :]
+            return _line_kernel_hat(r_)
+        KP = rows(P, MP, NQ)  # [M_P][N_Q][M_L]
+        KQ = rows(Q, MQ, NP)  # [M_Q][N_P][M_L]
+        dmult = ops.deriv_multiplier(ML, ML * hL)
+    psi_out, op_out = [], []
+    jP = np.arange(NP)
+    jQ = np.arange(NQ)
+    for iP, iQ in positions:
+        aP = np.abs(iP - jP)
+        aQ = np.abs(iQ - jQ)
+        Gl = Ghat[aP[:, None], aQ[None, :], :]
+        ph = [s * np.einsum("pqk,pqk->k", Gl, F[c]) for c in range(ncomp)]
+        psi_out.append([fft.idft(h_)[:NL].real for h_ in ph])
+        if need_op:
+            KPl = KP[np.mod(iP - jP, MP)[:, None], aQ[None, :], :]
+            KQl = KQ[np.mod(iQ - jQ, MQ)[:, None], aP[None, :], :].transpose(1, 0, 2)
+            d = {}
+            for c in range(ncomp):
+                d[(c, L)] = fft.idft(dmult * ph[c])[:NL].real
+                d[(c, P)] = fft.idft(s * np.einsum("pqk,pqk->k", KPl, F[c]))[:NL].real
+                d[(c, Q)] = fft.idft(s * np.einsum("pqk,pqk->k", KQl, F[c]))[:NL].real
+            if desc.op == "GRAD":
+                op_out.append([d[(0, a)] for a in range(3)])
+            elif desc.op == "DIV":
+                op_out.append([d[(0, 0)] + d[(1, 1)] + d[(2, 2)]])
+            else:
+                op_out.append([d[(2, 1)] - d[(1, 2)], d[(0, 2)] - d[(2, 0)], d[(1, 0)] - d[(0, 1)]])
+    psi_arr = np.array(psi_out)
+    op_arr = np.array(op_out) if op_out else None
+    return psi_arr, op_arr

@@ -323,3 +323,30 @@ def test_sampled_points_match_full_oracle_regular(op, ncomp, dim):
         idx = tuple(reversed(p))
         np.testing.assert_allclose(ps[i], psi[(slice(None),) + idx], rtol=1e-11, atol=1e-13)
         np.testing.assert_allclose(os_[i], opo[(slice(None),) + idx], rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("op,ncomp,staggered", [("CURL", 3, True), ("GRAD", 1, True), ("DIV", 3, True),
+                                                ("NONE", 2, True), ("CURL", 3, False), ("GRAD", 1, False)])
+def test_sampled_lines_match_full_oracle(op, ncomp, staggered):
+    # whole lines along each axis (direct sums across, the doubled grid's circular
+    # convolution along) equal the full doubled-domain solve on every point of the line;
+    # unequal extents and cell sizes per axis, both grid types (regular: padded 3 * 2^p)
+    from oracle import unbounded
+    n = (10, 8, 6)
+    d = Desc(3, n, (-0.5,) * 3, (0.5, 0.4, 0.3), ("U",) * 3, staggered, op=op, ncomp=ncomp, rhs_scale=-1.0,
+             sigma=0.12)
+    rng = np.random.default_rng(23)
+    f = rng.normal(size=(ncomp,) + d.shape())
+    psi, opo = oracle.solve(d, f)
+    for axis in range(3):
+        P, Q = [a for a in range(3) if a != axis]
+        pos = [(0, 0), (d.nodes(P) - 1, d.nodes(Q) - 1), (int(rng.integers(0, d.nodes(P))),
+                                                          int(rng.integers(0, d.nodes(Q))))]
+        ls, lo = unbounded.sample_lines(d, f, axis, pos)
+        for i, (iP, iQ) in enumerate(pos):
+            idx = [slice(None)] * 4
+            idx[1 + 2 - P] = iP
+            idx[1 + 2 - Q] = iQ
+            np.testing.assert_allclose(ls[i], psi[tuple(idx)], rtol=1e-11, atol=1e-13)
+            if opo is not None:
+                np.testing.assert_allclose(lo[i], opo[tuple(idx)], rtol=1e-10, atol=1e-12)
