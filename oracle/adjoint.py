@@ -26,7 +26,7 @@ import numpy as np
 
 from . import bounded, bounded_ops, fft, ops, r2r
 from .desc import Desc
-from .unbounded import _check, green_hat, multipliers
+from .unbounded import _check, green_hat, multipliers, padded_length
 
 
 def _apply_matrix_T(kind: str, x: np.ndarray, axis: int, scale: float = 1.0) -> np.ndarray:
@@ -107,8 +107,10 @@ def _unbounded_adjoint(desc: Desc, g_psi, g_op):
     _check(desc)
     dim = desc.dim
     axes = [1 + (dim - 1 - ax) for ax in range(dim)]
-    n_arr = tuple(desc.n[ax] for ax in reversed(range(dim)))
-    padded = tuple(2 * n for n in n_arr)
+    # node counts (N_c on staggered grids, N_c + 1 on regular grids) and the
+    # doubled lengths M of the forward solve (padded_length), [z][y][x] order
+    n_arr = tuple(desc.nodes(ax) for ax in reversed(range(dim)))
+    padded = tuple(padded_length(desc, ax) for ax in reversed(range(dim)))
     keep = (slice(None),) + tuple(slice(0, n) for n in n_arr)
 
     def pad(g, c):

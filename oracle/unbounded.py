@@ -220,21 +220,19 @@ def sample_points(desc: Desc, f: np.ndarray, points, tables=None):
 # The inner sum over j_L is an aperiodic 1D convolution, evaluated as the
 # circular convolution of length M (the doubled axis) of the zero-padded source
 # row with the kernel row of the doubled grid (mirrored distances, exactly the
-# row the full solve uses), i.e. as a product of the oracle's DFTs of the two
-# rows; the sums over j_P, j_Q are direct.  The derivative along L is the
-# doubled grid's i kappa applied to the line's DFT (the full solve applies it
-# to the whole padded solution, whose rows along L are these circular
-# convolutions); the derivatives across are direct sums with the derivative
-# tables K_a of sample_points, whose rows along L only enter at offsets
-# |j_L - i_L| < N_L.
+# row the full solve uses), i.e. as a product of DFTs of the two rows; the
+# sums over j_P, j_Q are direct.  The derivative along L is the doubled
+# grid's i kappa applied to the line's DFT (the full solve applies it to the
+# whole padded solution, whose rows along L are these circular convolutions).
+# A derivative across, along a in {P, Q}, uses the kernel
+# K_a = IDFT_a(i kappa_a DFT_a(G)) of the doubled grid along a (the same
+# definition as derivative_tables), whose rows along L only enter at offsets
+# |j_L - i_L| < N_L.  The transforms of this sampler are numpy.fft calls (a
+# library FFT as one step); it is pinned against the full doubled-domain
+# solve, which uses the oracle's own transform.
 
 
-def _line_kernel_hat(rows: np.ndarray) -> np.ndarray:
-    """Real DFT (along the last axis) of kernel rows that are even in their last index."""
-    return fft.dft(rows, -1).real
-
-
-def sample_lines(desc: Desc, f: np.ndarray, axis: int, positions, tables=None):
+def sample_lines(desc: Desc, f: np.ndarray, axis: int, positions):
     """psi and op_out along whole lines parallel to `axis` (3D; op NONE, GRAD, DIV or CURL).
 
     positions: (i_P, i_Q) index pairs on the two other axes P < Q.
@@ -251,41 +249,47 @@ def sample_lines(desc: Desc, f: np.ndarray, axis: int, positions, tables=None):
     ncomp = f.shape[0]
     L = axis
     P, Q = [a for a in range(3) if a != L]
-    ML = padded_length(desc, L)
+    ML, MP, MQ = padded_length(desc, L), padded_length(desc, P), padded_length(desc, Q)
     NL, NP, NQ = desc.nodes(L), desc.nodes(P), desc.nodes(Q)
     hL, hP, hQ = desc.h(L), desc.h(P), desc.h(Q)
-    hd = hL * hP * hQ
-    s = -desc.rhs_scale * hd
+    s = -desc.rhs_scale * hL * hP * hQ
+    kc = spectral_cutoff(desc)
+
+    def mirrored(M, h):
+        m = np.arange(M)
+        return np.minimum(m, M - m) * h
+
     # sources as [c][j_P][j_Q][j_L], zero-padded to M along L, transformed along L
     perm = (0,) + tuple(1 + (2 - a) for a in (P, Q, L))
     fr = np.zeros((ncomp, NP, NQ, ML))
     fr[..., :NL] = np.transpose(f, perm)
-    F = fft.dft(fr, -1)
+    F = np.fft.fft(fr, axis=-1)
     del fr
-    # kernel rows of G on the doubled grid along L, for offsets (|o_P|, |o_Q|)
-    m = np.arange(ML)
-    dL = np.minimum(m, ML - m) * hL
-    oP = np.arange(NP) * hP
-    oQ = np.arange(NQ) * hQ
-    r = np.sqrt(oP[:, None, None] ** 2 + oQ[None, :, None] ** 2 + dL[None, None, :] ** 2)
-    Ghat = _line_kernel_hat(green(3, r, desc.sigma, desc.kernel, spectral_cutoff(desc)))
+    # G rows along L (full mirrored row of the doubled grid) for offsets |o_P| < N_P, |o_Q| < N_Q
+    dL = mirrored(ML, hL)
+    r = np.sqrt((np.arange(NP) * hP)[:, None, None] ** 2 + (np.arange(NQ) * hQ)[None, :, None] ** 2 +
+                dL[None, None, :] ** 2)
+    Ghat = np.fft.fft(green(3, r, desc.sigma, desc.kernel, kc), axis=-1).real
     del r
     need_op = desc.op in ("GRAD", "DIV", "CURL")
     if need_op:
-        if tables is None:
-            tables = derivative_tables(desc)
-        MP, MQ = padded_length(desc, P), padded_length(desc, Q)
-        # rows along L of K_P (own axis P signed, mod M_P) and K_Q, zero beyond |o_L| < N_L
+        m = np.arange(ML)
         inside = (m < NL) | (m > ML - NL)
         oL = np.where(inside, np.minimum(m, ML - m), 0)
 
-        def rows(a, Ma, No):
-            t = np.transpose(tables[a], tuple(2 - b for b in ((P, Q, L) if a == P else (Q, P, L))))
-            # t: [own axis a (M_a)][other cross axis (N + 1)][L (N + 1)]
-            r_ = t[:, :No, :][:, :, oL] * inside[None, None, :]
-            return _line_kernel_hat(r_)
-        KP = rows(P, MP, NQ)  # [M_P][N_Q][M_L]
-        KQ = rows(Q, MQ, NP)  # [M_Q][N_P][M_L]
+        def cross_rows(Ma, ha, No, ho):
+            # K_a on [own axis a, doubled (M_a)][other cross axis (N_o)][|o_L| < N_L],
+            # then rows along L (zero outside |o_L| < N_L), transformed along L
+            ra = mirrored(Ma, ha)
+            rr = np.sqrt(ra[:, None, None] ** 2 + (np.arange(No) * ho)[None, :, None] ** 2 +
+                         (np.arange(NL) * hL)[None, None, :] ** 2)
+            g = green(3, rr, desc.sigma, desc.kernel, kc)
+            mult = ops.deriv_multiplier(Ma, Ma * ha)
+            k = np.fft.ifft(mult[:, None, None] * np.fft.fft(g, axis=0), axis=0).real
+            rows = k[:, :, oL] * inside[None, None, :]
+            return np.fft.fft(rows, axis=-1).real
+        KP = cross_rows(MP, hP, NQ, hQ)  # [M_P][N_Q][M_L]
+        KQ = cross_rows(MQ, hQ, NP, hP)  # [M_Q][N_P][M_L]
         dmult = ops.deriv_multiplier(ML, ML * hL)
     psi_out, op_out = [], []
     jP = np.arange(NP)
@@ -295,15 +299,15 @@ def sample_lines(desc: Desc, f: np.ndarray, axis: int, positions, tables=None):
         aQ = np.abs(iQ - jQ)
         Gl = Ghat[aP[:, None], aQ[None, :], :]
         ph = [s * np.einsum("pqk,pqk->k", Gl, F[c]) for c in range(ncomp)]
-        psi_out.append([fft.idft(h_)[:NL].real for h_ in ph])
+        psi_out.append([np.fft.ifft(h_)[:NL].real for h_ in ph])
         if need_op:
             KPl = KP[np.mod(iP - jP, MP)[:, None], aQ[None, :], :]
             KQl = KQ[np.mod(iQ - jQ, MQ)[:, None], aP[None, :], :].transpose(1, 0, 2)
             d = {}
             for c in range(ncomp):
-                d[(c, L)] = fft.idft(dmult * ph[c])[:NL].real
-                d[(c, P)] = fft.idft(s * np.einsum("pqk,pqk->k", KPl, F[c]))[:NL].real
-                d[(c, Q)] = fft.idft(s * np.einsum("pqk,pqk->k", KQl, F[c]))[:NL].real
+                d[(c, L)] = np.fft.ifft(dmult * ph[c])[:NL].real
+                d[(c, P)] = np.fft.ifft(s * np.einsum("pqk,pqk->k", KPl, F[c]))[:NL].real
+                d[(c, Q)] = np.fft.ifft(s * np.einsum("pqk,pqk->k", KQl, F[c]))[:NL].real
             if desc.op == "GRAD":
                 op_out.append([d[(0, a)] for a in range(3)])
             elif desc.op == "DIV":

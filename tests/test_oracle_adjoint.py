@@ -37,6 +37,12 @@ CASES = [
     Desc(2, (6, 4), (0,) * 2, (1, 1.5), ("D", "N"), False, "PS", op="NABLA", ncomp=1, rhs_scale=0.7),
     Desc(3, (4, 4, 3), (0,) * 3, (1,) * 3, ("N", "D", "N"), True, "PS", op="DIV", ncomp=3),
     Desc(1, (8,), (0.0,), (1.0,), ("DN",), False, "PS", op="GRAD", ncomp=1),
+    # unbounded solves on regular grids: N_c + 1 nodes, doubled length 2^p or 3 * 2^p >= 2 N_c + 1
+    Desc(3, (4, 3, 4), (-0.5,) * 3, (0.5, 0.4, 0.5), ("U",) * 3, False, op="CURL", ncomp=3, rhs_scale=-1.0,
+         sigma=0.2),
+    Desc(2, (5, 4), (-0.5,) * 2, (0.5, 0.3), ("U",) * 2, False, op="GRAD", ncomp=1, rhs_scale=2.0, sigma=0.1),
+    Desc(1, (6,), (-0.5,), (0.5,), ("U",), False, op="GRAD", ncomp=1, kernel="SPECT"),
+    Desc(2, (4, 5), (-0.5,) * 2, (0.5, 0.5), ("U",) * 2, False, op="NABLA", ncomp=1, sigma=0.15),
 ]
 
 
