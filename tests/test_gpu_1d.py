@@ -110,7 +110,8 @@ def test_unbounded_1d_spectral(n, grid, op, prec):
 @pytest.mark.parametrize("bc,grid,eig,op,kernel", [("P", "staggered", "PS", "GRAD", "G2"),
                                                    ("D", "regular", "FD2", "NONE", "G2"),
                                                    ("ND", "staggered", "PS", "NONE", "G2"),
-                                                   ("U", "staggered", "PS", "NABLA", "SPECT")])
+                                                   ("U", "staggered", "PS", "NABLA", "SPECT"),
+                                                   ("U", "regular", "PS", "GRAD", "SPECT")])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_adjoint_1d_vs_oracle(bc, grid, eig, op, kernel, prec):
     n = 48

@@ -114,3 +114,27 @@ def test_c5_dot_product_identity_fp32_fast_path():
     rhs = float((x.double() * gf.double()).sum())
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
     plan.close()
+
+
+@pytest.mark.parametrize("dim,n,op,ncomp", [(3, (24, 20, 16), "CURL", 3), (2, (40, 30), "GRAD", 1),
+                                            (3, (16, 16, 16), "NONE", 1)])
+def test_adjoint_regular_grid_unbounded_vs_oracle(dim, n, op, ncomp):
+    # unbounded solves on regular grids (N_c + 1 nodes, doubled length 2^p or 3 * 2^p
+    # >= 2 N_c + 1): the adjoint against the oracle's literal transpose
+    import paper_2301_01145_gb300 as sf
+    lo, hi = (-0.5,) * dim, (0.5, 0.4, 0.45)[:dim]
+    sigma = 2.0 * max((hi[a] - lo[a]) / n[a] for a in range(dim))
+    d = Desc(dim, n, lo, hi, ("U",) * dim, False, op=op, ncomp=ncomp, rhs_scale=-1.0, sigma=sigma)
+    rng = np.random.default_rng(31)
+    gp = rng.normal(size=(ncomp,) + d.shape())
+    nop = d.op_components() if op != "NONE" else 0
+    go = rng.normal(size=(nop,) + d.shape()) if nop else None
+    ref = oracle.adjoint_solve(d, gp, go)
+    for prec, tol in (("f32", 1e-5), ("f64", 1e-12)):
+        plan = sf.Plan(dim, n, lo, hi, "U" * dim, grid="regular", op=op, ncomp=ncomp, sigma=sigma, rhs_scale=-1.0,
+                       prec=prec)
+        gf = plan.adjoint(to_dev(gp, prec), to_dev(go, prec) if go is not None else None)
+        plan.sync()
+        for c in range(ncomp):
+            assert rel_l2(to_np(gf)[c], ref[c]) <= tol, (prec, c)
+        plan.close()

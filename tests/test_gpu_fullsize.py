@@ -5,9 +5,10 @@
     faces, FP32): the full oracle is affordable, element by element.
   * The same C2 solve with the gradient on its bounded axes (three derivative
     passes over psi), element by element.
-  * C3 (256^3 unbounded, 3 components, curl, FP32, register fast path with
-    the slab-pipelined executor): psi and u at sampled output points computed
-    one by one by the oracle's direct sums.
+  * C3 (256^3 unbounded, 3 components, curl, FP32 register fast path with
+    the slab-pipelined executor, and the FP64 path): psi and u on 13 whole
+    lines along all three axes (through the centre, the ring core and the
+    tile boundaries of the x and y stages) from the oracle's line sampler.
   * The register fast path (L = 256, 512) against the oracle at 128^3, and
     against the general engine on whole fields (forward and adjoint).
 """
@@ -91,24 +92,59 @@ def test_c6_fullsize_gradient_on_bounded_axes_elementwise():
     plan.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("f64", 1e-10)])
-def test_c3_fullsize_sampled(prec, tol):
+# Whole lines of the 256^3 curl solve: through the domain centre, through the
+# ring core (the largest |omega|), and on both sides of the physical tile
+# boundaries of the x transforms (16 y lines per tile) and of the y stages (16
+# z rows per tile), along all three axes: 13 lines x 256 points x 6 fields.
+def _c3_lines(omega):
+    n = omega.shape[-1]
+    core = np.unravel_index(int(np.argmax(np.abs(omega).sum(axis=0))), omega.shape[1:])  # (z, y, x)
+    cz, cy, cx = (int(v) for v in core)
+    c = n // 2
+    return {0: [(c, c), (15, 16), (16, 15), (n - 1, 0), (cy, cz)],       # x lines at (y, z)
+            1: [(c, c), (0, n - 1), (n - 1, 16), (cx, cz)],             # y lines at (x, z)
+            2: [(c, c), (16, 15), (0, 0), (cx, cy)]}                    # z lines at (x, y)
+
+
+@pytest.fixture(scope="module")
+def c3_oracle_lines():
     n = 256
-    ring = workloads.vortex_ring(n)
+    omega = workloads.vortex_ring(n)["omega"]
+    d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, op="CURL", ncomp=3, rhs_scale=-1.0,
+             sigma=2.0 / n)
+    lines = _c3_lines(omega)
+    ref = {ax: unbounded.sample_lines(d, omega, ax, pos) for ax, pos in lines.items()}
+    return omega, lines, ref
+
+
+def _line_of(field, axis, pos):
+    """field [c][z][y][x] -> [c][N] along `axis` through pos on the two other axes (increasing order)."""
+    i, j = pos
+    if axis == 0:
+        return field[:, j, i, :]
+    if axis == 1:
+        return field[:, j, :, i]
+    return field[:, :, j, i]
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("f64", 1e-12)])
+def test_c3_fullsize_lines(prec, tol, c3_oracle_lines):
+    # relative L2 per output field over all 3328 sampled points (13 whole lines)
+    omega, lines, ref = c3_oracle_lines
+    n = omega.shape[-1]
     plan = gpu_plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=2.0 / n,
                     rhs_scale=-1.0, prec=prec)
-    psi, u = plan(to_dev(ring["omega"], prec))
+    psi, u = plan(to_dev(omega, prec))
     plan.sync()
     gp, gu = to_np(psi), to_np(u)
     plan.close()
-    d = Desc(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, ("U",) * 3, True, op="CURL", ncomp=3, rhs_scale=-1.0,
-             sigma=2.0 / n)
-    pts = sample_idx(n, 9, 7)
-    # points near the ring core where the fields are largest
-    pts += [(int(np.argmax(np.abs(gu[0])) % n), int(np.argmax(np.abs(gu[0])) // n % n),
-             int(np.argmax(np.abs(gu[0])) // (n * n)))]
-    ref_psi, ref_u = unbounded.sample_points(d, ring["omega"], pts)
-    check_samples(gp, gu, ref_psi, ref_u, pts, tol)
+    for name, got_field, k in (("psi", gp, 0), ("u", gu, 1)):
+        for c in range(3):
+            got = np.concatenate([_line_of(got_field, ax, pos)[c] for ax, pos_l in lines.items() for pos in pos_l])
+            want = np.concatenate([ref[ax][k][i][c] for ax, pos_l in lines.items() for i in range(len(pos_l))])
+            assert got.size == 13 * n
+            err = rel_l2(got, want)
+            assert err <= tol, f"{prec} {name}[{c}]: relative L2 {err:.3e} over the sampled lines"
 
 
 def test_fast_path_128_vs_oracle_samples():
