@@ -19,6 +19,7 @@ Everything is written for clarity rather than speed:
   * bounded.py   -- bounded solve incl. FD2 boundary lifting (Sec. 2.5.2)
   * green.py     -- Gaussian-regularised Green's functions (Sec. 2.6.2)
   * unbounded.py -- Hockney-Eastwood solve with spectral operators
+  * semi.py      -- one unbounded axis with periodic axes (doubling of that axis only)
   * adjoint.py   -- the transpose of the solve (for gradients)
 
 Every function is pinned by tests in tests/test_oracle_*.py against closed
@@ -27,11 +28,15 @@ forms, brute force or library routines; see each module's header.
 from .desc import Desc  # noqa: F401
 from .bounded import solve_bounded  # noqa: F401
 from .unbounded import solve_unbounded, green_hat  # noqa: F401
+from .semi import solve_semi, is_semi  # noqa: F401
 from .adjoint import adjoint_solve  # noqa: F401
 
 
 def solve(desc, f, faces=None):
-    """Dispatch on boundary type: all-unbounded -> Hockney-Eastwood, else bounded."""
+    """Dispatch on boundary type: all-unbounded -> Hockney-Eastwood, one unbounded
+    axis with periodic axes -> semi-unbounded, else bounded."""
     if all(b == "U" for b in desc.bc[: desc.dim]):
         return solve_unbounded(desc, f)
+    if is_semi(desc):
+        return solve_semi(desc, f)
     return solve_bounded(desc, f, faces)

@@ -24,7 +24,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import bounded, bounded_ops, fft, ops, r2r
+from . import bounded, bounded_ops, fft, ops, r2r, semi
 from .desc import Desc
 from .unbounded import _check, green_hat, multipliers, padded_length
 
@@ -137,8 +137,53 @@ def _unbounded_adjoint(desc: Desc, g_psi, g_op):
     return fft.dftn(acc, axes).real[keep]  # DFT^T = DFT, then pad^T = extract
 
 
+def _semi_adjoint(desc: Desc, g_psi, g_op):
+    """Transpose of semi.solve_semi: the same steps reversed, each transposed
+    (DFT^T = DFT, (DFT^-1)^T = DFT^-1, crop^T = zero-pad, diagonal multipliers unchanged)."""
+    dim = desc.dim
+    ua = semi.unbounded_axis(desc)
+    uax = 1 + (dim - 1 - ua)
+    pax = [1 + (dim - 1 - a) for a in range(dim) if a != ua]
+    M = padded_length(desc, ua)
+    Nu = desc.nodes(ua)
+    n_arr = desc.shape()
+
+    def up(g, c):
+        # (crop after IDFT_U, then IDFT_P)^T = IDFT_P, zero-pad along U, IDFT_U
+        x = fft.idftn(np.asarray(g, dtype=np.float64).reshape((c,) + n_arr), pax)
+        shape = list(x.shape)
+        shape[uax] = M
+        xp = np.zeros(shape, dtype=np.complex128)
+        sl = [slice(None)] * len(shape)
+        sl[uax] = slice(0, Nu)
+        xp[tuple(sl)] = x
+        return fft.idft(xp, uax)
+
+    shape = list((desc.ncomp,) + n_arr)
+    shape[uax] = M
+    acc = np.zeros(shape, dtype=np.complex128)
+    if g_psi is not None:
+        acc = acc + up(g_psi, desc.ncomp)
+    if desc.op != "NONE" and g_op is not None:
+        gh = up(g_op, desc.op_components())
+        mults, laps = semi.multipliers(desc)
+        if desc.op == "NABLA":
+            lap = sum(ops._bcast(laps[a], dim, a) for a in range(dim))
+            acc = acc + lap[None] * gh
+        else:
+            acc = acc + ops.apply_op_transpose(desc.op, dim, gh, mults, desc.ncomp)
+    Kh = fft.dft(semi.kernel_rows(desc), uax - 1)
+    acc = acc * ((-desc.rhs_scale * desc.h(ua)) * Kh)[None]
+    out = fft.dft(acc, uax)  # DFT_U^T = DFT_U
+    sl = [slice(None)] * out.ndim
+    sl[uax] = slice(0, Nu)
+    return fft.dftn(out[tuple(sl)], pax).real  # pad^T = crop, DFT_P^T = DFT_P
+
+
 def adjoint_solve(desc: Desc, g_psi, g_op=None):
     """dL/df for dL/dpsi = g_psi and dL/dop_out = g_op (either may be None)."""
     if all(b == "U" for b in desc.bc[: desc.dim]):
         return _unbounded_adjoint(desc, g_psi, g_op)
+    if semi.is_semi(desc):
+        return _semi_adjoint(desc, g_psi, g_op)
     return _bounded_adjoint(desc, g_psi, g_op)

@@ -43,6 +43,10 @@ CASES = [
     Desc(2, (5, 4), (-0.5,) * 2, (0.5, 0.3), ("U",) * 2, False, op="GRAD", ncomp=1, rhs_scale=2.0, sigma=0.1),
     Desc(1, (6,), (-0.5,), (0.5,), ("U",), False, op="GRAD", ncomp=1, kernel="SPECT"),
     Desc(2, (4, 5), (-0.5,) * 2, (0.5, 0.5), ("U",) * 2, False, op="NABLA", ncomp=1, sigma=0.15),
+    # semi-unbounded: one unbounded axis, the others periodic
+    Desc(2, (6, 5), (0.0, -0.5), (1.0, 0.5), ("P", "U"), True, "PS", op="GRAD", ncomp=1, rhs_scale=-1.0),
+    Desc(3, (4, 4, 5), (0.0,) * 3, (1.0,) * 3, ("P", "U", "P"), False, "FD2", op="CURL", ncomp=3),
+    Desc(2, (5, 4), (0.0,) * 2, (1.0, 2.0), ("U", "P"), True, "PS", op="NABLA", ncomp=1, rhs_scale=0.5),
 ]
 
 
