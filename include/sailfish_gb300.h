@@ -63,9 +63,12 @@ typedef enum { SF_EIG_PS = 0, SF_EIG_FD2 = 1 } sf_eig;
  * G_P = G2 + sum_{j=1}^{P/2-1} sigma^{2j} / (2^j j!) (-lap)^{j-1} zeta_sigma, the
  * kernel whose smoothing has the transform exp(-(k sigma)^2/2) times the Taylor
  * series of exp(+(k sigma)^2/2) cut below order P (error O((k sigma)^P)). */
-/* SF_GREEN_SPECTRAL (1D and 3D; the only 1D kernel, Sec. 4.3): the sharp
+/* SF_GREEN_SPECTRAL (1D, 2D and 3D; the only 1D kernel, Sec. 4.3): the sharp
  * spectral cut-off G^(k) = 1/k^2 for |k| <= kc = pi / max_axis h, zero beyond,
- * i.e. G(r) = Si(kc r) / (2 pi^2 r) in 3D and
+ * i.e. G(r) = Si(kc r) / (2 pi^2 r) in 3D,
+ * G(r) = (ln(kc / 2) + gamma - F(kc r)) / (2 pi), F(x) = int_0^x (1 - J0(t)) / t dt
+ * in 2D (constant chosen so that G + ln(r) / (2 pi) -> 0, the far field of the
+ * 2D free-space kernel -ln(r) / (2 pi)), and
  * G(x) = -(|x| Si(kc |x|) + cos(kc x) / kc) / pi in 1D (constant chosen so that
  * G + |x|/2 -> 0, the far field of -|x|/2); green_sigma is not used. */
 typedef enum {
@@ -106,8 +109,17 @@ typedef enum { SF_F32 = 0, SF_F64 = 1 } sf_prec;
  *              Dirichlet face node is filled from the face data and a Neumann
  *              face node is solved for.  Either every axis is
  *              periodic/unbounded, or every axis is Dirichlet/Neumann.
+ *              Semi-unbounded (2D, 3D): exactly one unbounded axis, the others
+ *              periodic.  Per periodic mode, kappa^2 = -(sum of the periodic
+ *              axes' eigenvalues, PS or FD2) and the unbounded axis carries
+ *              the free-space kernel of -(d^2/dz^2 - kappa^2),
+ *              exp(-kappa |z|) / (2 kappa), or -|z| / 2 for kappa = 0,
+ *              point-sampled and summed by doubling that axis (the paper names
+ *              such domains as its next step without their kernels, Sec. 2.6,
+ *              Sec. 6); green and green_sigma are not used.  Two unbounded axes
+ *              with a periodic one return SF_ERR_UNSUPPORTED.
  *   grid       REGULAR (N_c + 1 nodes per axis) or STAGGERED (N_c cell centres).
- *   eig        PS or FD2 (bounded axes; ignored when unbounded).
+ *   eig        PS or FD2 (bounded and periodic axes; ignored on unbounded axes).
  *   op         spectral operator on psi.  On Dirichlet / Neumann axes a
  *              derivative differentiates the axis's sine / cosine series
  *              (sine <-> cosine) and is evaluated at every node (zero where the
@@ -336,6 +348,16 @@ sf_status sf_debug_corrupt_guard(sf_plan p);
  * register fast path (bound by instruction issue and the shared-memory pipe,
  * not by DRAM) is quoted; the paper has no such step.  SF_ERR_ARG for a null result pointer, SF_ERR_CUDA on a CUDA error. */
 sf_status sf_probe_fp32_fma(double *tflops, void *cuda_stream);
+
+/* The FP64 special functions with which plan set-up tabulates the kernels,
+ * evaluated on the host for n points x[i] -> out[i] (no GPU needed; the same
+ * code runs on the GPU when a plan builds its Green's table).  The paper has
+ * no such step; the call exists so that this code can be checked against
+ * independent implementations.  which = 0: the sine integral Si(x), x >= 0;
+ * 1: F(x) = int_0^x (1 - J0(t)) / t dt, x >= 0 (2D spectral kernel);
+ * 2: the exponential integral E1(x), x > 0 (2D Gaussian kernels).
+ * SF_ERR_ARG for null pointers, n < 0 or an unknown `which`. */
+sf_status sf_eval_special(int which, int n, const double *x, double *out);
 
 /* Release a plan or batch and its device memory (waits for its stream). */
 sf_status sf_plan_destroy(sf_plan p);

@@ -1,6 +1,6 @@
 """Regularised Green's functions (Sec. 2.6.2): Gaussian kernels "G2" to "G10" (2D, 3D)
-and the spectral kernel "SPECT" in 1D and 3D (a sharp cut-off at the grid
-wavenumber pi / max h).
+and the spectral kernel "SPECT" in 1D, 2D and 3D (a sharp cut-off at the
+grid wavenumber pi / max h).
 
 Convention: -lap G = zeta_sigma, the normalised Gaussian of width sigma, so
 that G > 0 and the solution of lap(psi) = s f is psi = -s (G * f).
@@ -81,6 +81,78 @@ def spectral_3d(r: np.ndarray, kc: float) -> np.ndarray:
     return np.where(r > 0.0, val, kc / (2.0 * math.pi ** 2))
 
 
+def int_one_minus_j0(x: np.ndarray) -> np.ndarray:
+    """F(x) = int_0^x (1 - J0(t)) / t dt for x >= 0.
+
+    Integrating J0's power series term by term gives the closed form
+    F(x) = (x^2 / 8) 2F3(1, 1; 2, 2, 2; -x^2 / 4), evaluated for every distinct
+    argument by mpmath's generalised hypergeometric function at 30 significant
+    digits (it switches to its asymptotic expansion for large arguments) and
+    rounded to FP64.  Without mpmath, the fallback is adaptive quadrature of
+    the integrand (int_one_minus_j0_quad).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    try:
+        import mpmath
+    except ImportError:
+        return int_one_minus_j0_quad(x)
+    xs, inv = np.unique(x, return_inverse=True)
+    vals = np.empty_like(xs)
+    with mpmath.workdps(30):
+        for i, v in enumerate(xs):
+            if v == 0.0:
+                vals[i] = 0.0
+                continue
+            t = mpmath.mpf(float(v))
+            vals[i] = float(t * t / 8 * mpmath.hyp2f3(1, 1, 2, 2, 2, -t * t / 4))
+    return vals[inv].reshape(x.shape)
+
+
+def int_one_minus_j0_quad(x: np.ndarray) -> np.ndarray:
+    """F(x) by adaptive quadrature (scipy.integrate.quad, J0 from scipy.special;
+    below t = 0.5 the integrand from J0's power series) over chunks of length
+    <= 20 between the sorted distinct arguments, accumulated from 0."""
+    from scipy import integrate
+    x = np.asarray(x, dtype=np.float64)
+    xs = np.unique(x)
+
+    def f(t):
+        if t < 0.5:  # (1 - J0(t)) / t from J0's series: 1 - J0 cancels for small t
+            q, term, acc = 0.25 * t * t, 1.0, 0.0
+            for m in range(1, 12):
+                term *= -q / (m * m)
+                acc -= term
+            return acc / t
+        return (1.0 - special.j0(t)) / t
+
+    import warnings
+    vals = np.empty_like(xs)
+    acc, prev = 0.0, 0.0
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", integrate.IntegrationWarning)  # tolerance set at rounding level
+        for i, b in enumerate(xs):
+            if b > prev:
+                # chunks of at most 20 (about three periods of J0) for the oscillatory tail
+                edges = np.linspace(prev, b, int(math.ceil((b - prev) / 20.0)) + 1)
+                for a0, a1 in zip(edges[:-1], edges[1:]):
+                    acc += integrate.quad(f, a0, a1, limit=200, epsabs=1e-17, epsrel=1e-14)[0]
+            vals[i] = acc
+            prev = b
+    return vals[np.searchsorted(xs, x)]
+
+
+def spectral_2d(r: np.ndarray, kc: float) -> np.ndarray:
+    """Sharp spectral cut-off in 2D: G^(k) = 1/k^2 for |k| <= kc.  The inverse
+    transform (1/2 pi) int_0^kc J0(k r) / k dk diverges at k = 0, so G is fixed
+    up to a constant: G(r) = -(1/2 pi) F(kc r) + C with F(x) = int_0^x
+    (1 - J0(t)) / t dt.  Since F(x) - ln x -> gamma - ln 2, the constant
+    C = (ln(kc/2) + gamma) / (2 pi) gives G + ln(r) / (2 pi) -> 0 (our reading:
+    the far field of the 2D free-space kernel -ln(r) / (2 pi), as the Gaussian
+    kernels have).  G(0) = (ln(kc/2) + gamma) / (2 pi)."""
+    r = np.asarray(r, dtype=np.float64)
+    return (math.log(0.5 * kc) + EULER_GAMMA - int_one_minus_j0(kc * r)) / (2.0 * math.pi)
+
+
 def spectral_1d(r: np.ndarray, kc: float) -> np.ndarray:
     """Sharp spectral cut-off in 1D (the only kernel the paper uses in 1D,
     Sec. 4.3): -G'' = sin(kc x) / (pi x), the band-limited delta.  Integrating
@@ -99,7 +171,7 @@ def green(dim: int, r: np.ndarray, sigma: float, kernel: str = "G2", kc: float =
             return spectral_3d(r, kc)
         if dim == 1:
             return spectral_1d(r, kc)
-        raise ValueError("the spectral kernel is defined for 1D and 3D")
+        return spectral_2d(r, kc)
     if dim == 1:
         raise ValueError("1D unbounded solves use the spectral kernel (Sec. 4.3)")
     g = g2_3d(r, sigma) if dim == 3 else g2_2d(r, sigma)

@@ -85,6 +85,7 @@ SIGNATURES = {
     "sf_debug_corrupt_guard": (c_int, [c_void_p]),
     "sf_solve_host_many": (c_int, [c_void_p, c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p)]),
     "sf_probe_fp32_fma": (c_int, [POINTER(c_double), c_void_p]),
+    "sf_eval_special": (c_int, [c_int, c_int, POINTER(c_double), POINTER(c_double)]),
     "sf_plan_kernel_ms": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), POINTER(c_int)]),
     "sf_plan_destroy": (c_int, [c_void_p]),
     "sf_status_string": (c_char_p, [c_int]),
@@ -291,6 +292,16 @@ def sf_solve_static(desc: sf_plan_desc, f, psi, stream=None):
 def sf_selftest_timeout(timeout_ms: int, stream=None) -> int:
     """Status of the scheduler's bounded-wait self-test (SF_ERR_TIMEOUT = -6 expected)."""
     return int(load().sf_selftest_timeout(int(timeout_ms), _stream(stream)))
+
+
+def sf_eval_special(which: int, x) -> list:
+    """Host evaluation of the FP64 set-up special functions (0: Si, 1: int_0^x (1 - J0)/t, 2: E1)."""
+    xs = [float(v) for v in x]
+    n = len(xs)
+    xa = (c_double * max(n, 1))(*xs)
+    out = (c_double * max(n, 1))()
+    _check(load().sf_eval_special(int(which), n, xa, out), "sf_eval_special")
+    return [out[i] for i in range(n)]
 
 
 def sf_version() -> str:

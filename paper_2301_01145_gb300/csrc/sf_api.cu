@@ -599,6 +599,7 @@ template <typename T> struct PlanImpl : sf_plan_s {
   size_t ws_bytes = 0;
   size_t field_elems = 0, op_elems = 0;
   int fastE = 0;  // 8 or 16: register fast path with L = 32 E; 0: generic engine
+  bool semi = false;  // one unbounded axis, the others periodic
   FastGeo geo{};
   FastList fl_fwd, fl_adj;
   void *st_in = nullptr, *st_psi = nullptr, *st_op = nullptr;  // host-solve staging
@@ -623,6 +624,7 @@ template <typename T> struct PlanImpl : sf_plan_s {
 
   sf_status init(const sf_plan_desc &desc, cudaStream_t st);
   sf_status build_green();
+  sf_status build_green_semi(const AxisHost *ah);
 
   sf_status run_fast(const Prob<T> &Q, const Prob<T> *dq, FastList &fl, bool front, bool back, const IOArgs<T> &io,
                      int *launches, cudaEvent_t *marks = nullptr);
@@ -895,13 +897,13 @@ static sf_status validate(const sf_plan_desc &d) {
     if (bc == SF_BC_UNBOUNDED) ++nunb;
   }
   if (ncp && nreal) return fail(SF_ERR_UNSUPPORTED, "mixing periodic/unbounded with Dirichlet/Neumann axes");
-  if (nunb && nunb != d.dim) return fail(SF_ERR_UNSUPPORTED, "semi-unbounded domains");
-  if (nunb && (d.green < SF_GREEN_G2 || d.green > SF_GREEN_SPECTRAL)) return fail(SF_ERR_ARG, "bad kernel");
-  if (nunb && d.green == SF_GREEN_SPECTRAL && d.dim == 2)
-    return fail(SF_ERR_UNSUPPORTED, "the spectral kernel is defined for 1D and 3D");
+  const bool semi = nunb == 1 && d.dim >= 2 && ncp == d.dim;  // one unbounded axis, the others periodic
+  if (nunb && nunb != d.dim && !semi)
+    return fail(SF_ERR_UNSUPPORTED, "semi-unbounded domains need exactly one unbounded axis, the others periodic");
+  if (nunb && !semi && (d.green < SF_GREEN_G2 || d.green > SF_GREEN_SPECTRAL)) return fail(SF_ERR_ARG, "bad kernel");
   if (nunb && d.dim == 1 && d.green != SF_GREEN_SPECTRAL)
     return fail(SF_ERR_UNSUPPORTED, "1D unbounded solves use the spectral kernel (SF_GREEN_SPECTRAL)");
-  if (nunb && d.green != SF_GREEN_SPECTRAL && !(d.green_sigma > 0.0 && std::isfinite(d.green_sigma)))
+  if (nunb && !semi && d.green != SF_GREEN_SPECTRAL && !(d.green_sigma > 0.0 && std::isfinite(d.green_sigma)))
     return fail(SF_ERR_ARG, "green_sigma must be positive and finite");
   if (ncp && d.bc[0][0] == SF_BC_PERIODIC && (d.n[0] % 2)) return fail(SF_ERR_UNSUPPORTED, "odd periodic x length");
   if (d.op != SF_OP_NONE) {
@@ -946,7 +948,10 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   p.op = d.op;
   const int k0 = axis_kind(d.bc[0][0], d.grid);
   p.cpath = (k0 == AK_P || k0 == AK_U) ? 1 : 0;
-  p.green = (k0 == AK_U) ? 1 : 0;
+  int nunb = 0;
+  for (int a = 0; a < d.dim; ++a) nunb += d.bc[a][0] == SF_BC_UNBOUNDED;
+  semi = nunb > 0 && nunb < d.dim;  // validated: one unbounded axis, the others periodic
+  p.green = nunb > 0 ? 1 : 0;
   p.rhs_scale = (T)d.rhs_scale;
   double prodL = 1.0, hd = 1.0;
   AxisHost ah[3];
@@ -1025,7 +1030,7 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   const size_t eA = (size_t)nf * p.nsx * p.nuz * p.nuy;
   size_t eI = d.dim == 3 ? (size_t)nf * p.nsx * p.nuz * p.nsy : 0;
   // register fast path: FP32, 3D, periodic/unbounded, one FFT length L = 256 or 512 on all axes
-  if (sizeof(T) == 4 && d.dim == 3 && p.cpath && !(d.flags & SF_FLAG_GENERIC) && p.ax[0].L == p.ax[1].L &&
+  if (sizeof(T) == 4 && d.dim == 3 && p.cpath && !semi && !(d.flags & SF_FLAG_GENERIC) && p.ax[0].L == p.ax[1].L &&
       p.ax[1].L == p.ax[2].L && (p.ax[0].L == 512 || p.ax[0].L == 256)) {
     fastE = p.ax[0].L / 32;
     int S = d.tune_slab > 0 ? d.tune_slab : 2;
@@ -1048,7 +1053,12 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   SF_TRY(mem.alloc(&tmp, sizeof(unsigned)));
   sticky = (unsigned *)tmp;
   SF_CK(cudaMemset(sticky, 0, sizeof(unsigned)));
-  if (p.green) {
+  if (p.green && semi) {
+    // table over the spectral indices: unbounded axis folded (L/2 + 1), periodic axes in full
+    p.gny = ah[1].kind == AK_U ? ah[1].L / 2 + 1 : ah[1].L;
+    p.gnz = d.dim == 3 ? (ah[2].kind == AK_U ? ah[2].L / 2 + 1 : ah[2].L) : 1;
+    SF_TRY(build_green_semi(ah));
+  } else if (p.green) {
     p.gny = ah[1].L / 2 + 1;  // octant of the padded axes
     p.gnz = d.dim == 3 ? ah[2].L / 2 + 1 : 1;
     SF_TRY(build_green());
@@ -1244,6 +1254,50 @@ template <typename T> sf_status PlanImpl<T>::build_green() {
     SF_CK(cudaGetLastError());
     P.ghat_t = (const T *)ght;
   }
+  SF_CK(cudaStreamSynchronize(stream));
+  P.ghat = (const T *)gh;
+  return SF_OK;
+}
+
+// Semi-unbounded Green's table (one unbounded axis ua, the others periodic):
+// for every periodic mode, kappa^2 = -(sum of the periodic axes' Table 1
+// eigenvalues, FP64 on the host), and along ua the DCT-I (the DFT of the
+// mirrored row) of the free-space kernel of -(d^2/dz^2 - kappa^2) sampled on the
+// doubled axis, exp(-kappa |z|) / (2 kappa) or -|z| / 2 for kappa = 0, scaled by
+// -rhs_scale h_ua / prod(L) (FP64 kernel, then rounded to T).
+template <typename T> sf_status PlanImpl<T>::build_green_semi(const AxisHost *ah) {
+  const int dim = d.dim;
+  int ua = 0;
+  for (int a = 0; a < dim; ++a)
+    if (ah[a].kind == AK_U) ua = a;
+  const int ext[3] = {P.nsx, P.gny, dim == 3 ? P.gnz : 1};
+  int pa = -1, pb = -1;  // the periodic axes, in increasing order
+  for (int a = 0; a < dim; ++a)
+    if (a != ua) (pa < 0 ? pa : pb) = a;
+  const int ea = ext[pa], eb = pb >= 0 ? ext[pb] : 1;
+  const size_t rows = (size_t)ea * eb;
+  std::vector<double> kap2(rows);
+  for (int i = 0; i < ea; ++i)
+    for (int j = 0; j < eb; ++j)
+      kap2[(size_t)i * eb + j] = -(ah[pa].lam[i] + (pb >= 0 ? ah[pb].lam[j] : 0.0));
+  double prodL = 1.0;
+  for (int a = 0; a < dim; ++a) prodL *= (double)P.ax[a].L;
+  const size_t cnt = (size_t)ext[0] * ext[1] * ext[2];
+  DevMem<double> tmem;
+  void *dk, *out;
+  SF_TRY(tmem.alloc(&dk, rows * sizeof(double)));
+  SF_TRY(tmem.alloc(&out, cnt * sizeof(double)));
+  SF_CK(cudaMemcpy(dk, kap2.data(), rows * sizeof(double), cudaMemcpyHostToDevice));
+  const int Lu = P.ax[ua].L;
+  const size_t smem = (size_t)(Lu + Lu / 2 + 1) * sizeof(double);
+  SF_CK(cudaFuncSetAttribute(sfg::k_green_semi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sfg::k_green_semi<<<(unsigned)rows, 256, smem, stream>>>((double *)out, (const double *)dk, dim, ua, pa, pb, ext[0],
+                                                            ext[1], ext[2], eb, Lu, ah[ua].h);
+  SF_CK(cudaGetLastError());
+  void *gh;
+  SF_TRY(mem.alloc(&gh, cnt * sizeof(T)));
+  sfg::k_convert_scale<T><<<1024, 256, 0, stream>>>((T *)gh, (const double *)out, cnt, -d.rhs_scale * ah[ua].h / prodL);
+  SF_CK(cudaGetLastError());
   SF_CK(cudaStreamSynchronize(stream));
   P.ghat = (const T *)gh;
   return SF_OK;
@@ -1625,6 +1679,14 @@ sf_status sf_selftest_timeout(int timeout_ms, void *cuda_stream) {
   unsigned s = 0;
   SF_CK(cudaMemcpy(&s, sticky, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (s) return fail(SF_ERR_TIMEOUT, "scheduler wait gave up as designed");
+  return SF_OK;
+}
+
+sf_status sf_eval_special(int which, int n, const double *x, double *out) {
+  if (!x || !out || n < 0) return fail(SF_ERR_ARG, "null pointer or negative count");
+  if (which < 0 || which > 2) return fail(SF_ERR_ARG, "unknown special function");
+  for (int i = 0; i < n; ++i)
+    out[i] = which == 0 ? sfg::sf_sine_integral(x[i]) : (which == 1 ? sfg::sf_int_1mj0(x[i]) : sfg::sf_expint_e1(x[i]));
   return SF_OK;
 }
 

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(SF_THREADS, 2)
 //   x >  1:  continued fraction 5.1.22 in its even form
 //            E1 = e^-x / (x + 1 - 1/(x + 3 - 4/(x + 5 - 9/(x + 7 - ...)))),
 //            evaluated with the modified Lentz method.
-__device__ inline double sf_expint_e1(double x) {
+__host__ __device__ inline double sf_expint_e1(double x) {
   const double euler = 0.57721566490153286060651209008240243;
   if (x <= 0.0) return 0.0;
   if (x > 700.0) return 0.0;
@@ -233,6 +233,109 @@ __host__ __device__ inline double sf_sine_integral(double x) {
   return half_pi + eim;
 }
 
+// ---- double-double arithmetic (Dekker's error-free sum and product) ------
+// The error-free steps need each rounded product as such: sf_rmul keeps the
+// compiler from fusing it with a following add (nvcc contracts device code,
+// and gcc contracts host code on FMA machines).
+__host__ __device__ inline double sf_rmul(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  volatile double p = a * b;
+  return p;
+#endif
+}
+struct sf_dd {
+  double hi, lo;
+};
+__host__ __device__ inline sf_dd sf_dd_two_sum(double a, double b) {
+  const double s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__host__ __device__ inline sf_dd sf_dd_add(sf_dd a, sf_dd b) {
+  sf_dd s = sf_dd_two_sum(a.hi, b.hi);
+  s.lo += a.lo + b.lo;
+  return sf_dd_two_sum(s.hi, s.lo);
+}
+__host__ __device__ inline sf_dd sf_dd_mul(sf_dd a, sf_dd b) {
+  const double p = sf_rmul(a.hi, b.hi);
+  const double e = fma(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi);
+  return sf_dd_two_sum(p, e);
+}
+__host__ __device__ inline sf_dd sf_dd_div(sf_dd a, double b) {
+  const double q1 = a.hi / b;
+  const double r = fma(-q1, b, a.hi) + a.lo;  // the remainder a.hi - q1 b is exact
+  return sf_dd_two_sum(q1, r / b);
+}
+
+// Bessel J0, J1 for x >= 40 from their Hankel asymptotic expansions (A&S 9.2.5,
+// 9.2.9, 9.2.10): J_nu(x) = sqrt(2 / (pi x)) [P cos(chi) - Q sin(chi)],
+// chi = x - (nu / 2 + 1 / 4) pi, with a_k = prod_{j <= k} (4 nu^2 - (2j - 1)^2) / (k! (8x)^k),
+// P = a_0 - a_2 + a_4 - ..., Q = a_1 - a_3 + ...; summed until the terms fall
+// below 1e-18 (at x >= 40 they do so long before the series starts to diverge).
+__host__ __device__ inline double sf_bessel_j_asym(int nu, double x) {
+  const double mu = 4.0 * nu * nu;
+  double a = 1.0, P = 1.0, Q = 0.0;
+  for (int k = 1; k < 60; ++k) {
+    a *= (mu - (2.0 * k - 1.0) * (2.0 * k - 1.0)) / (k * 8.0 * x);
+    const int r = k & 3;  // signs + (k = 0), + (1), - (2), - (3), + (4) ...
+    const double t = (r == 2 || r == 3) ? -a : a;
+    if (k & 1) Q += t;
+    else P += t;
+    if (fabs(a) < 1e-18) break;
+  }
+  const double pi = 3.14159265358979323846264338327950288;
+  const double chi = x - (0.5 * nu + 0.25) * pi;
+  return sqrt(2.0 / (pi * x)) * (P * cos(chi) - Q * sin(chi));
+}
+
+// F(x) = int_0^x (1 - J0(t)) / t dt, x >= 0, in FP64 (set-up of the 2D
+// spectral kernel).
+//   x <= 40: the power series sum_{m >= 1} (-1)^(m+1) (x^2/4)^m / (2m (m!)^2)
+//            (term-wise integration of J0's series), summed in double-double
+//            arithmetic so that its cancellation (terms up to ~1e15 at x = 40)
+//            leaves a result accurate to FP64 rounding;
+//   x >  40: F(x) = ln(x/2) + gamma + I(x), I(x) = int_x^inf J0(t)/t dt (the
+//            limit of F(x) - ln x is gamma - ln 2), with I from repeated
+//            integration by parts (J0 = J1' + J1/t, J1 = -J0'):
+//            I_n = -J1/x^n + (n+1) J0/x^(n+1) - (n+1)^2 I_(n+2) for
+//            I_n = int_x^inf J0(t) t^-n dt, summed until the smallest term.
+__host__ __device__ inline double sf_int_1mj0(double x) {
+  if (x <= 0.0) return 0.0;
+  if (x <= 40.0) {
+    const double x2 = sf_rmul(x, x);
+    const sf_dd xx = sf_dd_two_sum(x2, fma(x, x, -x2));
+    const sf_dd q = {xx.hi * 0.25, xx.lo * 0.25};
+    sf_dd term = {1.0, 0.0};  // (x^2/4)^m / (m!)^2
+    sf_dd sum = {0.0, 0.0};
+    for (int m = 1; m < 200; ++m) {
+      term = sf_dd_div(sf_dd_mul(term, q), (double)m * (double)m);
+      sf_dd t = sf_dd_div(term, 2.0 * m);
+      if (!(m & 1)) {
+        t.hi = -t.hi;
+        t.lo = -t.lo;
+      }
+      sum = sf_dd_add(sum, t);
+      if ((double)m * (double)m > q.hi && fabs(t.hi) < 1e-20 * fabs(sum.hi)) break;
+    }
+    return sum.hi + sum.lo;
+  }
+  const double euler = 0.57721566490153286060651209008240243;
+  const double j0 = sf_bessel_j_asym(0, x), j1 = sf_bessel_j_asym(1, x);
+  // I_1 = sum_k (-1)^k c_k [-J1 / x^(2k+1) + (2k+2) J0 / x^(2k+2)], c_k = (2^k k!)^2
+  double c = 1.0, xp = x, I = 0.0, prev = 1e300;
+  for (int k = 0; k < 60; ++k) {
+    const double t = c * (-j1 / xp + (2.0 * k + 2.0) * j0 / (xp * x));
+    if (fabs(t) > prev) break;  // asymptotic series: stop at its smallest term
+    I += (k & 1) ? -t : t;
+    prev = fabs(t);
+    if (prev < 1e-22) break;
+    c *= (2.0 * k + 2.0) * (2.0 * k + 2.0);
+    xp *= x * x;
+  }
+  return log(0.5 * x) + euler + I;
+}
+
 // Correction of the order-P kernel over G2 (P = 2m): sigma^2 zeta_sigma(r) Q_m(u),
 // u = r^2 / sigma^2, with Q_m = sum_{j=1}^{m-1} p_{j-1}(u) / (2^j j!) and p_j the
 // polynomial of (-lap)^j zeta_sigma = zeta_sigma p_j(u) / sigma^{2j} in d
@@ -272,6 +375,9 @@ static __global__ void k_green_octant(double *out, int nx, int ny, int nz, doubl
     double g;
     if (order == 0 && dim == 1) {  // spectral, 1D: -(r Si(kc r) + cos(kc r) / kc) / pi
       g = -(r * sf_sine_integral(kc * r) + cos(kc * r) / kc) / pi;
+    } else if (order == 0 && dim == 2) {  // spectral, 2D: (ln(kc/2) + gamma - F(kc r)) / (2 pi)
+      const double euler = 0.57721566490153286060651209008240243;
+      g = (log(0.5 * kc) + euler - sf_int_1mj0(kc * r)) / (2.0 * pi);
     } else if (order == 0) {  // spectral, 3D: Si(kc r) / (2 pi^2 r)
       g = r == 0.0 ? kc / (2.0 * pi * pi) : sf_sine_integral(kc * r) / (2.0 * pi * pi * r);
     } else if (dim == 3) {
@@ -288,6 +394,46 @@ static __global__ void k_green_octant(double *out, int nx, int ny, int nz, doubl
       g += sigma * sigma * zeta * kernel_q(dim, order / 2, u);
     }
     out[i] = g;
+  }
+}
+
+// Semi-unbounded Green's table, one CTA per periodic mode (row): the kernel row
+// g[m] = exp(-kappa m h) / (2 kappa) (kappa > 0) or -m h / 2 (kappa = 0) for the
+// offsets m = 0 .. Lu/2 of the doubled unbounded axis, then its DCT-I
+// g[0] + (-1)^k g[Lu/2] + 2 sum_{0 < m < Lu/2} g[m] cos(2 pi k m / Lu) at every
+// k = 0 .. Lu/2 (the DFT of the mirrored row).  The table is laid out like the
+// all-unbounded one: [i0][i2][i1] in 3D, [i0][i1] in 2D, with the unbounded
+// axis's index k and the periodic indices of the row (row = i_pa * eb + i_pb).
+static __global__ void k_green_semi(double *out, const double *kap2, int dim, int ua, int pa, int pb, int e0, int e1,
+                                    int e2, int eb, int Lu, double hu) {
+  extern __shared__ double gsem[];
+  double *cs = gsem;       // cos(2 pi j / Lu), j < Lu
+  double *g = gsem + Lu;   // kernel row, m <= Lu / 2
+  const int half = Lu / 2;
+  const int row = blockIdx.x;
+  const double k2 = kap2[row];
+  const double kap = k2 > 0.0 ? sqrt(k2) : 0.0;
+  for (int j = threadIdx.x; j < Lu; j += blockDim.x) cs[j] = cospi(2.0 * j / Lu);
+  for (int m = threadIdx.x; m <= half; m += blockDim.x) {
+    const double z = m * hu;
+    g[m] = kap > 0.0 ? exp(-kap * z) / (2.0 * kap) : -0.5 * z;
+  }
+  __syncthreads();
+  int c[3] = {0, 0, 0};
+  c[pa] = row / eb;
+  if (pb >= 0) c[pb] = row % eb;
+  for (int k = threadIdx.x; k <= half; k += blockDim.x) {
+    double acc = 0.0;
+    int idx = 0;  // k m mod Lu
+    for (int m = 1; m < half; ++m) {
+      idx += k;
+      if (idx >= Lu) idx -= Lu;
+      acc += g[m] * cs[idx];
+    }
+    const double v = g[0] + ((k & 1) ? -g[half] : g[half]) + 2.0 * acc;
+    c[ua] = k;
+    const size_t o = dim == 3 ? ((size_t)c[0] * e2 + c[2]) * e1 + c[1] : (size_t)c[0] * e1 + c[1];
+    out[o] = v;
   }
 }
 

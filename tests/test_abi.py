@@ -98,7 +98,7 @@ def test_status_strings_and_version(lib):
     (dict(n=(4096, 16, 16)), -2),      # FFT length above 2048
     (dict(n=(2, 16, 16)), -2),         # periodic FFT length 2 is below 4
     (dict(n=(17, 16, 16)), -2),        # odd periodic x length
-    (dict(dim=2, bc="UU", kernel="SPECT"), -2),  # the spectral kernel is defined for 1D and 3D
+    (dict(dim=2, bc="UD"), -2),        # unbounded mixed with a Dirichlet axis
     (dict(dim=1, bc="U", kernel="G2", sigma=0.1), -2),  # 1D unbounded: the spectral kernel only
     (dict(dim=1, op="CURL", ncomp=1), -1),       # no curl in 1D
     (dict(dim=0), -1),
@@ -172,3 +172,25 @@ def test_descriptor_fuzz_without_gpu(lib):
         assert lib.sf_last_error()
         seen.add(st)
     assert {-1, -2} <= seen
+
+
+def test_setup_special_functions_match_independent_implementations(lib):
+    # the FP64 special functions that plan set-up runs on the GPU to tabulate the
+    # kernels, evaluated on the host through the ABI: Si and E1 against scipy, and
+    # F(x) = int_0^x (1 - J0)/t dt (2D spectral kernel) against the oracle's
+    # quadrature, across both branches of each (series / continued fraction,
+    # double-double series / asymptotic expansion at x = 40)
+    from scipy import special
+    from oracle import green
+    from paper_2301_01145_gb300 import _lib
+    x = np.concatenate([np.linspace(0.0, 60.0, 601), [39.999, 40.0, 40.001, 123.4, 777.7, 2345.6, 9000.0]])
+    si = np.array(_lib.sf_eval_special(0, x))
+    np.testing.assert_allclose(si, special.sici(x)[0], rtol=2e-15, atol=1e-300)
+    F = np.array(_lib.sf_eval_special(1, x))
+    ref = green.int_one_minus_j0(x)
+    np.testing.assert_allclose(F, ref, rtol=1e-14, atol=1e-18)
+    xe = x[x > 0]
+    e1 = np.array(_lib.sf_eval_special(2, xe))
+    np.testing.assert_allclose(e1, special.exp1(xe), rtol=1e-14, atol=1e-300)
+    with pytest.raises(_lib.SolverError):
+        _lib.sf_eval_special(7, [1.0])

@@ -350,3 +350,58 @@ def test_sampled_lines_match_full_oracle(op, ncomp, staggered):
             np.testing.assert_allclose(ls[i], psi[tuple(idx)], rtol=1e-11, atol=1e-13)
             if opo is not None:
                 np.testing.assert_allclose(lo[i], opo[tuple(idx)], rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# spectral (sharp cut-off) kernel, 2D
+# ---------------------------------------------------------------------------
+def test_spectral_kernel_2d_laplacian_is_the_band_limited_delta():
+    # -lap G = kc J1(kc r) / (2 pi r): the inverse 2D transform of the indicator of |k| <= kc
+    kc = 5.0
+    g = lambda x: float(green.green(2, np.array(x), 0.0, "SPECT", kc))
+    for r in (0.1, 0.5, 1.3, 3.0, 7.7):
+        d = 1e-4
+        g0, gp, gm = g(r), g(r + d), g(r - d)
+        lap = (gp - 2 * g0 + gm) / d ** 2 + 1 / r * (gp - gm) / (2 * d)
+        zeta = kc * special.j1(kc * r) / (2 * math.pi * r)
+        assert abs(-lap - zeta) < 1e-6 * kc ** 2
+    # r -> 0 limit and the gauge: G + ln(r) / (2 pi) -> 0 in the far field
+    assert abs(g(0.0) - (math.log(kc / 2) + 0.5772156649015329) / (2 * math.pi)) < 1e-15
+    for r in (400.0, 2000.0):
+        assert abs(g(r) + math.log(r) / (2 * math.pi)) < 2.0 / (kc * r) ** 1.5
+
+
+def test_spectral_kernel_2d_beats_g2_on_a_resolved_blob():
+    # a Gaussian blob of width s: the free-space potential of lap(psi) = -blob is
+    # -(ln r + E1(r^2 / (2 s^2)) / 2) / (2 pi) (the 2D G2 closed form with sigma = s)
+    n = 64
+    h = 1.0 / n
+    x = -0.5 + h * (np.arange(n) + 0.5)
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    R = np.sqrt(X ** 2 + Y ** 2)
+    s = 0.06
+    om = np.exp(-R ** 2 / (2 * s * s)) / (2 * math.pi * s * s)
+    exact = green.g2_2d(R, s)
+    errs = {}
+    for kern in ("G2", "SPECT"):
+        d = Desc(2, (n,) * 2, (-0.5,) * 2, (0.5,) * 2, ("U",) * 2, True, rhs_scale=-1.0, sigma=2 * h, kernel=kern)
+        psi, _ = oracle.solve(d, om[None])
+        errs[kern] = np.max(np.abs(psi[0] - exact)) / np.max(np.abs(exact))
+    assert errs["SPECT"] < 0.1 * errs["G2"], errs
+
+
+def test_int_one_minus_j0_hypergeometric_form_matches_quadrature():
+    # the closed form used by the oracle against direct quadrature of the integrand
+    x = np.concatenate([np.linspace(0.0, 50.0, 101), [123.4, 777.7, 2345.6]])
+    np.testing.assert_allclose(green.int_one_minus_j0(x), green.int_one_minus_j0_quad(x), rtol=2e-15, atol=1e-20)
+
+
+def test_int_one_minus_j0_closed_forms():
+    # F(x) = int_0^x (1 - J0(t)) / t dt: series x^2/8 - x^4/256 for small x, and
+    # F(x) - ln(x/2) - gamma = int_x^inf J0(t)/t dt -> -J1(x)/x + 2 J0(x)/x^2 for large x
+    F = lambda v: float(green.int_one_minus_j0(np.array([v]))[0])
+    for v in (1e-3, 2e-2):
+        assert abs(F(v) - (v * v / 8 - v ** 4 / 256 + v ** 6 / 13824)) < 1e-14 * v * v
+    for v in (300.0, 1500.0):
+        tail = -special.j1(v) / v + 2 * special.j0(v) / v ** 2
+        assert abs(F(v) - math.log(v / 2) - 0.5772156649015329 - tail) < 10.0 / v ** 3
