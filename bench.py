@@ -98,9 +98,9 @@ def kernel_bytes(n: int, elem: int = 4):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fyz launch of this
-# workload (256^3 curl, split z stage), from the ncu capture summarised in
-# profiles/k_fyz_c3_256.md; None when the kernel has changed since.
-K_FYZ_TRAFFIC_256 = 474_517_504 + 987_640_832
+# workload (256^3 curl, parity-split y / z stages), from the ncu capture
+# summarised in profiles/k_fyz_c3_256.md; None when the kernel has changed since.
+K_FYZ_TRAFFIC_256 = 472_875_776 + 944_158_976
 
 
 def read_peaks():
