@@ -745,13 +745,14 @@ __device__ __forceinline__ void fast_yi(const Prob<float> &P, const FastGeo &g, 
 
 // persistent YZ executor over the slab work list (same queue / bounded-wait
 // protocol as k_exec).  The pass table is packed into shared memory at start.
-// Thread 0 prepares the next item while the other warps finish the current
-// tile: once its own warp's share of tile k is done it decodes item k + 1
-// (claimed one tile earlier) and probes that item's dependency counters once,
-// without blocking (item k + 1 may depend on the very tile this CTA is still
-// finishing).  The end-of-tile barrier then both completes tile k and
-// publishes the prepared descriptor, so an item whose dependencies were met
-// at the probe starts without a second barrier; otherwise thread 0 waits
+// Thread 0 prepares the next item during the current tile: at the start of
+// tile k it decodes item k + 1 (claimed one tile earlier) and issues the loads
+// of that item's dependency counters, whose L2 round trip then overlaps the
+// tile; at the end of tile k it checks the loaded counts, without blocking
+// (item k + 1 may depend on the very tile this CTA is still finishing), and
+// claims the item after it.  The end-of-tile barrier then both completes tile
+// k and publishes the prepared descriptor, so an item whose dependencies were
+// met at the probe starts without a second barrier; otherwise thread 0 waits
 // (bounded) while the CTA holds at one extra barrier.  Thread 32 publishes
 // the completed tile with a release reduction after the barrier.  The
 // descriptor is double-buffered: slot k & 1 is read during tile k while slot
@@ -771,7 +772,6 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS >= 2 ? 2 : 1)
   __shared__ __align__(16) Prob<float> sP;
   __shared__ FPass sPass[2];
   __shared__ int s_item[2], s_pass[2], s_ok[2], s_ready[2];
-  __shared__ unsigned long long s_tprep[2];
   load_prob<float>(sP, probs, io);
   constexpr int MM = fast_yz_lines(OPS);  // interleaved lines per warp (warp buffer depth)
   V *wsm_all = reinterpret_cast<V *>(fsm);
@@ -793,17 +793,18 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS >= 2 ? 2 : 1)
   int next_it = 0;  // thread 0: item claimed one tile ahead (the queue round trip overlaps a tile)
   int cur = 0;      // thread 0: pass of the last item (items arrive in increasing order)
 
-  // thread 0: decode the claimed item into slot k, claim the one after it and
-  // probe the item's dependency counters once
-  auto prepare = [&](int k) {
+  // thread 0: decode the claimed item into slot k and issue the loads of its
+  // dependency counters (early: at the start of the current tile, so that
+  // their L2 round trip overlaps the tile); the values are checked by
+  // finish_claim at the end of the tile, which then claims the item after it
+  unsigned probe[2] = {0u, 0u}, need[2] = {0u, 0u};
+  auto decode_issue = [&](int k) {
     const int it = next_it;
-    if (it < total) next_it = (int)atomicAdd(&ctl->next, 1u);
     s_item[k] = it;
     s_ok[k] = 1;
     s_ready[k] = 1;
+    probe[0] = probe[1] = need[0] = need[1] = 0u;
     if (it >= total) return;
-    const unsigned long long t0 = global_ns();
-    s_tprep[k] = t0;
     while (s_start[cur + 1] <= it) ++cur;
     const int lo = cur;
     FPass &sp = sPass[k];
@@ -816,18 +817,25 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS >= 2 ? 2 : 1)
     sp.dep[0] = (b & 0xffff) - 1;
     sp.dep[1] = ((b >> 16) & 0xffff) - 1;
     s_pass[k] = lo;
-    bool ready = true;
     for (int d = 0; d < 2; ++d) {
       const int dp = sp.dep[d];
-      if (dp >= 0 && ld_acquire(&done[dp]) < (unsigned)(s_start[dp + 1] - s_start[dp])) ready = false;
+      if (dp >= 0) {
+        need[d] = (unsigned)(s_start[dp + 1] - s_start[dp]);
+        probe[d] = ld_acquire(&done[dp]);
+      }
     }
-    s_ready[k] = ready ? 1 : 0;
-    if (ready) atomicAdd(&ctl->wait_ns[a & 3], global_ns() - t0);
   };
-  // thread 0: bounded wait for the dependencies of the item in slot k
+  auto finish_claim = [&](int k) {
+    if (s_item[k] >= total) return;
+    const bool ready = probe[0] >= need[0] && probe[1] >= need[1];
+    s_ready[k] = ready ? 1 : 0;  // ready at the first probe: no time is spent waiting
+    next_it = (int)atomicAdd(&ctl->next, 1u);
+  };
+  // thread 0: bounded wait for the dependencies of the item in slot k (the
+  // CTA stalls from here on: the time is recorded as waiting)
   auto wait_deps = [&](int k) {
     const FPass &sp = sPass[k];
-    const unsigned long long tw0 = s_tprep[k];
+    const unsigned long long tw0 = global_ns();
     for (int d = 0; d < 2; ++d) {
       const int dp = sp.dep[d];
       if (dp < 0) continue;
@@ -849,19 +857,21 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS >= 2 ? 2 : 1)
 
   if (threadIdx.x == 0) {
     next_it = (int)atomicAdd(&ctl->next, 1u);
-    prepare(0);
+    decode_issue(0);
+    finish_claim(0);
   }
   __syncthreads();
   for (int k = 0;; k ^= 1) {
     const int it = s_item[k];
     if (it >= total) break;
-    // read before the slot can be rewritten (prepare(k) runs two tiles later)
+    // read before the slot can be rewritten (decode_issue(k) runs at the next tile's start)
     const int my_pass = s_pass[k];
     const int my_kind = sPass[k].kind;
     if (!s_ready[k]) {  // uniform over the CTA
       if (threadIdx.x == 0) wait_deps(k);
       __syncthreads();
     }
+    if (threadIdx.x == 0) decode_issue(k ^ 1);  // the item after this one (claimed one tile ago)
     unsigned long long t_start = 0;  // thread 32: start of the tile (tracing)
     if (threadIdx.x == 32) t_start = global_ns();
     if (s_ok[k]) {
@@ -882,7 +892,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, OPS >= 2 ? 2 : 1)
         else fast_yi<E, PAD>(sP, g, ps, tile, wsm, T);
       }
     }
-    if (threadIdx.x == 0) prepare(k ^ 1);
+    if (threadIdx.x == 0) finish_claim(k ^ 1);
     __syncthreads();
     if (threadIdx.x == 32) {
       red_release_add(&done[my_pass], 1u);  // publishes the tile (cumulative over the barrier above)

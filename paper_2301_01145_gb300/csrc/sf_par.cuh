@@ -256,10 +256,36 @@ __device__ __forceinline__ void par_zs(const Prob<float> &P, int S, size_t slot_
     for (int uu = 0; uu < 16; ++uu) xd[17 * uu] = v[uu];
   }
   __syncthreads();
+  if (c == 2) {
+    // no d/dz output: thread (l, u, p) takes one parity of psi into the free d/dz
+    // region, then every thread sums half a line's points of both parities and stores
+    const int lo = threadIdx.x & 7, u = (threadIdx.x >> 3) & 15, p = threadIdx.x >> 7;
+    float2 w[16];
+    const float2 *xs = X + (p * SF_PAR_ZS_ROWS + lo) * SF_PAR_LS8 + 17 * u;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) w[q] = xs[q];
+    if (p) par_inv2<1>(w);
+    else par_inv2<0>(w);
+    float2 *xd = X + ((2 + p) * SF_PAR_ZS_ROWS + lo) * SF_PAR_LS8 + 17 * u;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) xd[q] = w[q];
+    __syncthreads();
+    const int hs = p;  // this thread stores s in [8 hs, 8 hs + 8)
+    const float2 *y0 = X + (2 * SF_PAR_ZS_ROWS + lo) * SF_PAR_LS8 + 17 * u;
+    const float2 *y1 = X + (3 * SF_PAR_ZS_ROWS + lo) * SF_PAR_LS8 + 17 * u;
+    float2 *I2 = reinterpret_cast<float2 *>(P.I2) + slot_off + (((size_t)2 * S + kxl) * nuz) * 512 + ky0 + lo;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int sidx = 8 * hs + q;
+      const int z = u + 16 * sidx;
+      if (z < nuz) __stcg(&I2[(size_t)z * 512], cadd(y0[sidx], y1[sidx]));
+    }
+    return;
+  }
   {
     // inverse stage 2: thread (l, u, o), l fastest; both parities summed; rows of I2 along k'y
     const int lo = threadIdx.x & 7, u = (threadIdx.x >> 3) & 15, o = threadIdx.x >> 7;
-    if (o == 0 || c < 2) {
+    {
       float2 acc[16];
       {
         const float2 *xs = X + ((2 * o) * SF_PAR_ZS_ROWS + lo) * SF_PAR_LS8 + 17 * u;
