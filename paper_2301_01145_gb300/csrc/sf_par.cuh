@@ -91,17 +91,13 @@ __device__ __forceinline__ float par_kap(int p, int m, float kap1) {
 #define SF_PAR_YI_ROWS 16  // z rows per YI tile
 #define SF_PAR_LS16 273    // line stride (complex) of a 16-line exchange buffer (odd: conflict-free)
 #define SF_PAR_LS8 274     // line stride of an 8-line exchange buffer (2 mod 16)
-#define SF_PAR_GS 257      // floats per staged Green's row (1 mod 32)
 
-// shared memory of the parity tiles (bytes): the largest of YF / YI (two
-// parities x 16 lines) and ZS (two outputs x two parities x 8 lines, then 8
-// Green's rows)
+// shared memory of the parity tiles (bytes): the larger of YF / YI (two
+// parities x 16 lines) and ZS (two outputs x two parities x 8 lines)
 __host__ __device__ constexpr int par_ex16_elems() { return 2 * 16 * SF_PAR_LS16; }
 __host__ __device__ constexpr int par_zs_ex_elems() { return 2 * 2 * SF_PAR_ZS_ROWS * SF_PAR_LS8; }
 __host__ __device__ constexpr size_t par_smem_bytes() {
-  return (par_zs_ex_elems() * 8 + SF_PAR_ZS_ROWS * SF_PAR_GS * 4 > par_ex16_elems() * 8)
-             ? (size_t)par_zs_ex_elems() * 8 + SF_PAR_ZS_ROWS * SF_PAR_GS * 4
-             : (size_t)par_ex16_elems() * 8;
+  return (size_t)(par_zs_ex_elems() > par_ex16_elems() ? par_zs_ex_elems() : par_ex16_elems()) * 8;
 }
 
 // ---------------------------------------------------------------------------
@@ -180,20 +176,6 @@ __device__ __forceinline__ void par_zs(const Prob<float> &P, int S, size_t slot_
   const int kx = kx0 + kxl;
   const int ky0 = iy * SF_PAR_ZS_ROWS;
   const float2 *twp = P.ax[2].twf + SF_TWP_OFF;
-  float *gs = reinterpret_cast<float *>(X + par_zs_ex_elems());
-  // Green's rows of the 8 lines (k'y = 256 p + m is FFT index 2 m + p, folded
-  // to |ky|), staged by asynchronous copies while stage 1 runs
-  {
-    // one warp per row (8 warps, 8 rows)
-    static_assert(SF_PAR_ZS_ROWS * 32 == SF_PAR_THREADS, "one warp per Green's row");
-    const int l = threadIdx.x >> 5;
-    const int kyp = ky0 + l;
-    const int ky = 2 * (kyp & 255) + (kyp >> 8);
-    const int kyf = min(ky, 512 - ky);
-    const float *grow = P.ghat_t + ((size_t)kx * P.gny + kyf) * P.gnz;
-    for (int i = threadIdx.x & 31; i < P.gnz; i += 32) cp_async4(gs + l * SF_PAR_GS + i, grow + i);
-    cp_async_commit();
-  }
   const float2 *I1 = reinterpret_cast<const float2 *>(P.I1) + slot_off + (((size_t)c * S + kxl) * 512) * nuz;
   {
     // stage 1: warp-uniform parity pz = warp / 4; half-warp line l
@@ -213,7 +195,6 @@ __device__ __forceinline__ void par_zs(const Prob<float> &P, int S, size_t slot_
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) xd[17 * k1] = v[k1];
   }
-  cp_async_wait_all();
   __syncthreads();
   // stage 2 + multiply + inverse stage 1: thread (k1, l, pz), k1 fastest
   const int k1 = threadIdx.x & 15, l = (threadIdx.x >> 4) & 7, pz = threadIdx.x >> 7;
@@ -227,10 +208,15 @@ __device__ __forceinline__ void par_zs(const Prob<float> &P, int S, size_t slot_
   dft16<false>(v);
   {
     // Green's table at kz = 2 (k1 + 16 k2) + pz, folded to min(kz, 512 - kz)
-    const float *g = gs + l * SF_PAR_GS;
+    // read straight from the table (L1 / L2): a half-warp reads 16 values two
+    // floats apart, and staging the rows in shared memory first cost more
+    // (twice the L1 traffic and a wait before the barrier)
     const int lo = 2 * k1 + pz, hi = 512 - 2 * k1 - pz;
+    const int kyp = ky0 + l;
+    const int ky = 2 * (kyp & 255) + (kyp >> 8);
+    const float *g = P.ghat_t + ((size_t)kx * P.gny + min(ky, 512 - ky)) * P.gnz;
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) v[k2] = cscale(v[k2], g[k2 < 8 ? lo + 32 * k2 : hi - 32 * k2]);
+    for (int k2 = 0; k2 < 16; ++k2) v[k2] = cscale(v[k2], __ldg(&g[k2 < 8 ? lo + 32 * k2 : hi - 32 * k2]));
   }
   if (c < 2) {
     const float kz1 = __ldg(&P.ax[2].kap[1]);
