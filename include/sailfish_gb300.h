@@ -269,8 +269,8 @@ int sf_plan_launches(sf_plan p);
 /* Tracing of the last persistent-executor launch of a plan (waits for the
  * plan's stream).  For each of up to 8 pass kinds k (register path: 0 = y
  * forward, 1 = z stage, 2 = y inverse; general engine: the pass kind of the
- * tile, kinds 8 and 9 -- the 1D multiply and the derivative passes -- counted
- * with kinds 0 and 1): out[3k] = summed tile time (ns, over all CTAs),
+ * tile, kinds 8, 9 and 10 -- the 1D multiply and the derivative passes --
+ * counted with kinds 0, 1 and 2): out[3k] = summed tile time (ns, over all CTAs),
  * out[3k+1] = summed time spent waiting for dependencies (ns), out[3k+2] =
  * tiles.  out must hold 24 doubles.  The paper times the solve steps separately (Sec. 5.3); this is
  * the per-pass breakdown of the GPU schedule. */

@@ -317,6 +317,8 @@ template <typename T> int pass_tiles(const Prob<T> &P, const Pass<T> &ps) {
       const int nlines = P.ax[a == 0 ? 1 : 0].nodes * P.ax[a == 2 ? 1 : 2].nodes;
       return cdiv(nlines, 2 * W);
     }
+    case PK_DXINV:  // every (y, z) node line
+      return (P.dim == 3 ? P.ax[2].nodes : 1) * cdiv(P.dim >= 2 ? P.ax[1].nodes : 1, 2 * W);
   }
   return 0;
 }
@@ -328,6 +330,7 @@ template <typename T> void size_pass(const Prob<T> &P, Pass<T> &ps, int wcap) {
   switch (ps.kind) {
     case PK_XFWD: L = P.ax[0].L; lines = cdiv(P.nuy, 2); break;
     case PK_XINV: L = P.ax[0].L; lines = cdiv(P.nuy, 2); break;
+    case PK_DXINV: L = P.ax[0].L; lines = cdiv(P.dim >= 2 ? P.ax[1].nodes : 1, 2); break;
     case PK_YFWD:
     case PK_YINV: L = P.ax[1].L; lines = P.cpath ? P.nuz : cdiv(P.nuz, 2); break;
     case PK_ZSTAGE: L = P.ax[2].L; nbuf = P.ncomp + 2; lines = P.cpath ? P.nsy : cdiv(P.nsy, 2); break;
@@ -1041,12 +1044,15 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
     eI = (size_t)geo.nslot * nf * geo.S * p.ax[1].L * p.nuz;
   }
   SF_TRY(mem.alloc(&p.A, eA * esz));
-  SF_TRY(mem.alloc(&p.B, eA * esz));
+  // B also holds the y-derivative terms of a 2D operator on Dirichlet / Neumann
+  // axes, indexed by y node (up to two more per line than the unknowns)
+  const size_t eB = eA + (size_t)nf * p.nsx * p.nuz * 2;
+  SF_TRY(mem.alloc(&p.B, eB * esz));
   if (eI) {
     SF_TRY(mem.alloc(&p.I1, eI * esz));
     SF_TRY(mem.alloc(&p.I2, eI * esz));
   }
-  ws_bytes = (2 * eA + 2 * eI) * esz;
+  ws_bytes = (eA + eB + 2 * eI) * esz;
   void *tmp;
   SF_TRY(mem.alloc(&tmp, sizeof(ExecCtl)));
   ctl = (ExecCtl *)tmp;
@@ -1089,6 +1095,17 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
     p.dphase[a] = reinterpret_cast<const cx<T> *>(dph);
     p.kunit[a] = (T)(2.0 * kPi / (ah[a].L * ah[a].h));
   }
+  // 2D operators on Dirichlet / Neumann axes: their y-derivative terms are
+  // formed in the y stage (term order: outputs, then components)
+  p.nyt = 0;
+  if (!p.cpath && d.dim == 2 && d.op != SF_OP_NONE && d.op != SF_OP_NABLA)
+    for (int o = 0; o < p.nop; ++o)
+      for (int c = 0; c < p.ncomp; ++c)
+        if ((p.opc[o][c] == 1 || p.opc[o][c] == -1) && p.opa[o][c] == 1 && p.nyt < SF_MAXYT) {
+          p.yt_comp[p.nyt] = c;
+          p.yt_sgn[p.nyt] = p.opc[o][c];
+          ++p.nyt;
+        }
   // forward / adjoint variants
   p.nin = p.ncomp;
   p.nout = (p.cpath || d.op == SF_OP_NABLA) ? nf : p.ncomp;
@@ -1099,6 +1116,7 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   PA.nin = deriv_ops ? p.ncomp : nf;  // derivative operators: their gradients enter through h
   PA.nout = p.ncomp;
   PA.adjoint = 1;
+  PA.nyt = 0;
   for (int a = 0; a < d.dim; ++a)
     if (p.ax[a].kind == AK_NR || p.ax[a].kind == AK_DNR || p.ax[a].kind == AK_NDR) PA.nrw = 1;
   SF_TRY(mem.alloc(&tmp, 2 * sizeof(Prob<T>)));
@@ -1123,13 +1141,22 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
     const int xinv = (int)ex.passes.size() - 1;
     if (Q.fill_count) ex.add(Q, PK_FILL, 0);
     if (Q.cpath || Q.op == OPK_NONE || Q.op == OPK_NABLA || Q.adjoint) return;
-    // operator outputs on Dirichlet / Neumann axes: derivative terms of psi,
-    // the terms of one output chained (the first writes, the others add)
+    // operator outputs on Dirichlet / Neumann axes: derivative terms, the
+    // terms of one output chained (the first writes, the others add).  An x
+    // derivative is formed from B, where x is still spectral (PK_DXINV); a y
+    // or z derivative is a pass over the computed psi (PK_DERIV)
+    int yt = 0;  // y-derivative terms of the 2D y stage, in its order
     for (int o = 0; o < Q.nop; ++o) {
       int prev = -1;
       auto term = [&](int ax, int c, int order, int sign) {
-        const int args[6] = {ax, c, o, order, sign, prev >= 0 ? 1 : 0};
-        ex.add(Q, PK_DERIV, 0, xinv, prev, args);
+        if (ax == 1 && yt < Q.nyt) {
+          const int args[6] = {ax, yt++, o, 4, sign, prev >= 0 ? 1 : 0};
+          ex.add(Q, PK_DXINV, 0, dep, prev, args);
+        } else {
+          const int args[6] = {ax, c, o, order, sign, prev >= 0 ? 1 : 0};
+          if (ax == 0) ex.add(Q, PK_DXINV, 0, dep, prev, args);
+          else ex.add(Q, PK_DERIV, 0, xinv, prev, args);
+        }
         prev = (int)ex.passes.size() - 1;
       };
       for (int c = 0; c < Q.ncomp; ++c)

@@ -257,6 +257,7 @@ enum PassKind : int {
   PK_ZFWD = 7,     // forward-only z transform (Green's table set-up): I1 -> fwd_out
   PK_MULT1D = 8,   // 1D: multiply and operator in x-spectral space: A -> B
   PK_DERIV = 9,    // Dirichlet / Neumann axes: one derivative term of an operator output
+  PK_DXINV = 10,   // Dirichlet / Neumann x axis: one x-derivative term, inverse x from B
 };
 
 template <typename T> struct Axis {
@@ -279,6 +280,7 @@ template <typename T> struct Axis {
 };
 
 #define SF_MAXF 6
+#define SF_MAXYT 4  // y-derivative terms of a 2D operator (at most one per component and output)
 
 template <typename T> struct Prob {
   int dim, ncomp, nop;
@@ -311,6 +313,10 @@ template <typename T> struct Prob {
   int dkind[3], du0[3], dnu[3], dk0[3], dns[3];
   const cx<T> *dphase[3];
   T kunit[3];
+  // 2D: y-derivative terms of the operator outputs, formed in the y stage in
+  // the dual basis of y and stored after the psi fields of B as [t][kx][y node]
+  int nyt;
+  int yt_comp[SF_MAXYT], yt_sgn[SF_MAXYT];
 };
 
 template <typename T> struct Pass {
@@ -323,7 +329,7 @@ template <typename T> struct Pass {
   int bufsz;  // complex elements per shared buffer
   int dep[2];
   int depcnt[2];
-  int arg[6];  // PK_DERIV: axis, psi component, output, order (1, 2), sign, accumulate
+  int arg[6];  // PK_DERIV / PK_DXINV: axis, psi component, output, order (1, 2, 3), sign, accumulate
 };
 
 // executor control block (device)

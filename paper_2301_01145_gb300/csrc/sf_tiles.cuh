@@ -436,9 +436,11 @@ __device__ void stage_multiply_c(const Prob<T> &P, cx<T> **bufs, int nl, int W, 
 // Geometry of one stage tile: nl lines of the transform axis.
 //   load(c, j, q)  -> data point q of line j of input field c (complex or real)
 //   store(f, j, q, v) writes data point q of line j of output field f
-template <typename T, bool CP, bool LINE_FAST, typename LoadC, typename LoadR, typename StoreC, typename StoreR, typename KOf>
+//   storet(t, j, n, v) writes node n of line j of y-derivative term t (2D real path)
+template <typename T, bool CP, bool LINE_FAST, typename LoadC, typename LoadR, typename StoreC, typename StoreR,
+          typename KOf, typename StoreT>
 __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, int nl, cx<T> *sm, size_t bufsz,
-                          LoadC loadc, LoadR loadr, StoreC storec, StoreR storer, KOf kof) {
+                          LoadC loadc, LoadR loadr, StoreC storec, StoreR storer, KOf kof, StoreT storet) {
   typedef cx<T> V;
   const int L = ax.L;
   const int ncomp = P.ncomp;
@@ -522,8 +524,11 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
   } else {
     // real path: two real lines per packed line; multiply coefficient-wise.
     // NABLA (no basis change on Dirichlet / Neumann axes) is formed here as a
-    // spectral output, -|kappa|^2 psi^, in the spare buffer; first derivatives
-    // are derivative passes over psi (PK_DERIV).
+    // spectral output, -|kappa|^2 psi^, in the spare buffer.  In 2D the
+    // y-derivative terms of the other operators are formed here too, in the
+    // spare buffer and the dual basis of y (sine <-> cosine, the same
+    // wavenumbers), and stored by node (storet); x derivatives are formed from
+    // B (PK_DXINV) and 3D y / z derivatives are passes over psi (PK_DERIV).
     const int Wl = cdiv(nl, 2);
     const bool nabla = P.op == OPK_NABLA && !P.adjoint;
     const bool nabla_adj = P.op == OPK_NABLA && P.adjoint;  // psi gradient += -|kappa|^2 (operator gradient)
@@ -583,6 +588,53 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
         }
       }
       __syncthreads();
+      for (int yt = 0; yt < P.nyt; ++yt) {
+        if (P.adjoint || P.yt_comp[yt] != c) continue;  // uniform over the block
+        Axis<T> Dy = ax;  // the dual basis of y
+        Dy.kind = P.dkind[1];
+        Dy.u0 = P.du0[1];
+        Dy.nu = P.dnu[1];
+        Dy.k0 = P.dk0[1];
+        Dy.ns = P.dns[1];
+        Dy.phase = P.dphase[1];
+        const bool dlike = ax.kind == AK_DR || ax.kind == AK_DS || ax.kind == AK_DNR || ax.kind == AK_DNS;
+        const T sgn = (T)P.yt_sgn[yt];
+        V *at = bufs[ncomp];  // the spare buffer (the FFT below may exchange it with the scratch)
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+          const int l = e % Wl, k = e / Wl;
+          const int ci = mixed ? ((k & 1) ? (k >> 1) : -1) : k - ax.k0;
+          const int cd = mixed ? ci : k - Dy.k0;
+          V za = czero<V>(), zb = czero<V>();
+          if (ci >= 0 && ci < ax.ns && cd >= 0 && cd < Dy.ns) {
+            const V zk = a[k * Wp + l];
+            const V zm = a[((L - k) % L) * Wp + l];
+            const V ea = mk<V>((zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5);
+            const V eb = mk<V>((zk.y + zm.y) * (T)0.5, -(zk.x - zm.x) * (T)0.5);
+            const V ph = ax.phase[k];
+            const T kap = P.kunit[1] * (T)k;
+            const T fac = sgn * (dlike ? kap : -kap) * ((mixed && (ci & 1)) ? (T)-1 : (T)1);
+            const T ca = (ea.x * ph.x + ea.y * ph.y) * fac, cb = (eb.x * ph.x + eb.y * ph.y) * fac;
+            const V pd = Dy.phase[k];
+            const V da = cscale(pd, ca), db = cscale(pd, cb);
+            za = mk<V>(da.x - db.y, da.y + db.x);
+            zb = mk<V>(da.x + db.y, db.x - da.y);
+          }
+          at[k * Wp + l] = za;
+          if (k >= 1 && k <= half - 1) at[(L - k) * Wp + l] = zb;
+        }
+        __syncthreads();
+        fft_lines<T, true>(bufs[ncomp], scr, Dy, W, Wp);
+        const V *r = bufs[ncomp];
+        const int nodes = ax.nodes;
+        const int cnt2 = nl * nodes;
+        for (int e = threadIdx.x; e < cnt2; e += blockDim.x) {
+          const int j = e / nodes, n = e - j * nodes;
+          T v = 0;
+          if (n >= Dy.u0 && n < Dy.u0 + Dy.nu) v = get_ext_r<T>(r, Dy, Wp, j, n - Dy.u0);
+          storet(yt, j, n, v);
+        }
+        __syncthreads();
+      }
       inv_field(c, c);
       if (nabla) inv_field(ncomp, ncomp + c);
     }
@@ -616,7 +668,7 @@ template <typename T> __device__ void tile_zstage(const Prob<T> &P, const Pass<T
         [&](int f, int j, int q) -> V { return __ldcg(&in[f * fstride + base + (size_t)q * nsy + j]); },
         [&](int, int, int) -> T { return (T)0; },
         [&](int f, int j, int q, V v) { __stcg(&out[f * fstride + base + (size_t)q * nsy + j], v); },
-        [&](int, int, int, T) {}, kof);
+        [&](int, int, int, T) {}, kof, [&](int, int, int, T) {});
   } else {
     const T *in = reinterpret_cast<const T *>(P.I1);
     T *out = reinterpret_cast<T *>(P.I2);
@@ -624,7 +676,8 @@ template <typename T> __device__ void tile_zstage(const Prob<T> &P, const Pass<T
         P, Z, W, Wp, nl, sm, bufsz, [&](int, int, int) -> V { return czero<V>(); },
         [&](int f, int j, int q) -> T { return __ldcg(&in[f * fstride + base + (size_t)q * nsy + j]); },
         [&](int, int, int, V) {},
-        [&](int f, int j, int q, T v) { __stcg(&out[f * fstride + base + (size_t)q * nsy + j], v); }, kof);
+        [&](int f, int j, int q, T v) { __stcg(&out[f * fstride + base + (size_t)q * nsy + j], v); }, kof,
+        [&](int, int, int, T) {});
   }
 }
 
@@ -651,7 +704,7 @@ template <typename T> __device__ void tile_ystage2(const Prob<T> &P, const Pass<
         [&](int f, int j, int q) -> V { return __ldcg(&in[f * fstride + base + (size_t)j * nuy + q]); },
         [&](int, int, int) -> T { return (T)0; },
         [&](int f, int j, int q, V v) { __stcg(&out[f * fstride + base + (size_t)j * nuy + q], v); },
-        [&](int, int, int, T) {}, kof);
+        [&](int, int, int, T) {}, kof, [&](int, int, int, T) {});
   } else {
     const T *in = reinterpret_cast<const T *>(P.A);
     T *out = reinterpret_cast<T *>(P.B);
@@ -659,7 +712,11 @@ template <typename T> __device__ void tile_ystage2(const Prob<T> &P, const Pass<
         P, Y, W, Wp, nl, sm, bufsz, [&](int, int, int) -> V { return czero<V>(); },
         [&](int f, int j, int q) -> T { return __ldcg(&in[f * fstride + base + (size_t)j * nuy + q]); },
         [&](int, int, int, V) {},
-        [&](int f, int j, int q, T v) { __stcg(&out[f * fstride + base + (size_t)j * nuy + q], v); }, kof);
+        [&](int f, int j, int q, T v) { __stcg(&out[f * fstride + base + (size_t)j * nuy + q], v); }, kof,
+        // y-derivative terms after the psi fields, [t][kx][y node]
+        [&](int yt, int j, int n, T v) {
+          __stcg(&out[(size_t)P.ncomp * fstride + ((size_t)yt * nsx + kx0 + j) * Y.nodes + n], v);
+        });
   }
 }
 
@@ -1004,6 +1061,104 @@ template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T>
   }
 }
 
+// ---------------------------------------------------------------------------
+// DXINV: one derivative term of an operator output on Dirichlet / Neumann
+// axes, formed where its axis is still spectral, then inverse transformed
+// along x and added to (or written as) the output.
+//  order 1, x derivative: from B, the x coefficients of psi_c are scaled by
+//    sign * kappa, moved to the dual basis (sine <-> cosine, the same
+//    wavenumbers; (-1)^m between the quarter-wave pair's doubled-axis
+//    representations) and inverse transformed in that basis (the series
+//    derivative of reading Z13 of Sec. 2.4.3).
+//  order 4, 2D y derivative: term t of the y stage (already in the dual basis
+//    of y, stored by y node after the psi fields of B) inverse transformed in
+//    psi's own x basis.
+// Formed this way, a term's rounding scales with the term itself; a pass over
+// the computed psi (PK_DERIV) weights psi's rounding by kappa.  The tile covers
+// every (y, z) node line: lines through regular Dirichlet face nodes, and x
+// nodes outside the basis's unknowns, are zero (the series vanishes there).
+// acc = 1 adds the term.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ void tile_dxinv(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
+  typedef cx<T> V;
+  const int src_i = ps.arg[1], o = ps.arg[2], order = ps.arg[3], sgn = ps.arg[4], acc = ps.arg[5];
+  const bool yterm = order == 4;
+  const Axis<T> &X = P.ax[0], &Y = P.ax[1], &Z = P.ax[2];
+  Axis<T> Dx = X;  // the dual basis of x
+  Dx.kind = P.dkind[0];
+  Dx.u0 = P.du0[0];
+  Dx.nu = P.dnu[0];
+  Dx.k0 = P.dk0[0];
+  Dx.ns = P.dns[0];
+  Dx.phase = P.dphase[0];
+  const Axis<T> &Ai = yterm ? X : Dx;  // basis of the output lines
+  const int W = ps.W, Wp = ps.Wp, RL = 2 * W;
+  const int nuy = P.nuy, nuz = P.nuz, nsx = P.nsx;
+  const int ndx = X.nodes;
+  const int ndy = P.dim >= 2 ? Y.nodes : 1, ndz = P.dim == 3 ? Z.nodes : 1;
+  const int yu0 = P.dim >= 2 ? Y.u0 : 0, zu0 = P.dim == 3 ? Z.u0 : 0;
+  const int ty = cdiv(ndy, RL);
+  const int iy = t % ty;
+  const int zn = t / ty;
+  if (zn >= ndz) return;
+  const int yn0 = iy * RL;
+  const int nl = min(RL, ndy - yn0);
+  const int qz = zn - zu0;
+  const bool zin = qz >= 0 && qz < nuz;
+  V *a = sm, *stg = sm + bufsz;
+  T *stgr = reinterpret_cast<T *>(stg);
+  const T *in = reinterpret_cast<const T *>(P.B);
+  const size_t plane = (size_t)nuz * nuy;
+  // the transposed block [kx][r]: psi_c's x coefficients on the unknown y / z
+  // lines, or term t's on every y node line
+  const int cnt = nsx * RL;
+  if (yterm) {
+    const size_t base = (size_t)P.ncomp * nsx * plane + (size_t)src_i * nsx * ndy;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int r = e % RL, kx = e / RL;
+      stgr[e] = r < nl ? __ldcg(&in[base + (size_t)kx * ndy + yn0 + r]) : (T)0;
+    }
+  } else {
+    const size_t base = (size_t)src_i * nsx * plane + (size_t)(zin ? qz : 0) * nuy;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int r = e % RL, kx = e / RL;
+      const int qy = yn0 + r - yu0;
+      stgr[e] = (r < nl && zin && qy >= 0 && qy < nuy) ? __ldcg(&in[base + (size_t)kx * plane + qy]) : (T)0;
+    }
+  }
+  __syncthreads();
+  if (yterm) {
+    build_spec_r<T>(a, X, Wp, W, [&](int j, int ci) -> T { return stgr[ci * RL + j]; });
+  } else {
+    const bool mixed = ak_mixed(X.kind);
+    const bool dlike = X.kind == AK_DR || X.kind == AK_DS || X.kind == AK_DNR || X.kind == AK_DNS;
+    build_spec_r<T>(a, Dx, Wp, W, [&](int j, int cd) -> T {
+      const int k = mixed ? 2 * cd + 1 : cd + Dx.k0;  // FFT index: the same wavenumber in both bases
+      const int ci = mixed ? cd : k - X.k0;
+      if (ci < 0 || ci >= X.ns) return (T)0;
+      const T kap = P.kunit[0] * (T)k;
+      const T fac = (T)sgn * (dlike ? kap : -kap) * ((mixed && (ci & 1)) ? (T)-1 : (T)1);
+      return fac * stgr[ci * RL + j];
+    });
+  }
+  __syncthreads();
+  fft_lines<T, true>(a, stg, Ai, W, Wp);
+  T *dst = P.out_ptr[P.ncomp + o];
+  const int cnt2 = nl * ndx;
+  for (int e = threadIdx.x; e < cnt2; e += blockDim.x) {
+    const int r = e / ndx;
+    const int xn = e - r * ndx;
+    const int yn = yn0 + r;
+    const int qy = yn - yu0;
+    T v = 0;
+    const bool line = yterm || (zin && qy >= 0 && qy < nuy);
+    if (line && xn >= Ai.u0 && xn < Ai.u0 + Ai.nu) v = get_ext_r<T>(a, Ai, Wp, r, xn - Ai.u0);
+    const size_t idx = ((size_t)zn * ndy + yn) * ndx + xn;
+    if (acc) dst[idx] += v;
+    else dst[idx] = v;
+  }
+}
+
 // dispatch one tile of a pass
 template <typename T> __device__ void run_tile(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
   switch (ps.kind) {
@@ -1017,6 +1172,7 @@ template <typename T> __device__ void run_tile(const Prob<T> &P, const Pass<T> &
     case PK_ZFWD: tile_zfwd<T>(P, ps, t, sm, bufsz); break;
     case PK_MULT1D: tile_mult1d<T>(P, ps, t); break;
     case PK_DERIV: tile_deriv<T>(P, ps, t, sm, bufsz); break;
+    case PK_DXINV: tile_dxinv<T>(P, ps, t, sm, bufsz); break;
     default: break;
   }
 }

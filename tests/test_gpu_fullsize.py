@@ -72,8 +72,9 @@ def test_c2_fullsize_elementwise():
 
 def test_c6_fullsize_gradient_on_bounded_axes_elementwise():
     # the 256^3 D/N/D FD2 solve with faces plus the gradient on the bounded axes,
-    # every node against the oracle (derivative bound 2 u n on 257 nodes, see
-    # tests/test_gpu_bounded_ops.py)
+    # every node against the oracle at the stated tolerance (the y and z
+    # derivatives are passes over psi: about 2 u kappa_max / kappa_1 = 3e-5 is
+    # their worst case at 257 nodes; measured 6.5e-6)
     import paper_2301_01145_gb300 as sf
     n = 256
     man = workloads.manufactured(seed_index=1)
@@ -86,9 +87,8 @@ def test_c6_fullsize_gradient_on_bounded_axes_elementwise():
     d = Desc(3, (n,) * 3, (0,) * 3, (1,) * 3, ("D", "N", "D"), False, "FD2", op="GRAD")
     ref, ref_g = oracle.solve(d, case["f"], case["faces"])
     assert rel_l2(to_np(psi)[0], ref[0]) <= TOL["f32"]
-    tol = max(TOL["f32"], 2 * 2.0 ** -24 * (n + 1))
     for a in range(3):
-        assert rel_l2(to_np(grad)[a], ref_g[a]) <= tol, a
+        assert rel_l2(to_np(grad)[a], ref_g[a]) <= TOL["f32"], a
     plan.close()
 
 
@@ -186,6 +186,27 @@ def test_fast_vs_general_engine(n, op, ncomp, fused):
     for generic in (False, True):
         plan = sf.Plan(3, (n,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op=op, ncomp=ncomp, sigma=2.0 / n,
                        rhs_scale=-1.0, fused=fused, generic=generic)
+        out = plan(f)
+        plan.sync()
+        res.append([to_np(o) for o in (out if isinstance(out, tuple) else (out,))])
+        plan.close()
+    for a, b in zip(res[0], res[1]):
+        for c in range(a.shape[0]):
+            assert rel_l2(a[c], b[c]) <= 2e-6
+
+
+@pytest.mark.parametrize("op,ncomp", [("CURL", 3), ("GRAD", 1), ("NONE", 2)])
+def test_fast_ragged_512_vs_general_engine(op, ncomp):
+    # regular grid, 201 x 231 x 255 nodes (all padded to 512): odd row lengths,
+    # a partial 32-line y block ending in a single line, unaligned y pairs
+    import paper_2301_01145_gb300 as sf
+    n = (200, 230, 254)
+    rng = np.random.default_rng(5 + ncomp)
+    f = to_dev(rng.normal(size=(ncomp, n[2] + 1, n[1] + 1, n[0] + 1)), "f32")
+    res = []
+    for generic in (False, True):
+        plan = sf.Plan(3, n, (-0.5, -0.6, -0.55), (0.5, 0.55, 0.6), "UUU", grid="regular", op=op, ncomp=ncomp,
+                       sigma=2.0 / 256, rhs_scale=-1.0, generic=generic)
         out = plan(f)
         plan.sync()
         res.append([to_np(o) for o in (out if isinstance(out, tuple) else (out,))])
