@@ -100,7 +100,7 @@ def kernel_bytes(n: int, elem: int = 4):
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fyz launch of this
 # workload (256^3 curl, parity-split y / z stages), from the ncu capture
 # summarised in profiles/k_fyz_c3_256.md; None when the kernel has changed since.
-K_FYZ_TRAFFIC_256 = 472_875_776 + 944_158_976
+K_FYZ_TRAFFIC_256 = 473_374_720 + 947_329_536
 
 
 def read_peaks():
@@ -543,7 +543,7 @@ def config_case(name: str, world: int = 1, rank: int = 0):
                                "FD2 eigenvalues, inhomogeneous faces (manufactured sin/cos solution)", "grid": n}
         else:
             cfg = {"workload": "3D Dirichlet/Neumann/Dirichlet Poisson 256^3 regular grid, FD2, inhomogeneous "
-                               "faces, plus the gradient on the bounded axes (three derivative passes over psi)",
+                               "faces, plus the gradient on the bounded axes (x from the x-spectral field, y and z passes over psi)",
                    "grid": n}
 
         def check():
