@@ -543,7 +543,7 @@ def config_case(name: str, world: int = 1, rank: int = 0):
                                "FD2 eigenvalues, inhomogeneous faces (manufactured sin/cos solution)", "grid": n}
         else:
             cfg = {"workload": "3D Dirichlet/Neumann/Dirichlet Poisson 256^3 regular grid, FD2, inhomogeneous "
-                               "faces, plus the gradient on the bounded axes (x from the x-spectral field, y and z passes over psi)",
+                               "faces, plus the gradient on the bounded axes (each term formed where its axis is still spectral)",
                    "grid": n}
 
         def check():

@@ -319,6 +319,8 @@ template <typename T> int pass_tiles(const Prob<T> &P, const Pass<T> &ps) {
     }
     case PK_DXINV:  // every (y, z) node line
       return (P.dim == 3 ? P.ax[2].nodes : 1) * cdiv(P.dim >= 2 ? P.ax[1].nodes : 1, 2 * W);
+    case PK_YTERM:  // every z node row of every kx
+      return P.nsx * cdiv(P.ax[2].nodes, 2 * W);
   }
   return 0;
 }
@@ -331,6 +333,7 @@ template <typename T> void size_pass(const Prob<T> &P, Pass<T> &ps, int wcap) {
     case PK_XFWD: L = P.ax[0].L; lines = cdiv(P.nuy, 2); break;
     case PK_XINV: L = P.ax[0].L; lines = cdiv(P.nuy, 2); break;
     case PK_DXINV: L = P.ax[0].L; lines = cdiv(P.dim >= 2 ? P.ax[1].nodes : 1, 2); break;
+    case PK_YTERM: L = P.ax[1].L; lines = cdiv(P.ax[2].nodes, 2); break;
     case PK_YFWD:
     case PK_YINV: L = P.ax[1].L; lines = P.cpath ? P.nuz : cdiv(P.nuz, 2); break;
     case PK_ZSTAGE: L = P.ax[2].L; nbuf = P.ncomp + 2; lines = P.cpath ? P.nsy : cdiv(P.nsy, 2); break;
@@ -1027,6 +1030,26 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
     p.facew[a][0] = (T)(w0 / d.rhs_scale);
     p.facew[a][1] = (T)(w1 / d.rhs_scale);
   }
+  // first-derivative terms of operators on Dirichlet / Neumann axes (reading
+  // Z13), in the order the pass list takes them (outputs, then components): x
+  // terms are formed from B, terms along the stage axis (y in 2D, z in 3D) in
+  // the spectral stage, 3D y terms by the y-inverse term pass
+  p.nst = p.n3yt = 0;
+  if (!p.cpath && d.dim >= 2 && d.op != SF_OP_NONE && d.op != SF_OP_NABLA)
+    for (int o = 0; o < p.nop; ++o)
+      for (int c = 0; c < p.ncomp; ++c) {
+        if (p.opc[o][c] != 1 && p.opc[o][c] != -1) continue;
+        const int ax = p.opa[o][c];
+        if (ax == d.dim - 1 && p.nst < SF_MAXYT) {
+          p.st_comp[p.nst] = c;
+          p.st_sgn[p.nst] = p.opc[o][c];
+          ++p.nst;
+        } else if (d.dim == 3 && ax == 1 && p.n3yt < SF_MAXYT) {
+          p.yt_comp[p.n3yt] = c;
+          p.yt_sgn[p.n3yt] = p.opc[o][c];
+          ++p.n3yt;
+        }
+      }
   // workspace: every buffer sized for ncomp + nop fields (forward and adjoint)
   const int nf = p.ncomp + p.nop;
   const size_t esz = p.cpath ? sizeof(cx<T>) : sizeof(T);
@@ -1044,15 +1067,18 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
     eI = (size_t)geo.nslot * nf * geo.S * p.ax[1].L * p.nuz;
   }
   SF_TRY(mem.alloc(&p.A, eA * esz));
-  // B also holds the y-derivative terms of a 2D operator on Dirichlet / Neumann
-  // axes, indexed by y node (up to two more per line than the unknowns)
-  const size_t eB = eA + (size_t)nf * p.nsx * p.nuz * 2;
+  // the derivative terms follow the psi fields, indexed by node: in B every
+  // term as [t][kx][z node][y node], in I2 (3D) the z terms as [t][kx][z node][ky]
+  const size_t ndy = d.dim >= 2 ? (size_t)p.ax[1].nodes : 1, ndz = d.dim == 3 ? (size_t)p.ax[2].nodes : 1;
+  const size_t eB = std::max(eA, (size_t)p.ncomp * p.nsx * p.nuz * p.nuy + (size_t)(p.nst + p.n3yt) * p.nsx * ndz * ndy);
+  const size_t eI2 = d.dim == 3 ? std::max(eI, (size_t)p.ncomp * p.nsx * p.nuz * p.nsy + (size_t)p.nst * p.nsx * ndz * p.nsy)
+                                : eI;
   SF_TRY(mem.alloc(&p.B, eB * esz));
   if (eI) {
     SF_TRY(mem.alloc(&p.I1, eI * esz));
-    SF_TRY(mem.alloc(&p.I2, eI * esz));
+    SF_TRY(mem.alloc(&p.I2, eI2 * esz));
   }
-  ws_bytes = (eA + eB + 2 * eI) * esz;
+  ws_bytes = (eA + eB + eI + eI2) * esz;
   void *tmp;
   SF_TRY(mem.alloc(&tmp, sizeof(ExecCtl)));
   ctl = (ExecCtl *)tmp;
@@ -1095,17 +1121,6 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
     p.dphase[a] = reinterpret_cast<const cx<T> *>(dph);
     p.kunit[a] = (T)(2.0 * kPi / (ah[a].L * ah[a].h));
   }
-  // 2D operators on Dirichlet / Neumann axes: their y-derivative terms are
-  // formed in the y stage (term order: outputs, then components)
-  p.nyt = 0;
-  if (!p.cpath && d.dim == 2 && d.op != SF_OP_NONE && d.op != SF_OP_NABLA)
-    for (int o = 0; o < p.nop; ++o)
-      for (int c = 0; c < p.ncomp; ++c)
-        if ((p.opc[o][c] == 1 || p.opc[o][c] == -1) && p.opa[o][c] == 1 && p.nyt < SF_MAXYT) {
-          p.yt_comp[p.nyt] = c;
-          p.yt_sgn[p.nyt] = p.opc[o][c];
-          ++p.nyt;
-        }
   // forward / adjoint variants
   p.nin = p.ncomp;
   p.nout = (p.cpath || d.op == SF_OP_NABLA) ? nf : p.ncomp;
@@ -1116,7 +1131,7 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
   PA.nin = deriv_ops ? p.ncomp : nf;  // derivative operators: their gradients enter through h
   PA.nout = p.ncomp;
   PA.adjoint = 1;
-  PA.nyt = 0;
+  PA.nst = PA.n3yt = 0;
   for (int a = 0; a < d.dim; ++a)
     if (p.ax[a].kind == AK_NR || p.ax[a].kind == AK_DNR || p.ax[a].kind == AK_NDR) PA.nrw = 1;
   SF_TRY(mem.alloc(&tmp, 2 * sizeof(Prob<T>)));
@@ -1145,17 +1160,29 @@ template <typename T> sf_status PlanImpl<T>::init(const sf_plan_desc &desc, cuda
     // terms of one output chained (the first writes, the others add).  An x
     // derivative is formed from B, where x is still spectral (PK_DXINV); a y
     // or z derivative is a pass over the computed psi (PK_DERIV)
-    int yt = 0;  // y-derivative terms of the 2D y stage, in its order
+    int ist = 0, iyt = 0;  // stage terms and 3D y terms, in the order of the tables
     for (int o = 0; o < Q.nop; ++o) {
       int prev = -1;
       auto term = [&](int ax, int c, int order, int sign) {
-        if (ax == 1 && yt < Q.nyt) {
-          const int args[6] = {ax, yt++, o, 4, sign, prev >= 0 ? 1 : 0};
+        const int acc = prev >= 0 ? 1 : 0;
+        int tb = -1;  // the term's index in B
+        if (ax == Q.dim - 1 && ist < Q.nst) tb = ist++;
+        else if (Q.dim == 3 && ax == 1 && iyt < Q.n3yt) tb = Q.nst + iyt++;
+        if (ax == 0) {
+          const int args[6] = {0, c, o, order, sign, acc};
           ex.add(Q, PK_DXINV, 0, dep, prev, args);
+        } else if (tb >= 0) {
+          int src = dep;  // 2D: the y stage wrote the term to B
+          if (Q.dim == 3) {
+            const int yargs[6] = {ax, tb, o, 0, 0, 0};
+            ex.add(Q, PK_YTERM, 0, dep, -1, yargs);
+            src = (int)ex.passes.size() - 1;
+          }
+          const int args[6] = {ax, tb, o, 4, sign, acc};
+          ex.add(Q, PK_DXINV, 0, src, prev, args);
         } else {
-          const int args[6] = {ax, c, o, order, sign, prev >= 0 ? 1 : 0};
-          if (ax == 0) ex.add(Q, PK_DXINV, 0, dep, prev, args);
-          else ex.add(Q, PK_DERIV, 0, xinv, prev, args);
+          const int args[6] = {ax, c, o, order, sign, acc};
+          ex.add(Q, PK_DERIV, 0, xinv, prev, args);
         }
         prev = (int)ex.passes.size() - 1;
       };

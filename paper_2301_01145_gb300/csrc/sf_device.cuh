@@ -257,7 +257,8 @@ enum PassKind : int {
   PK_ZFWD = 7,     // forward-only z transform (Green's table set-up): I1 -> fwd_out
   PK_MULT1D = 8,   // 1D: multiply and operator in x-spectral space: A -> B
   PK_DERIV = 9,    // Dirichlet / Neumann axes: one derivative term of an operator output
-  PK_DXINV = 10,   // Dirichlet / Neumann x axis: one x-derivative term, inverse x from B
+  PK_DXINV = 10,   // Dirichlet / Neumann axes: a derivative term's inverse x into the output
+  PK_YTERM = 11,   // Dirichlet / Neumann axes (3D): a derivative term's inverse y into B
 };
 
 template <typename T> struct Axis {
@@ -280,7 +281,7 @@ template <typename T> struct Axis {
 };
 
 #define SF_MAXF 6
-#define SF_MAXYT 4  // y-derivative terms of a 2D operator (at most one per component and output)
+#define SF_MAXYT 4  // derivative terms of one kind along one axis (at most one per component and output)
 
 template <typename T> struct Prob {
   int dim, ncomp, nop;
@@ -313,9 +314,16 @@ template <typename T> struct Prob {
   int dkind[3], du0[3], dnu[3], dk0[3], dns[3];
   const cx<T> *dphase[3];
   T kunit[3];
-  // 2D: y-derivative terms of the operator outputs, formed in the y stage in
-  // the dual basis of y and stored after the psi fields of B as [t][kx][y node]
-  int nyt;
+  // first-derivative terms of the operator outputs along the stage axis (y in
+  // 2D, z in 3D), formed in the spectral stage in that axis's dual basis and
+  // stored by node after the psi fields of the stage's output (B in 2D as
+  // [t][kx][y node], I2 in 3D as [t][kx][z node][ky])
+  int nst;
+  int st_comp[SF_MAXYT], st_sgn[SF_MAXYT];
+  // 3D: y-derivative terms, formed by the y-inverse term pass from psi's y
+  // coefficients in I2; B holds every 3D term after the psi fields as
+  // [t][kx][z node][y node], the stage terms first
+  int n3yt;
   int yt_comp[SF_MAXYT], yt_sgn[SF_MAXYT];
 };
 

@@ -524,11 +524,12 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
   } else {
     // real path: two real lines per packed line; multiply coefficient-wise.
     // NABLA (no basis change on Dirichlet / Neumann axes) is formed here as a
-    // spectral output, -|kappa|^2 psi^, in the spare buffer.  In 2D the
-    // y-derivative terms of the other operators are formed here too, in the
-    // spare buffer and the dual basis of y (sine <-> cosine, the same
-    // wavenumbers), and stored by node (storet); x derivatives are formed from
-    // B (PK_DXINV) and 3D y / z derivatives are passes over psi (PK_DERIV).
+    // spectral output, -|kappa|^2 psi^, in the spare buffer.  The first
+    // derivatives of the other operators along the stage axis are formed here
+    // too, in the spare buffer and that axis's dual basis (sine <-> cosine,
+    // the same wavenumbers), and stored by node (storet); x derivatives are
+    // formed from B (PK_DXINV) and 3D y derivatives by the y-inverse term
+    // pass (PK_YTERM).
     const int Wl = cdiv(nl, 2);
     const bool nabla = P.op == OPK_NABLA && !P.adjoint;
     const bool nabla_adj = P.op == OPK_NABLA && P.adjoint;  // psi gradient += -|kappa|^2 (operator gradient)
@@ -588,17 +589,18 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
         }
       }
       __syncthreads();
-      for (int yt = 0; yt < P.nyt; ++yt) {
-        if (P.adjoint || P.yt_comp[yt] != c) continue;  // uniform over the block
-        Axis<T> Dy = ax;  // the dual basis of y
-        Dy.kind = P.dkind[1];
-        Dy.u0 = P.du0[1];
-        Dy.nu = P.dnu[1];
-        Dy.k0 = P.dk0[1];
-        Dy.ns = P.dns[1];
-        Dy.phase = P.dphase[1];
+      const int sa = P.dim - 1;  // the stage axis
+      for (int st = 0; st < P.nst; ++st) {
+        if (P.adjoint || P.st_comp[st] != c) continue;  // uniform over the block
+        Axis<T> Dy = ax;  // the dual basis of the stage axis
+        Dy.kind = P.dkind[sa];
+        Dy.u0 = P.du0[sa];
+        Dy.nu = P.dnu[sa];
+        Dy.k0 = P.dk0[sa];
+        Dy.ns = P.dns[sa];
+        Dy.phase = P.dphase[sa];
         const bool dlike = ax.kind == AK_DR || ax.kind == AK_DS || ax.kind == AK_DNR || ax.kind == AK_DNS;
-        const T sgn = (T)P.yt_sgn[yt];
+        const T sgn = (T)P.st_sgn[st];
         V *at = bufs[ncomp];  // the spare buffer (the FFT below may exchange it with the scratch)
         for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
           const int l = e % Wl, k = e / Wl;
@@ -611,7 +613,7 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
             const V ea = mk<V>((zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5);
             const V eb = mk<V>((zk.y + zm.y) * (T)0.5, -(zk.x - zm.x) * (T)0.5);
             const V ph = ax.phase[k];
-            const T kap = P.kunit[1] * (T)k;
+            const T kap = P.kunit[sa] * (T)k;
             const T fac = sgn * (dlike ? kap : -kap) * ((mixed && (ci & 1)) ? (T)-1 : (T)1);
             const T ca = (ea.x * ph.x + ea.y * ph.y) * fac, cb = (eb.x * ph.x + eb.y * ph.y) * fac;
             const V pd = Dy.phase[k];
@@ -628,10 +630,11 @@ __device__ void run_stage(const Prob<T> &P, const Axis<T> &ax, int W, int Wp, in
         const int nodes = ax.nodes;
         const int cnt2 = nl * nodes;
         for (int e = threadIdx.x; e < cnt2; e += blockDim.x) {
-          const int j = e / nodes, n = e - j * nodes;
+          int j, n;
+          if (LINE_FAST) { j = e % nl; n = e / nl; } else { n = e % nodes; j = e / nodes; }
           T v = 0;
           if (n >= Dy.u0 && n < Dy.u0 + Dy.nu) v = get_ext_r<T>(r, Dy, Wp, j, n - Dy.u0);
-          storet(yt, j, n, v);
+          storet(st, j, n, v);
         }
         __syncthreads();
       }
@@ -677,7 +680,10 @@ template <typename T> __device__ void tile_zstage(const Prob<T> &P, const Pass<T
         [&](int f, int j, int q) -> T { return __ldcg(&in[f * fstride + base + (size_t)q * nsy + j]); },
         [&](int, int, int, V) {},
         [&](int f, int j, int q, T v) { __stcg(&out[f * fstride + base + (size_t)q * nsy + j], v); }, kof,
-        [&](int, int, int, T) {});
+        // z-derivative terms after the psi fields, [t][kx][z node][ky]
+        [&](int st, int j, int n, T v) {
+          __stcg(&out[(size_t)P.ncomp * fstride + (((size_t)st * nsx + kx) * Z.nodes + n) * nsy + ky0 + j], v);
+        });
   }
 }
 
@@ -714,8 +720,8 @@ template <typename T> __device__ void tile_ystage2(const Prob<T> &P, const Pass<
         [&](int, int, int, V) {},
         [&](int f, int j, int q, T v) { __stcg(&out[f * fstride + base + (size_t)j * nuy + q], v); }, kof,
         // y-derivative terms after the psi fields, [t][kx][y node]
-        [&](int yt, int j, int n, T v) {
-          __stcg(&out[(size_t)P.ncomp * fstride + ((size_t)yt * nsx + kx0 + j) * Y.nodes + n], v);
+        [&](int st, int j, int n, T v) {
+          __stcg(&out[(size_t)P.ncomp * fstride + ((size_t)st * nsx + kx0 + j) * Y.nodes + n], v);
         });
   }
 }
@@ -1070,9 +1076,9 @@ template <typename T> __device__ void tile_deriv(const Prob<T> &P, const Pass<T>
 //    wavenumbers; (-1)^m between the quarter-wave pair's doubled-axis
 //    representations) and inverse transformed in that basis (the series
 //    derivative of reading Z13 of Sec. 2.4.3).
-//  order 4, 2D y derivative: term t of the y stage (already in the dual basis
-//    of y, stored by y node after the psi fields of B) inverse transformed in
-//    psi's own x basis.
+//  order 4, a y or z derivative: term t of B (already inverse transformed
+//    along y and z, stored by node after the psi fields of B as
+//    [t][kx][z node][y node]) inverse transformed in psi's own x basis.
 // Formed this way, a term's rounding scales with the term itself; a pass over
 // the computed psi (PK_DERIV) weights psi's rounding by kappa.  The tile covers
 // every (y, z) node line: lines through regular Dirichlet face nodes, and x
@@ -1113,10 +1119,10 @@ template <typename T> __device__ void tile_dxinv(const Prob<T> &P, const Pass<T>
   // lines, or term t's on every y node line
   const int cnt = nsx * RL;
   if (yterm) {
-    const size_t base = (size_t)P.ncomp * nsx * plane + (size_t)src_i * nsx * ndy;
+    const size_t base = (size_t)P.ncomp * nsx * plane + (size_t)src_i * nsx * ndz * ndy + (size_t)zn * ndy + yn0;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
       const int r = e % RL, kx = e / RL;
-      stgr[e] = r < nl ? __ldcg(&in[base + (size_t)kx * ndy + yn0 + r]) : (T)0;
+      stgr[e] = r < nl ? __ldcg(&in[base + (size_t)kx * ndz * ndy + r]) : (T)0;
     }
   } else {
     const size_t base = (size_t)src_i * nsx * plane + (size_t)(zin ? qz : 0) * nuy;
@@ -1159,6 +1165,84 @@ template <typename T> __device__ void tile_dxinv(const Prob<T> &P, const Pass<T>
   }
 }
 
+// ---------------------------------------------------------------------------
+// YTERM (3D, Dirichlet / Neumann axes): the y inverse of derivative term t of
+// an operator output, stored by node after the psi fields of B as
+// [t][kx][z node][y node] (its x inverse is a PK_DXINV pass of order 4).
+//  t < nst, a z term of the z stage (in I2 after psi's fields as
+//    [t][kx][z node][ky]): inverse y in psi's own y basis.
+//  t >= nst, a y term: psi_c's y coefficients (I2, the unknown z rows) scaled
+//    by sign * kappa and moved to the dual basis of y, inverse y in that basis
+//    (reading Z13 of Sec. 2.4.3); rows through z face nodes are zero.
+// y nodes outside the output basis's unknowns are zero (the series vanishes).
+// ---------------------------------------------------------------------------
+template <typename T> __device__ void tile_yterm(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
+  typedef cx<T> V;
+  const int term = ps.arg[1];
+  const bool yt = term >= P.nst;
+  const int comp = yt ? P.yt_comp[term - P.nst] : 0;
+  const T sgn = yt ? (T)P.yt_sgn[term - P.nst] : (T)0;
+  const Axis<T> &Y = P.ax[1], &Z = P.ax[2];
+  Axis<T> Dy = Y;  // the dual basis of y
+  Dy.kind = P.dkind[1];
+  Dy.u0 = P.du0[1];
+  Dy.nu = P.dnu[1];
+  Dy.k0 = P.dk0[1];
+  Dy.ns = P.dns[1];
+  Dy.phase = P.dphase[1];
+  const Axis<T> &Ai = yt ? Dy : Y;  // basis of the output rows
+  const int W = ps.W, Wp = ps.Wp, RPT = 2 * W;
+  const int nuy = P.nuy, nuz = P.nuz, nsx = P.nsx, nsy = P.nsy;
+  const int ndy = Y.nodes, ndz = Z.nodes;
+  const int tz = cdiv(ndz, RPT);
+  const int iz = t % tz;
+  const int kx = t / tz;
+  if (kx >= nsx) return;
+  const int zn0 = iz * RPT;
+  const int nl = min(RPT, ndz - zn0);
+  V *a = sm, *b = sm + bufsz;
+  const T *I2 = reinterpret_cast<const T *>(P.I2);
+  // row j (z node zn0 + j) of the input coefficients, or null where it is zero
+  auto row = [&](int j) -> const T * {
+    if (j >= nl) return nullptr;
+    const int zn = zn0 + j;
+    if (!yt) return I2 + (size_t)P.ncomp * nsx * nuz * nsy + (((size_t)term * nsx + kx) * ndz + zn) * nsy;
+    const int qz = zn - Z.u0;
+    if (qz < 0 || qz >= nuz) return nullptr;
+    return I2 + (((size_t)comp * nsx + kx) * nuz + qz) * nsy;
+  };
+  if (!yt) {
+    build_spec_r<T>(a, Y, Wp, W, [&](int j, int ci) -> T {
+      const T *r = row(j);
+      return r ? __ldcg(&r[ci]) : (T)0;
+    });
+  } else {
+    const bool mixed = ak_mixed(Y.kind);
+    const bool dlike = Y.kind == AK_DR || Y.kind == AK_DS || Y.kind == AK_DNR || Y.kind == AK_DNS;
+    build_spec_r<T>(a, Dy, Wp, W, [&](int j, int cd) -> T {
+      const T *r = row(j);
+      if (!r) return (T)0;
+      const int k = mixed ? 2 * cd + 1 : cd + Dy.k0;  // FFT index: the same wavenumber in both bases
+      const int ci = mixed ? cd : k - Y.k0;
+      if (ci < 0 || ci >= Y.ns) return (T)0;
+      const T kap = P.kunit[1] * (T)k;
+      return sgn * (dlike ? kap : -kap) * ((mixed && (ci & 1)) ? (T)-1 : (T)1) * __ldcg(&r[ci]);
+    });
+  }
+  __syncthreads();
+  fft_lines<T, true>(a, b, Ai, W, Wp);
+  T *out = reinterpret_cast<T *>(P.B) + (size_t)P.ncomp * nsx * nuz * nuy + ((size_t)term * nsx + kx) * ndz * ndy;
+  const int cnt = nl * ndy;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int j = e / ndy, yn = e - j * ndy;
+    const int zn = zn0 + j;
+    const bool line = !yt || (zn - Z.u0 >= 0 && zn - Z.u0 < nuz);
+    T v = 0;
+    if (line && yn >= Ai.u0 && yn < Ai.u0 + Ai.nu) v = get_ext_r<T>(a, Ai, Wp, j, yn - Ai.u0);
+    __stcg(&out[(size_t)zn * ndy + yn], v);
+  }
+}
+
 // dispatch one tile of a pass
 template <typename T> __device__ void run_tile(const Prob<T> &P, const Pass<T> &ps, int t, cx<T> *sm, size_t bufsz) {
   switch (ps.kind) {
@@ -1173,6 +1257,7 @@ template <typename T> __device__ void run_tile(const Prob<T> &P, const Pass<T> &
     case PK_MULT1D: tile_mult1d<T>(P, ps, t); break;
     case PK_DERIV: tile_deriv<T>(P, ps, t, sm, bufsz); break;
     case PK_DXINV: tile_dxinv<T>(P, ps, t, sm, bufsz); break;
+    case PK_YTERM: tile_yterm<T>(P, ps, t, sm, bufsz); break;
     default: break;
   }
 }

@@ -31,11 +31,9 @@ def make(dim, n, bc, grid, eig, op, ncomp, prec, fused=True, rhs_scale=0.9):
 
 
 # First derivatives on Dirichlet / Neumann axes are formed where their axis is
-# still spectral (x from the x-spectral field, 2D y in the y stage), so their
-# rounding scales with the derivative itself, and they are held to the stated
-# tolerance.  3D y / z derivatives are passes over the computed psi, whose
-# rounding they weight by kappa (about 2 u kappa_max / kappa_1 relative); the
-# 3D cases here have at most 16 nodes per axis, where that stays far below it.
+# still spectral (x from the x-spectral field, the stage axis in the spectral
+# stage, 3D y in the y-inverse term pass), so their rounding scales with the
+# derivative itself and every output is held to the stated tolerance.
 def op_tol(d, prec):
     return TOL[prec]
 
