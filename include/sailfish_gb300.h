@@ -207,8 +207,9 @@ sf_status sf_solve(sf_plan p);
 /* Paper's Get_Output: enqueue the final inverse transform along x fused with
  * the extraction of the unpadded result and the Dirichlet boundary fill,
  * writing psi ([ncomp][...]) and, when op != NONE, the operator output (for
- * first derivatives on Dirichlet / Neumann axes, derivative passes over the
- * written psi follow). */
+ * first derivatives on Dirichlet / Neumann axes, the inverse y / x passes of
+ * each derivative term follow; they read the plan's spectral workspace, so no
+ * other solve of the plan may run between sf_solve and this call). */
 sf_status sf_get_output(sf_plan p, void *dev_psi, void *dev_op_out);
 
 /* Set_Input + solve + Get_Output in one call (one persistent kernel launch
@@ -269,8 +270,8 @@ int sf_plan_launches(sf_plan p);
 /* Tracing of the last persistent-executor launch of a plan (waits for the
  * plan's stream).  For each of up to 8 pass kinds k (register path: 0 = y
  * forward, 1 = z stage, 2 = y inverse; general engine: the pass kind of the
- * tile, kinds 8, 9 and 10 -- the 1D multiply and the derivative passes --
- * counted with kinds 0, 1 and 2): out[3k] = summed tile time (ns, over all CTAs),
+ * tile, kinds 8 to 11 -- the 1D multiply and the derivative passes -- counted
+ * with kinds 0 to 3): out[3k] = summed tile time (ns, over all CTAs),
  * out[3k+1] = summed time spent waiting for dependencies (ns), out[3k+2] =
  * tiles.  out must hold 24 doubles.  The paper times the solve steps separately (Sec. 5.3); this is
  * the per-pass breakdown of the GPU schedule. */
