@@ -247,7 +247,8 @@ sf_status sf_solve_host_many(sf_plan p, int n, const void *const *host_f, void *
  * transposed derivative passes into plan-owned workspace. */
 sf_status sf_solve_adjoint(sf_plan p, const void *dev_g_psi, const void *dev_g_op, void *dev_g_f);
 
-/* Batched solve of independent problems in one persistent kernel launch.
+/* Batched solve of independent problems in one CUDA graph (one persistent
+ * kernel launch for the members on the general engine).
  * plans: n plans of the same precision (their own stream is ignored; the
  * batch uses cuda_stream).  The batch references the plans' tables and owns
  * a work list and workspace; destroy it before its plans. */
@@ -256,7 +257,11 @@ sf_status sf_batch_create(sf_plan *batch, const sf_plan *plans, int n, void *cud
 /* Enqueue one batched solve: f[i], psi[i], op[i] are the i-th problem's
  * buffers (op may be NULL, or op[i] NULL when that plan has no operator).
  * The first call captures the launch sequence into a CUDA graph that later
- * calls replay while the pointers stay the same. */
+ * calls replay while the pointers stay the same.  Members on the register
+ * fast path run their own three launches in that graph after the persistent
+ * launch of the other members; their buffers are kernel arguments, so a
+ * change of buffers re-captures the graph, and the first call also solves
+ * those members once outside the graph. */
 sf_status sf_batch_solve(sf_plan batch, const void *const *f, void *const *psi, void *const *op);
 
 /* Wait for the plan's stream and report device-side status (SF_ERR_TIMEOUT if

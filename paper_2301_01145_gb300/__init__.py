@@ -132,7 +132,9 @@ class Plan:
 
 
 class Batch:
-    """Independent plans solved together in one persistent launch (CUDA graph)."""
+    """Independent plans solved together in one CUDA graph: one persistent launch
+    for the general-engine members, plus the own launches of members on the
+    register fast path."""
 
     def __init__(self, plans: Sequence[Plan], stream=None):
         self.plans = list(plans)
@@ -140,6 +142,9 @@ class Batch:
 
     def solve(self, fs, psis, ops: Optional[Sequence] = None):
         sf_batch_solve(self.handle, fs, psis, ops)
+
+    def launches(self) -> int:
+        return sf_plan_launches(self.handle)
 
     def sync(self):
         sf_sync(self.handle)

@@ -632,8 +632,9 @@ template <typename T> struct PlanImpl : sf_plan_s {
   sf_status build_green();
   sf_status build_green_semi(const AxisHost *ah);
 
+  // on: the stream to launch on (the plan's stream when null)
   sf_status run_fast(const Prob<T> &Q, const Prob<T> *dq, FastList &fl, bool front, bool back, const IOArgs<T> &io,
-                     int *launches, cudaEvent_t *marks = nullptr);
+                     int *launches, cudaEvent_t *marks = nullptr, cudaStream_t on = nullptr);
 
   sf_status solve_part(bool front, bool back, const void *f, void *psi, void *op, int *launches) override {
     IOArgs<T> io = io_forward(f, psi, op);
@@ -816,12 +817,12 @@ template <typename T> struct PlanImpl : sf_plan_s {
 
 template <typename T>
 sf_status PlanImpl<T>::run_fast(const Prob<T> &, const Prob<T> *, FastList &, bool, bool, const IOArgs<T> &, int *,
-                                cudaEvent_t *) {
+                                cudaEvent_t *, cudaStream_t) {
   return fail(SF_ERR_UNSUPPORTED, "fast path is FP32 only");
 }
 template <>
 sf_status PlanImpl<float>::run_fast(const Prob<float> &Q, const Prob<float> *dq, FastList &fl, bool front, bool back,
-                                    const IOArgs<float> &io, int *launches, cudaEvent_t *marks) {
+                                    const IOArgs<float> &io, int *launches, cudaEvent_t *marks, cudaStream_t on) {
   FastLaunch L{};
   L.marks = marks;
   L.d_prob = dq;
@@ -837,7 +838,7 @@ sf_status PlanImpl<float>::run_fast(const Prob<float> &Q, const Prob<float> *dq,
   L.timeout_ns = kTimeoutNs;
   L.front = front;
   L.back = back;
-  L.stream = stream;
+  L.stream = on ? on : stream;
   const int e = fastE == 16 ? sf_fast_launch_e16(L, io, launches) : sf_fast_launch_e8(L, io, launches);
   if (e) return fail(SF_ERR_CUDA, std::string("fast path launch: ") + cudaGetErrorString((cudaError_t)e));
   return SF_OK;
@@ -1372,6 +1373,12 @@ template <typename T> struct BatchImpl : sf_plan_s {
   std::vector<void *> last_psi, last_op;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t cap = nullptr;  // private stream for graph capture (the legacy stream cannot be captured)
+  // members on the register fast path: their own launches (x forward, y/z
+  // executor, x inverse) in the same graph, after the general members'
+  // persistent launch; their buffers are kernel arguments, so a change of
+  // buffers re-captures the graph
+  std::vector<int> fastm;
+  bool fast_ready = false;  // the fast members' kernels have run once outside a capture
 
   ~BatchImpl() override {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -1385,18 +1392,13 @@ template <typename T> struct BatchImpl : sf_plan_s {
     probs.resize(n);
     for (int i = 0; i < n; ++i) {
       probs[i] = plans[i]->P;
-      if (plans[i]->fastE) {
-        // the batch runs the general engine: give register-path plans full-size intermediates
-        const Prob<T> &q = probs[i];
-        const size_t eI = (size_t)(q.ncomp + q.nop) * q.nsx * q.nuz * q.nsy * sizeof(cx<T>);
-        SF_TRY(mem.alloc(&probs[i].I1, eI));
-        SF_TRY(mem.alloc(&probs[i].I2, eI));
-      }
+      if (plans[i]->fastE) fastm.push_back(i);
     }
     // level-synchronous order: every problem's pass j before any pass j+1, so a
     // problem's dependency is (almost always) complete when its next pass starts
     std::vector<std::vector<Pass<T>>> lists(n);
-    for (int i = 0; i < n; ++i) lists[i] = plans[i]->ex_all.passes;
+    for (int i = 0; i < n; ++i)
+      if (!plans[i]->fastE) lists[i] = plans[i]->ex_all.passes;
     std::vector<int> last(n, -1);
     ex.wcap = plans[0]->d.tune_tile;
     size_t maxlen = 0;
@@ -1423,7 +1425,7 @@ template <typename T> struct BatchImpl : sf_plan_s {
     last_f.assign(n, nullptr);
     last_psi.assign(n, nullptr);
     last_op.assign(n, nullptr);
-    launches_per_exec = 1;
+    launches_per_exec = (ex.passes.empty() ? 0 : 1) + 3 * (int)fastm.size();
     return SF_OK;
   }
 
@@ -1454,6 +1456,20 @@ template <typename T> struct BatchImpl : sf_plan_s {
         last_op[i] = o;
       }
       SF_CK(cudaMemcpy(d_probs, probs.data(), n * sizeof(Prob<T>), cudaMemcpyHostToDevice));
+      if (gexec && !fastm.empty()) {
+        SF_CK(cudaGraphExecDestroy(gexec));
+        gexec = nullptr;
+      }
+      if (!fast_ready && !fastm.empty()) {
+        // one uncaptured run sets the fast kernels' attributes (a solve into the given buffers)
+        for (int i : fastm) {
+          PlanImpl<T> *pl = plans[i];
+          SF_TRY(pl->run_fast(pl->P, pl->d_probs, pl->fl_fwd, true, true, pl->io_forward(f[i], psi[i], op ? op[i] : nullptr),
+                              nullptr, nullptr, stream));
+        }
+        SF_CK(cudaStreamSynchronize(stream));
+        fast_ready = true;
+      }
       if (!gexec) {
         // capture memsets + the persistent launch into a graph (Sec. "persistent batched scheduler")
         cudaGraph_t g;
@@ -1462,6 +1478,12 @@ template <typename T> struct BatchImpl : sf_plan_s {
         IOArgs<T> io{};
         io.use = 0;
         sf_status s = launch_list<T>(ex, d_probs, true, cap, ctl, sticky, io, nullptr);
+        for (size_t m = 0; s == SF_OK && m < fastm.size(); ++m) {
+          PlanImpl<T> *pl = plans[fastm[m]];
+          const int i = fastm[m];
+          s = pl->run_fast(pl->P, pl->d_probs, pl->fl_fwd, true, true, pl->io_forward(f[i], psi[i], op ? op[i] : nullptr),
+                           nullptr, nullptr, cap);
+        }
         cudaError_t e = cudaStreamEndCapture(cap, &g);
         if (s != SF_OK) return s;
         if (e != cudaSuccess) return fail(SF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -1480,13 +1502,23 @@ template <typename T> struct BatchImpl : sf_plan_s {
   sf_status adjoint(const void *, const void *, void *) override { return fail(SF_ERR_STATE, "not available on a batch"); }
   sf_status sync() override {
     SF_CK(cudaStreamSynchronize(stream));
-    unsigned s = 0;
-    SF_CK(cudaMemcpy(&s, sticky, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    if (s) {
-      SF_CK(cudaMemset(sticky, 0, sizeof(unsigned)));
-      return fail(SF_ERR_TIMEOUT, "a scheduler wait exceeded its bound; results are invalid");
+    bool bad = false;
+    for (unsigned *flag : sticky_flags()) {
+      unsigned s = 0;
+      SF_CK(cudaMemcpy(&s, flag, sizeof(unsigned), cudaMemcpyDeviceToHost));
+      if (s) {
+        SF_CK(cudaMemset(flag, 0, sizeof(unsigned)));
+        bad = true;
+      }
     }
+    if (bad) return fail(SF_ERR_TIMEOUT, "a scheduler wait exceeded its bound; results are invalid");
     return SF_OK;
+  }
+  // the batch's timeout flag and those of the fast members' executors
+  std::vector<unsigned *> sticky_flags() const {
+    std::vector<unsigned *> v{sticky};
+    for (int i : fastm) v.push_back(plans[i]->sticky);
+    return v;
   }
   sf_status query(size_t *, size_t *, size_t *, size_t *) override { return fail(SF_ERR_STATE, "query a member plan"); }
   sf_status set_face(int, int, const void *) override { return fail(SF_ERR_STATE, "not available on a batch"); }

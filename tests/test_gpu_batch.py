@@ -107,3 +107,37 @@ def test_clean_batch_reports_no_timeout():
     batch.close()
     for p in plans:
         p.close()
+
+
+def test_batch_runs_register_path_members_on_their_own_launches():
+    # members eligible for the register fast path (3D unbounded 128^3 curl:
+    # padded 256-point axes; 3D periodic 256^3) run their own launches in the
+    # batch's graph, the others the persistent launch; every member equals its
+    # single solve bit for bit, also after the buffers change (re-capture)
+    import torch
+    import paper_2301_01145_gb300 as sf
+    specs = [dict(dim=3, n=(128,) * 3, lo=(-0.5,) * 3, hi=(0.5,) * 3, bc="UUU", op="CURL", ncomp=3, sigma=2.0 / 128,
+                  rhs_scale=-1.0),
+             dict(dim=2, n=(256, 192), lo=(0.0, 0.0), hi=(1.0, 1.0), bc="DN", grid="regular"),
+             dict(dim=3, n=(256,) * 3, lo=(0.0,) * 3, hi=(1.0,) * 3, bc="PPP"),
+             dict(dim=3, n=(32, 48, 64), lo=(-0.5,) * 3, hi=(0.5,) * 3, bc="UUU", sigma=1.0 / 24, rhs_scale=-1.0)]
+    plans = [sf.Plan(**s) for s in specs]
+    batch = sf.Batch(plans)
+    assert batch.launches() == 1 + 3 * 2
+    rng = np.random.default_rng(21)
+    for rep in range(2):
+        fs = [to_dev(rng.normal(size=pl.in_shape), "f32") for pl in plans]
+        psis = [torch.empty(pl.out_shape, dtype=torch.float32, device="cuda") for pl in plans]
+        ops = [torch.empty(pl.op_shape, dtype=torch.float32, device="cuda") if pl.op_shape else None for pl in plans]
+        batch.solve(fs, psis, ops)
+        batch.sync()
+        for pl, f, psi, opo in zip(plans, fs, psis, ops):
+            out = pl(f)
+            pl.sync()
+            ref_psi, ref_op = out if isinstance(out, tuple) else (out, None)
+            assert torch.equal(psi, ref_psi)
+            if opo is not None:
+                assert torch.equal(opo, ref_op)
+    batch.close()
+    for pl in plans:
+        pl.close()
