@@ -119,3 +119,48 @@ def test_get_output_before_solve_is_a_state_error():
     with pytest.raises(sf.SolverError):
         plan.get_output(psi)
     plan.close()
+
+
+# operators on Dirichlet / Neumann axes at the smallest grids: one or two
+# unknowns per axis, regular Dirichlet faces (lines of zeros in every term),
+# the quarter-wave pairs, both precisions
+MINIMAL_OPS = [
+    (3, (3, 3, 3), ("D", "D", "D"), "regular", "GRAD", 1),
+    (3, (2, 3, 2), ("N", "D", "DN"), "regular", "CURL", 3),
+    (3, (2, 2, 2), ("ND", "N", "D"), "staggered", "DIV", 3),
+    (2, (3, 2), ("D", "N"), "regular", "CURL", 1),
+    (2, (2, 2), ("DN", "ND"), "staggered", "GRAD", 1),
+    (2, (2, 3), ("N", "D"), "regular", "DIV", 2),
+    (1, (3,), ("D",), "regular", "GRAD", 1),
+    (1, (2,), ("ND",), "staggered", "GRAD", 1),
+]
+
+
+@pytest.mark.parametrize("case", MINIMAL_OPS, ids=lambda c: f"{c[0]}D-{'-'.join(c[2])}-{c[3]}-{c[4]}")
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_minimal_grids_with_operators(case, prec):
+    dim, n, bc, grid, op, ncomp = case
+    check(dim, n, bc, grid, prec, op=op, ncomp=ncomp)
+
+
+@pytest.mark.parametrize("bc,grid,op,ncomp", [(("D", "N", "DN"), "regular", "CURL", 3),
+                                               (("N", "D", "N"), "staggered", "GRAD", 1),
+                                               (("DN", "D", "N"), "regular", "DIV", 3)])
+def test_bounded_operator_writes_every_output_node(bc, grid, op, ncomp):
+    # outputs filled with NaN first: every node of every operator output is
+    # written (the derivative terms cover face lines and face nodes with zeros)
+    import torch
+    n = (12, 16, 8)
+    plan = gpu_plan(3, n, (0,) * 3, (1,) * 3, bc, grid, op=op, ncomp=ncomp)
+    psi, opo = plan.empty_outputs()
+    psi.fill_(float("nan"))
+    opo.fill_(float("nan"))
+    f = to_dev(np.random.default_rng(4).normal(size=plan.in_shape), "f32")
+    plan.execute(f, psi, opo)
+    plan.sync()
+    assert not torch.isnan(psi).any() and not torch.isnan(opo).any()
+    d = oracle_desc(3, n, (0,) * 3, (1,) * 3, bc, grid, "PS", op, 0.0, ncomp, 1.0)
+    ref_psi, ref_op = oracle.solve(d, to_np(f))
+    for o in range(ref_op.shape[0]):
+        assert rel_l2(to_np(opo)[o], ref_op[o]) <= TOL["f32"], o
+    plan.close()
