@@ -764,15 +764,17 @@ template <typename T> struct PlanImpl : sf_plan_s {
 
   // n host solves in a pipeline: the upload of solve i+1 and the download of
   // solve i-1 run on two side streams while solve i runs on the plan stream;
-  // two device staging sets alternate, ordered by events
-  void *pin[2] = {nullptr, nullptr}, *ppsi[2] = {nullptr, nullptr}, *pop[2] = {nullptr, nullptr};
+  // NSTAGE device staging sets rotate, ordered by events, so that a solve
+  // waits only for the download of the solve NSTAGE steps back
+  static constexpr int NSTAGE = 3;
+  void *pin[NSTAGE] = {}, *ppsi[NSTAGE] = {}, *pop[NSTAGE] = {};
   cudaStream_t s_up = nullptr, s_down = nullptr;
-  cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_down[2] = {nullptr, nullptr};
+  cudaEvent_t ev_up[NSTAGE] = {}, ev_comp[NSTAGE] = {}, ev_down[NSTAGE] = {};
 
   ~PlanImpl() override {
     if (s_up) cudaStreamSynchronize(s_up);
     if (s_down) cudaStreamSynchronize(s_down);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NSTAGE; ++b) {
       if (ev_up[b]) cudaEventDestroy(ev_up[b]);
       if (ev_comp[b]) cudaEventDestroy(ev_comp[b]);
       if (ev_down[b]) cudaEventDestroy(ev_down[b]);
@@ -784,7 +786,7 @@ template <typename T> struct PlanImpl : sf_plan_s {
   sf_status host_solve_many(int n, const void *const *hf, void *const *hpsi, void *const *hop) override {
     const size_t fb = field_elems * sizeof(T);
     if (!s_up) {
-      for (int b = 0; b < 2; ++b) {
+      for (int b = 0; b < NSTAGE; ++b) {
         SF_TRY(mem.alloc(&pin[b], fb * P.ncomp));
         SF_TRY(mem.alloc(&ppsi[b], fb * P.ncomp));
         if (P.nop) SF_TRY(mem.alloc(&pop[b], fb * P.nop));
@@ -796,12 +798,12 @@ template <typename T> struct PlanImpl : sf_plan_s {
       SF_CK(cudaStreamCreateWithFlags(&s_down, cudaStreamNonBlocking));
     }
     for (int i = 0; i < n; ++i) {
-      const int b = i & 1;
-      if (i >= 2) SF_CK(cudaStreamWaitEvent(s_up, ev_comp[b], 0));  // solve i-2 has read pin[b]
+      const int b = i % NSTAGE;
+      if (i >= NSTAGE) SF_CK(cudaStreamWaitEvent(s_up, ev_comp[b], 0));  // the solve that read pin[b] is done
       SF_CK(cudaMemcpyAsync(pin[b], hf[i], fb * P.ncomp, cudaMemcpyHostToDevice, s_up));
       SF_CK(cudaEventRecord(ev_up[b], s_up));
       SF_CK(cudaStreamWaitEvent(stream, ev_up[b], 0));
-      if (i >= 2) SF_CK(cudaStreamWaitEvent(stream, ev_down[b], 0));  // outputs of solve i-2 are home
+      if (i >= NSTAGE) SF_CK(cudaStreamWaitEvent(stream, ev_down[b], 0));  // its outputs are home
       SF_TRY(solve_part(true, true, pin[b], ppsi[b], pop[b], nullptr));
       SF_CK(cudaEventRecord(ev_comp[b], stream));
       SF_CK(cudaStreamWaitEvent(s_down, ev_comp[b], 0));
