@@ -1433,6 +1433,11 @@ template <typename T> struct BatchImpl : sf_plan_s {
 
   sf_status run(const void *const *f, void *const *psi, void *const *op) {
     const int n = (int)plans.size();
+    for (int i = 0; i < n; ++i) {
+      if (!f[i] || !psi[i]) return fail(SF_ERR_ARG, "null buffer in table");
+      if (plans[i]->d.op != SF_OP_NONE && (!op || !op[i]))
+        return fail(SF_ERR_ARG, "a plan with an operator needs its op output");
+    }
     bool changed = !gexec;
     for (int i = 0; i < n; ++i) {
       void *o = op ? op[i] : nullptr;

@@ -141,3 +141,28 @@ def test_batch_runs_register_path_members_on_their_own_launches():
     batch.close()
     for pl in plans:
         pl.close()
+
+
+def test_batch_refuses_missing_buffers():
+    # a member with an operator and no op output, or a null source, is refused
+    # on the host (SF_ERR_ARG) before anything is launched
+    import torch
+    import paper_2301_01145_gb300 as sf
+    from paper_2301_01145_gb300 import SolverError
+    plans = [sf.Plan(3, (32,) * 3, (-0.5,) * 3, (0.5,) * 3, "UUU", op="CURL", ncomp=3, sigma=1.0 / 16, rhs_scale=-1.0),
+             sf.Plan(2, (64, 32), (0.0, 0.0), (1.0, 1.0), "PP")]
+    batch = sf.Batch(plans)
+    fs = [torch.randn(pl.in_shape, device="cuda") for pl in plans]
+    psis = [torch.empty(pl.out_shape, device="cuda") for pl in plans]
+    with pytest.raises(SolverError) as e:
+        batch.solve(fs, psis, None)
+    assert e.value.status == -1
+    with pytest.raises(SolverError) as e:
+        batch.solve(fs, psis, [None, None])
+    assert e.value.status == -1
+    ops = [torch.empty(plans[0].op_shape, device="cuda"), None]
+    batch.solve(fs, psis, ops)
+    batch.sync()
+    batch.close()
+    for pl in plans:
+        pl.close()
