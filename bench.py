@@ -649,6 +649,24 @@ def config_case(name: str, world: int = 1, rank: int = 0):
         if parallelism:
             extra["parallelism"] = parallelism
 
+        def buckets():
+            # each size class (dimension, largest FFT length) of the batch timed as its own batch
+            groups = {}
+            for i, kw in enumerate(kwargs):
+                groups.setdefault(autotune.size_class(kw), []).append(i)
+            out = {}
+            for cls, idx in sorted(groups.items()):
+                sub = sf.Batch([plans[i] for i in idx])
+                fsub, psub = [fs[i] for i in idx], [ps[i] for i in idx]
+                for _ in range(3):
+                    sub.solve(fsub, psub)
+                ms = _events_time(lambda: sub.solve(fsub, psub), 5, torch.cuda.current_stream())
+                pts = sum(probs[i].out_points() for i in idx)
+                out[cls] = {"problems": len(idx), "points": pts, "ms": ms, "points_per_s": pts / (ms * 1e-3)}
+                sub.close()
+            return out
+        extra["buckets"] = buckets
+
         def check():
             picked, seen = [], set()
             for i, bp in enumerate(probs):
@@ -677,7 +695,7 @@ def config_case(name: str, world: int = 1, rank: int = 0):
         torch.cuda.empty_cache()
 
     return {"step": step, "points": points, "dtype": dtype, "cfg": cfg, "check": check, "close": close,
-            "parallelism": extra.get("parallelism")}
+            "parallelism": extra.get("parallelism"), "buckets": extra.get("buckets")}
 
 
 def measure_config(name: str, steps: int, warmup: int, check: bool = True):
@@ -693,6 +711,8 @@ def measure_config(name: str, steps: int, warmup: int, check: bool = True):
                "unit": UNIT, "dtype": case["dtype"], "steps": steps}
         if "knobs" in case["cfg"]:
             out["knobs"] = case["cfg"]["knobs"]
+        if case["buckets"]:
+            out["per_class"] = case["buckets"]()
         if check:
             out["oracle"] = case["check"]()
         return out
@@ -728,6 +748,8 @@ def run_other(args):
     points_all = sum_over_ranks(float(points))  # units every rank processed in one step
     line.update({"metric": f"grid points/s ({args.workload})", "value": points_all / (ms * 1e-3), "ms_per_step": ms,
                  "dtype": dtype, "config": cfg})
+    if rank == 0 and world == 1 and case["buckets"]:
+        line["per_class"] = case["buckets"]()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["oracle"] = case["check"]()
     case["close"]()
