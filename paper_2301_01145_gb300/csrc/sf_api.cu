@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/sailfish_gb300.h"
+#include "sf_engine.cuh"
 #include "sf_fast.cuh"
 
 using namespace sfg;
@@ -417,8 +418,7 @@ template <typename T> sf_status set_kernel_attrs() {
   SF_CK(cudaGetDevice(&dev));
   const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
   if (bit && (done.load() & bit)) return SF_OK;
-  SF_CK(cudaFuncSetAttribute(k_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  SF_CK(cudaFuncSetAttribute(k_exec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  SF_CK(engine_set_attrs<T>());
   done.fetch_or(bit);
   return SF_OK;
 }
@@ -436,19 +436,17 @@ sf_status launch_list(ExecList<T> &ex, const Prob<T> *d_probs, bool fused, cudaS
     int dev = 0, nsm = 0, per = 0;
     SF_CK(cudaGetDevice(&dev));
     SF_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    SF_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_exec<T>, SF_THREADS, ex.smem));
+    SF_CK(engine_exec_occupancy<T>(&per, ex.smem));
     if (per < 1) return fail(SF_ERR_CUDA, "executor does not fit on an SM");
     const int grid = std::min(ex.total, nsm * per);
-    k_exec<T><<<grid, SF_THREADS, ex.smem, st>>>(d_probs, ex.d_passes, ex.d_start, (int)ex.passes.size(), ex.d_done, ctl,
-                                                 sticky, kTimeoutNs, io);
-    SF_CK(cudaGetLastError());
+    SF_CK(engine_launch_exec<T>(grid, ex.smem, st, d_probs, ex.d_passes, ex.d_start, (int)ex.passes.size(), ex.d_done,
+                                ctl, sticky, kTimeoutNs, io));
     if (launches) *launches += 1;
   } else {
     for (size_t i = 0; i < ex.passes.size(); ++i) {
       const Pass<T> &ps = ex.passes[i];
       const size_t sm = (size_t)ps.nbuf * ps.bufsz * sizeof(cx<T>);
-      k_pass<T><<<ps.ntiles, SF_THREADS, sm, st>>>(d_probs, ex.d_passes, (int)i, io);
-      SF_CK(cudaGetLastError());
+      SF_CK(engine_launch_pass<T>(ps.ntiles, sm, st, d_probs, ex.d_passes, (int)i, io));
       if (launches) *launches += 1;
     }
   }
@@ -1765,9 +1763,8 @@ sf_status sf_selftest_timeout(int timeout_ms, void *cuda_stream) {
   SF_CK(cudaMemsetAsync(ex.d_done, 0, ex.passes.size() * sizeof(unsigned), st));
   SF_CK(cudaMemsetAsync(ctl, 0, sizeof(ExecCtl), st));
   IOArgs<float> io{};
-  k_exec<float><<<4, SF_THREADS, 0, st>>>(dq, ex.d_passes, ex.d_start, (int)ex.passes.size(), ex.d_done, ctl, sticky,
-                                          (unsigned long long)timeout_ms * 1000000ull, io);
-  SF_CK(cudaGetLastError());
+  SF_CK(engine_launch_exec<float>(4, 0, st, dq, ex.d_passes, ex.d_start, (int)ex.passes.size(), ex.d_done, ctl, sticky,
+                                  (unsigned long long)timeout_ms * 1000000ull, io));
   SF_CK(cudaStreamSynchronize(st));
   unsigned s = 0;
   SF_CK(cudaMemcpy(&s, sticky, sizeof(unsigned), cudaMemcpyDeviceToHost));
