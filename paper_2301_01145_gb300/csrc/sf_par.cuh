@@ -177,6 +177,19 @@ __device__ __forceinline__ void par_zs(const Prob<float> &P, int S, size_t slot_
   const int ky0 = iy * SF_PAR_ZS_ROWS;
   const float2 *twp = P.ax[2].twf + SF_TWP_OFF;
   const float2 *I1 = reinterpret_cast<const float2 *>(P.I1) + slot_off + (((size_t)c * S + kxl) * 512) * nuz;
+  // the Green's values this thread multiplies in stage 2 (thread (k1, l, pz)),
+  // loaded first so that their latency (the table is mostly not in L2)
+  // overlaps stage 1
+  float gv[16];
+  {
+    const int k1 = threadIdx.x & 15, l = (threadIdx.x >> 4) & 7, pz = threadIdx.x >> 7;
+    const int lo = 2 * k1 + pz, hi = 512 - 2 * k1 - pz;
+    const int kyp = ky0 + l;
+    const int ky = 2 * (kyp & 255) + (kyp >> 8);
+    const float *g = P.ghat_t + ((size_t)kx * P.gny + min(ky, 512 - ky)) * P.gnz;
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) gv[k2] = __ldg(&g[k2 < 8 ? lo + 32 * k2 : hi - 32 * k2]);
+  }
   {
     // stage 1: warp-uniform parity pz = warp / 4; half-warp line l
     const int warp = threadIdx.x >> 5, u = threadIdx.x & 15;
@@ -206,18 +219,9 @@ __device__ __forceinline__ void par_zs(const Prob<float> &P, int S, size_t slot_
   }
   __syncthreads();  // the exchange buffer is rewritten below
   dft16<false>(v);
-  {
-    // Green's table at kz = 2 (k1 + 16 k2) + pz, folded to min(kz, 512 - kz)
-    // read straight from the table (L1 / L2): a half-warp reads 16 values two
-    // floats apart, and staging the rows in shared memory first cost more
-    // (twice the L1 traffic and a wait before the barrier)
-    const int lo = 2 * k1 + pz, hi = 512 - 2 * k1 - pz;
-    const int kyp = ky0 + l;
-    const int ky = 2 * (kyp & 255) + (kyp >> 8);
-    const float *g = P.ghat_t + ((size_t)kx * P.gny + min(ky, 512 - ky)) * P.gnz;
+  // times the Green's table at kz = 2 (k1 + 16 k2) + pz, folded to min(kz, 512 - kz)
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) v[k2] = cscale(v[k2], __ldg(&g[k2 < 8 ? lo + 32 * k2 : hi - 32 * k2]));
-  }
+  for (int k2 = 0; k2 < 16; ++k2) v[k2] = cscale(v[k2], gv[k2]);
   if (c < 2) {
     const float kz1 = __ldg(&P.ax[2].kap[1]);
     float2 d[16];
