@@ -100,7 +100,7 @@ def kernel_bytes(n: int, elem: int = 4):
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fyz launch of this
 # workload (256^3 curl, parity-split y / z stages), from the ncu capture
 # summarised in profiles/k_fyz_c3_256.md; None when the kernel has changed since.
-K_FYZ_TRAFFIC_256 = 473_374_720 + 947_329_536
+K_FYZ_TRAFFIC_256 = 472_694_784 + 1_097_557_760
 
 
 def read_peaks():
