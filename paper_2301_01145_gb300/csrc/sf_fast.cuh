@@ -99,6 +99,25 @@ template <typename T> __host__ __device__ inline int fast_tiles_yi(const Prob<T>
   return Q.nout * nkx * cdiv(Q.nuz, rows);
 }
 
+// Row stride (complex elements) of the 16-line transpose tile of the x
+// inverse transform.  With 512 points the rows are 18 apart, so that the two
+// columns of a line pair are read as one 16-byte load (k layout, 8 lanes
+// per quarter warp; the only bank conflict is a 2-way one between lanes 0
+// and 1); 256-point lines keep 17.  The x forward tile keeps stride 17.
+template <int E> __host__ __device__ constexpr int xts() { return E == 16 ? 18 : 17; }
+// the two columns (a, b) of one line pair at element i of the tile (i even
+// when the stride is: one 16-byte load)
+template <int TS, typename V> __device__ __forceinline__ void col_pair(const V *T, int i, V &a, V &b) {
+  if constexpr (TS % 2 == 0) {
+    const float4 r = *reinterpret_cast<const float4 *>(&T[i]);
+    a = mk<V>(r.x, r.y);
+    b = mk<V>(r.z, r.w);
+  } else {
+    a = T[i];
+    b = T[i + 1];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // XFWD: 16 source lines (8 packed pairs, one per warp) -> A[c][kx][z][y]
 // ---------------------------------------------------------------------------
@@ -204,7 +223,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, 5) k_fx(const Prob<float> *pr
 // shared memory of k_fx / k_fxi: one region that serves as the 16-line
 // transpose tile and, at another time, as the warp buffers
 template <int E> __host__ __device__ constexpr int fast_xi_elems() {
-  return (16 * E + 1) * 17 > fast_wsm_elems<E, 1>() ? (16 * E + 1) * 17 : fast_wsm_elems<E, 1>();
+  return (16 * E + 1) * xts<E>() > fast_wsm_elems<E, 1>() ? (16 * E + 1) * xts<E>() : fast_wsm_elems<E, 1>();
 }
 
 template <int E, bool PAD>
@@ -231,6 +250,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, 5) k_fxi(const Prob<float> *p
   const V *in = reinterpret_cast<const V *>(P.B);
   const size_t plane = (size_t)nuz * nuy;
   const int half = L / 2;
+  constexpr int TS = xts<E>();
   {
     constexpr int CNT = (16 * E + 1) * 16;
     constexpr int PER = (CNT + SF_FAST_THREADS - 1) / SF_FAST_THREADS;
@@ -245,7 +265,7 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, 5) k_fxi(const Prob<float> *p
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
       const int e = threadIdx.x + i * SF_FAST_THREADS;
-      if (e < CNT) T[(e >> 4) * 17 + (e & 15)] = tmp[i];
+      if (e < CNT) T[(e >> 4) * TS + (e & 15)] = tmp[i];
     }
   }
   __syncthreads();
@@ -255,7 +275,8 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, 5) k_fxi(const Prob<float> *p
   for (int j = 0; j < E; ++j) {
     const int k = klayout<E>(t, j);
     if (k <= half) {
-      V A = T[k * 17 + 2 * warp], B = T[k * 17 + 2 * warp + 1];
+      V A, B;
+      col_pair<TS>(T, k * TS + 2 * warp, A, B);
       if (k == 0 || k == half) {
         A.y = 0.f;
         B.y = 0.f;
@@ -263,7 +284,8 @@ __global__ void __launch_bounds__(SF_FAST_THREADS, 5) k_fxi(const Prob<float> *p
       v[j] = mk<V>(A.x - B.y, A.y + B.x);
     } else {
       const int kk = L - k;
-      const V A = T[kk * 17 + 2 * warp], B = T[kk * 17 + 2 * warp + 1];
+      V A, B;
+      col_pair<TS>(T, kk * TS + 2 * warp, A, B);
       v[j] = mk<V>(A.x + B.y, B.x - A.y);
     }
   }
